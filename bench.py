@@ -1,0 +1,474 @@
+"""Benchmark of the SPDZ online phase on one B300 (or N, one process each).
+
+A step is one run of the layered arithmetic circuit of the benchmark
+workload -- 2^20 gates in 32 layers (widths log-uniform in [1k, 64k]), 60%
+Beaver multiplications, 30% add/sub, 10% public-constant multiplications,
+3 parties, p = 2^61 - 1 -- through ``spdz_run_dag``: every gate's masks,
+opens and combines, then the batched MAC check over every opened value.
+Each step consumes fresh triples (a triple is never reused).  Inputs are
+dealt on the device before timing; L2 is flushed (a 256 MB write) between
+timed steps, outside the timed region.
+
+Printed (rank 0, one JSON line): Beaver multiplications per second of the
+scheduled form, the plain per-layer-launch form beside it, the end-to-end
+figure with host buffers, the roofline of the dominant kernel, the batched
+Beaver kernel's roofline at N = 2^24, and the CPU oracle timed on the host.
+
+``--impl reference`` times the CPU oracle instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import spdz_workloads as W  # noqa: E402
+
+METRIC = "Beaver mults/s at n=3, p=2^61-1: batched+learned vs per-layer launch; % roofline"
+N_PARTIES = 3
+INPUT_SUB = 16
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def circuit_bytes(dag, n=N_PARTIES, w=8):
+    """Algorithmic HBM bytes of one run: per party, MUL reads x, y, a, b, c
+    (values and MACs) and writes z (value and MAC) = 12 words; ADD/SUB read 4
+    and write 2 = 6 words; CMUL/CADD read 2 and write 2 = 4 words."""
+    ops = dag.ops
+    nm = int(np.count_nonzero(ops == W.OP_MUL))
+    nas = int(np.count_nonzero((ops == W.OP_ADD) | (ops == W.OP_SUB)))
+    nk = int(np.count_nonzero((ops == W.OP_CMUL) | (ops == W.OP_CADD)))
+    return n * w * (12 * nm + 6 * nas + 4 * nk)
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running (the
+    newer clocks_event_reasons names first, else clocks_throttle_reasons)."""
+    FIELDS = ("active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+        self.Q = None
+        for prefix in ("clocks_event_reasons", "clocks_throttle_reasons"):
+            q = "index,clocks.sm,clocks.max.sm,power.draw," + ",".join(f"{prefix}.{f}" for f in self.FIELDS)
+            try:
+                r = subprocess.run(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                    "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+                if r.returncode == 0:
+                    self.Q = q
+                    break
+            except Exception:
+                pass
+
+    def __enter__(self):
+        if self.Q is None:
+            return self
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, name in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(name)
+            except Exception:
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def max_over_ranks(values, world, device="cuda"):
+    """Element-wise maximum of per-rank timings (the job's time is the
+    slowest rank's); identity on one rank."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+# --------------------------------------------------------------------- ours
+
+class Circuit:
+    """Device world of one circuit: alpha, input wires, a triple pool for
+    `runs` runs, the uploaded circuit."""
+
+    def __init__(self, dag, seed, runs, pool_runs=None):
+        import torch
+        from paper_2512_11112_b300 import shares as SH
+        from paper_2512_11112_b300 import spdz as S
+        self.S, self.SH, self.torch = S, SH, torch
+        self.dag, self.seed = dag, seed
+        self.field = SH.field_of(dag.p)
+        self.stream = torch.cuda.current_stream()
+        self.ctx = S.spdz_ctx_create(N_PARTIES, self.field, self.stream.cuda_stream)
+        self.alpha_sh = SH.zeros(self.field, N_PARTIES)
+        S.spdz_deal_alpha(self.ctx, seed, self.alpha_sh)
+        self.wires = SH.alloc(self.field, N_PARTIES, dag.n_wires)
+        S.spdz_deal_shared(self.ctx, seed, S.SPDZ_KIND_INPUT, INPUT_SUB, 0, dag.n_inputs, self.alpha_sh,
+                           None, self.wires.buf())
+        self.pool_runs = min(runs, pool_runs or runs)
+        self.T = self.pool_runs * dag.n_mul
+        self.tri = [SH.alloc(self.field, N_PARTIES, self.T) for _ in range(3)]
+        self.next_j0 = 0
+        self.refill()
+        S.spdz_set_check_seed(self.ctx, 0x5EED)
+        self.h = S.spdz_dag_create(self.ctx, dag.n_inputs, dag.layer_offsets, dag.ops, dag.in0, dag.in1,
+                                   dag.kconst)
+        self.used = 0
+
+    def refill(self):
+        """Deals a fresh pool of triples (never-used dealer indices) and
+        registers it; the offline phase, never inside a timed region."""
+        S = self.S
+        S.spdz_deal_triples(self.ctx, self.seed, self.next_j0, self.T, self.alpha_sh, *[t.buf() for t in self.tri])
+        S.spdz_load_preproc(self.ctx, self.alpha_sh, *[t.buf() for t in self.tri], self.T)
+        self.next_j0 += self.T
+
+    def ensure(self, runs=1):
+        if self.S.spdz_triples_left(self.ctx) < runs * self.dag.n_mul:
+            self.refill()
+
+    def run(self, plan):
+        self.S.spdz_run_dag(self.ctx, self.h, plan, self.wires.buf(), want_stats=False)
+        self.used += 1
+
+
+def time_steps(circ, plan, steps, warmup, flush):
+    """Times `steps` runs, each bracketed by CUDA events on the context's
+    stream; the L2 flush and any refill of the triple pool sit between the
+    event pairs, outside the timed region."""
+    torch = circ.torch
+    s = circ.stream
+    for _ in range(warmup):
+        circ.ensure()
+        circ.run(plan)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        circ.ensure()
+        flush.zero_()
+        ev[k][0].record(s)
+        circ.run(plan)
+        ev[k][1].record(s)
+    torch.cuda.synchronize()
+    ok = circ.S.spdz_check_result(circ.ctx)
+    return [a.elapsed_time(b) for a, b in ev], ok
+
+
+def beaver_roofline(torch, S, SH, hbm_peak, N=2**24, calls=4):
+    """Standalone batched Beaver multiplication (spdz_mul_batch), n=3, p61:
+    288 algorithmic bytes per product (12 words per party)."""
+    field = S.SPDZ_F61
+    ctx = S.spdz_ctx_create(N_PARTIES, field, torch.cuda.current_stream().cuda_stream)
+    try:
+        a_sh = SH.zeros(field, N_PARTIES)
+        S.spdz_deal_alpha(ctx, 1, a_sh)
+        x, y, z = (SH.alloc(field, N_PARTIES, N) for _ in range(3))
+        S.spdz_deal_shared(ctx, 1, S.SPDZ_KIND_INPUT, 0, 0, N, a_sh, None, x.buf())
+        S.spdz_deal_shared(ctx, 1, S.SPDZ_KIND_INPUT, 1, 0, N, a_sh, None, y.buf())
+        T = (calls + 1) * N
+        tri = [SH.alloc(field, N_PARTIES, T) for _ in range(3)]
+        S.spdz_deal_triples(ctx, 1, 0, T, a_sh, *[t.buf() for t in tri])
+        S.spdz_load_preproc(ctx, a_sh, *[t.buf() for t in tri], T)
+        S.spdz_mul_batch(ctx, x.buf(), y.buf(), z.buf(), N)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(calls):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            S.spdz_mul_batch(ctx, x.buf(), y.buf(), z.buf(), N)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ok = S.spdz_mac_check(ctx)
+        ms = statistics.median(ts)
+        gbs = 288 * N / (ms * 1e-3) / 1e9
+        return {"kernel": "k_mul<F61,3,2> (spdz_mul_batch)", "N": N, "bytes_per_mult": 288,
+                "ms": round(ms, 4), "mults_per_s": N / (ms * 1e-3), "achieved_gbs": round(gbs, 1),
+                "peak_gbs": hbm_peak, "frac": round(gbs / hbm_peak, 4), "mac_check_passed": ok}
+    finally:
+        S.spdz_ctx_destroy(ctx)
+
+
+def e2e_steps(circ, plan, steps):
+    """Same metric through the public call with host buffers: each step
+    copies its input shares and the triples it consumes from pinned host
+    memory, runs, and reads the last layer's output shares back."""
+    torch = circ.torch
+    dag, S = circ.dag, circ.S
+    nin, nm = dag.n_inputs, dag.n_mul
+    out_lo = dag.n_inputs + int(dag.layer_offsets[-2])
+    h_in = [circ.wires.val[:, :nin].cpu().pin_memory(), circ.wires.mac[:, :nin].cpu().pin_memory()]
+    circ.ensure(steps)
+    base = circ.S.spdz_triples_left(circ.ctx)
+    c0 = circ.T - base
+    # each step's own triples (a triple is never reused), staged in pinned memory
+    h_tri = []
+    for k in range(steps):
+        lo = c0 + k * nm
+        h_tri.append([part[:, lo:lo + nm].cpu().pin_memory() for t in circ.tri for part in (t.val, t.mac)])
+    h_out = [torch.empty_like(circ.wires.val[:, out_lo:dag.n_wires], device="cpu").pin_memory()
+             for _ in range(2)]
+    bi = sum(x.numel() * 8 for x in h_in) + sum(x.numel() * 8 for x in h_tri[0])
+    bo = sum(x.numel() * 8 for x in h_out) + 4
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        c = circ.T - S.spdz_triples_left(circ.ctx)
+        circ.wires.val[:, :nin].copy_(h_in[0], non_blocking=True)
+        circ.wires.mac[:, :nin].copy_(h_in[1], non_blocking=True)
+        j = 0
+        for t in circ.tri:
+            for part in (t.val, t.mac):
+                part[:, c:c + nm].copy_(h_tri[k][j], non_blocking=True)
+                j += 1
+        circ.run(plan)
+        h_out[0].copy_(circ.wires.val[:, out_lo:dag.n_wires], non_blocking=True)
+        h_out[1].copy_(circ.wires.mac[:, out_lo:dag.n_wires], non_blocking=True)
+        ok = S.spdz_check_result(circ.ctx)       # reads the verdict: synchronises
+    dt = time.perf_counter() - t0
+    return dt, bi, bo, ok
+
+
+def cpu_baseline(dag, seed):
+    """The CPU oracle as it stands: one evaluation of the whole circuit
+    (gate order, one thread) on the oracle's own dealt shares."""
+    import oracle as O
+    p, n = dag.p, N_PARTIES
+    alpha, ash = O.deal_alpha(p, n, seed)
+    iv, im, _ = O.deal_shared(p, n, seed, O.K_INPUT, INPUT_SUB, 0, dag.n_inputs, alpha)
+    wv, wm = O.zeros(p, n, dag.n_wires), O.zeros(p, n, dag.n_wires)
+    wv[:, :dag.n_inputs], wm[:, :dag.n_inputs] = iv, im
+    tri = O.deal_triples(p, n, seed, 0, dag.n_mul, alpha)
+    t0 = time.perf_counter()
+    O.dag_eval(p, dag, wv, wm, tri, ash)
+    dt = time.perf_counter() - t0
+    return {"value": dag.n_mul / dt, "unit": "Beaver mults/s", "cores": 1, "kind": "oracle",
+            "sample": f"one full evaluation of the benchmark circuit ({dag.n_gates} gates, "
+                      f"{dag.n_mul} Beaver mults, 3 parties) by the oracle's gate-order loop, "
+                      f"{dt:.2f} s"}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_2512_11112_b300 import shares as SH
+    from paper_2512_11112_b300 import spdz as S
+    hbm, peak_src = peaks()
+    dag = W.layered_dag(seed=2)
+    steps, warmup = args.steps, args.warmup
+    e2e_n = min(steps, 5)
+    circ = Circuit(dag, seed=2 + 1000 * rank, runs=2 * (steps + warmup) + e2e_n, pool_runs=64)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    fused = S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=1)
+    per_layer = S.plan(mode=S.SPDZ_SCHED_PER_LAYER, use_graph=0)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    with ClockSampler(local_rank) as clk:
+        t_f, ok_f = time_steps(circ, fused, steps, warmup, flush)
+    barrier()
+    t_p, ok_p = time_steps(circ, per_layer, steps, warmup, flush)
+    barrier()
+    tot_f, tot_p = max_over_ranks([sum(t_f), sum(t_p)], world)
+    e2e_dt, bi, bo, ok_e = e2e_steps(circ, fused, e2e_n)
+    (e2e_dt,) = max_over_ranks([e2e_dt], world)
+    if rank != 0:
+        return
+    nm = dag.n_mul
+    value = world * nm * steps / (tot_f * 1e-3)
+    per_layer_value = world * nm * steps / (tot_p * 1e-3)
+    bytes_run = circuit_bytes(dag)
+    ms = tot_f / steps
+    # the fused kernel dominates the step (one begin and one check kernel of a
+    # few microseconds beside it); its launch duration is bounded by the step
+    achieved = bytes_run / (ms * 1e-3) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            traffic = json.load(open(tr_path)).get("k_dag_fused")
+        except Exception:
+            traffic = None
+    beaver = beaver_roofline(torch, S, SH, hbm)
+    cpu = cpu_baseline(dag, seed=2) if not args.no_cpu_baseline else None
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "Beaver mults/s",
+        "n_gpus": world,
+        "steps": steps,
+        "warmup": warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u64",
+        "data": "synthetic (seeded device dealer; circuit shape from the benchmark recipe)",
+        "config": {"workload": "layered circuit: 2^20 gates, 32 layers, widths log-uniform [1k,64k], "
+                               "60% mul / 15% add / 15% sub / 10% const-mul, n=3, p=2^61-1",
+                   "gates": dag.n_gates, "beaver_mults": nm, "parties": N_PARTIES, "field": "p61",
+                   "scheduler": "fused persistent kernel + CUDA graph", "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}", "widths": dag.meta["widths"]},
+        "mac_check_passed": bool(ok_f and ok_p and ok_e),
+        "per_layer": {"value": per_layer_value, "ms_per_step": tot_p / steps,
+                      "speedup_of_scheduled_form": tot_p / tot_f},
+        "e2e": {"value": world * nm * e2e_n / e2e_dt, "unit": "Beaver mults/s",
+                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+        "roofline": {"bound": "hbm", "kernel": "k_dag_fused<F61,3>", "achieved": round(achieved, 1),
+                     "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
+                     "peak_source": peak_src, "algorithmic_bytes_per_launch": bytes_run},
+        "beaver_batch_roofline": beaver,
+        "gpu_launches": 3 * steps,   # begin, fused circuit and check kernel per step
+        "clocks": clk.summary(),
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- reference
+
+def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle as it stands, each step one bounded
+    sample of the benchmark circuit (its first layers, up to 2^18 gates)."""
+    if rank != 0:
+        return
+    import oracle as O
+    dag = W.layered_dag(seed=2)
+    offs = dag.layer_offsets
+    L = int(np.searchsorted(offs, 2**18, side="right") - 1)
+    L = max(1, L)
+    G = int(offs[L])
+    sub = W.Dag(p=dag.p, n_inputs=dag.n_inputs, ops=dag.ops[:G], in0=dag.in0[:G], in1=dag.in1[:G],
+                kconst=dag.kconst[:G], layer_offsets=offs[:L + 1], seed=dag.seed)
+    p, n = dag.p, N_PARTIES
+    alpha, ash = O.deal_alpha(p, n, 2)
+    iv, im, _ = O.deal_shared(p, n, 2, O.K_INPUT, INPUT_SUB, 0, sub.n_inputs, alpha)
+    tri = O.deal_triples(p, n, 2, 0, sub.n_mul, alpha)
+    times = []
+    for k in range(args.warmup + args.steps):
+        wv, wm = O.zeros(p, n, sub.n_wires), O.zeros(p, n, sub.n_wires)
+        wv[:, :sub.n_inputs], wm[:, :sub.n_inputs] = iv, im
+        t0 = time.perf_counter()
+        O.dag_eval(p, sub, wv, wm, tri, ash)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = sub.n_mul * len(times) / tot
+    sample = f"first {L} layers of the benchmark circuit ({G} gates, {sub.n_mul} Beaver mults, 3 parties)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Beaver mults/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": {"workload": "layered circuit (sample), n=3, p=2^61-1",
+                                            "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "Beaver mults/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "Beaver mults/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_profile(args):
+    """A few launches of one kernel, for ncu: 'dag' runs the benchmark
+    circuit (fused, no graph) `steps` times; 'beaver' runs spdz_mul_batch on
+    2^24 products (n=3, p61) `steps` times."""
+    import torch
+    from paper_2512_11112_b300 import shares as SH
+    from paper_2512_11112_b300 import spdz as S
+    if args.profile == "dag":
+        circ = Circuit(W.layered_dag(seed=2), seed=2, runs=args.steps)
+        plan = S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=0)
+        for _ in range(args.steps):
+            circ.run(plan)
+        torch.cuda.synchronize()
+        assert S.spdz_check_result(circ.ctx)
+    else:
+        beaver_roofline(torch, S, SH, peaks()[0], N=2**24, calls=args.steps)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", default=None, choices=["dag", "beaver"],
+                    help="small run of one kernel for an ncu capture (prints nothing)")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if args.profile:
+        run_profile(args)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,273 @@
+/*
+ * spdz.h -- C ABI of the B300 (sm_103a) SPDZ online-phase library.
+ *
+ * The library evaluates the online phase of SPDZ (An LLVM-Based Optimization
+ * Pipeline for SPDZ, arXiv 2512.11112, Sec. II-A) on additively secret-shared,
+ * MAC-authenticated field elements.  All n parties are simulated on one GPU:
+ * each party's value shares and MAC shares are separate device rows, so
+ * opening a value is an on-device sum over the party rows.
+ *
+ * Fields: p = 2^61 - 1 (one uint64 per element) and p = 2^127 - 1 (two uint64
+ * words per element, low word first, 16-byte aligned).  Every stored share is
+ * canonical, in [0, p).  All arithmetic is exact; nothing here changes the
+ * protocol's results.
+ *
+ * Conventions for every call:
+ *   - Returns an int status (SPDZ_OK or one of the SPDZ_ERR_* codes below);
+ *     no call aborts the process or traps the device.  spdz_last_error()
+ *     returns a text description of the last failure on the context.
+ *   - Device pointers are owned by the caller (for example torch tensors);
+ *     the library never frees them.  Host pointers are read or written
+ *     during the call only.
+ *   - Work is enqueued on the context's stream, in call order.  Calls that
+ *     return a result to the host (spdz_mac_check, spdz_run_dag with stats)
+ *     synchronise that stream.  A context is not thread-safe.
+ */
+#ifndef SPDZ_H
+#define SPDZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+enum spdz_status {
+    SPDZ_OK = 0,
+    SPDZ_ERR_ARG = 1,      /* bad argument (null pointer, size, field, op) */
+    SPDZ_ERR_ALIGN = 2,    /* a device pointer or stride breaks the alignment rule */
+    SPDZ_ERR_OOM = 3,      /* device allocation failed or budget exceeded */
+    SPDZ_ERR_TRIPLES = 4,  /* not enough unused triples: a triple is never reused (Sec. II-A.3) */
+    SPDZ_ERR_MAC = 5,      /* MAC check failed: the protocol aborts (Sec. II-A.4) */
+    SPDZ_ERR_TIMEOUT = 6,  /* a bounded device wait gave up; the results are invalid */
+    SPDZ_ERR_CUDA = 7,     /* a CUDA runtime call failed */
+    SPDZ_ERR_STATE = 8     /* call not valid in the context's current state */
+};
+
+enum spdz_field { SPDZ_F61 = 0, SPDZ_F127 = 1 };
+
+/* Gate / linear-operation codes (Sec. II-A.3 addition; Sec. III-B gate set:
+ * shl by k lowers to a public-constant multiply by 2^k). */
+enum spdz_op {
+    SPDZ_OP_ADD = 0,   /* z = x + y                                     */
+    SPDZ_OP_SUB = 1,   /* z = x - y                                     */
+    SPDZ_OP_CMUL = 2,  /* z = k * x, k public                           */
+    SPDZ_OP_CADD = 3,  /* z = x + k, k public                           */
+    SPDZ_OP_MUL = 4    /* z = x * y by a Beaver triple (circuits only)  */
+};
+
+/* Dealer array kinds: the stream-id "kind" field of the counter PRG. */
+enum spdz_kind {
+    SPDZ_KIND_ALPHA = 1, SPDZ_KIND_TRIPLE_A = 2, SPDZ_KIND_TRIPLE_B = 3,
+    SPDZ_KIND_TRIPLE_C = 4, SPDZ_KIND_INPUT = 5, SPDZ_KIND_CHECK = 6,
+    SPDZ_KIND_MTRIPLE_A = 7, SPDZ_KIND_MTRIPLE_B = 8, SPDZ_KIND_MTRIPLE_C = 9
+};
+
+#define SPDZ_MAX_PARTIES 8
+
+/* A secret-shared array on the device (Sec. II-A.2: party i holds (x_i, m_i)).
+ * Party i's value shares start at val + i*stride elements and its MAC shares
+ * at mac + i*stride elements.  A view of elements [off, off+len) is the same
+ * struct with both pointers advanced by off elements.  Pointers must be
+ * 8-byte aligned (16-byte for p127); 16-byte alignment of the rows enables
+ * 128-bit vector access for p61. */
+typedef struct {
+    void *val;
+    void *mac;
+    int64_t stride;
+} spdz_buf;
+
+typedef struct spdz_ctx spdz_ctx;
+
+/* ---------------------------------------------------------------- context
+ * Creates a context for n_parties (2..SPDZ_MAX_PARTIES) parties over `field`,
+ * enqueuing on `stream` (a cudaStream_t; NULL = legacy default stream) of the
+ * current device.  The context owns a small device workspace (MAC-check
+ * accumulators, the epoch key, barrier counters) and nothing else.
+ * Errors: SPDZ_ERR_ARG, SPDZ_ERR_CUDA, SPDZ_ERR_OOM. */
+int spdz_ctx_create(spdz_ctx **out, int n_parties, int field, void *stream);
+int spdz_ctx_destroy(spdz_ctx *ctx);
+const char *spdz_last_error(const spdz_ctx *ctx);
+/* Replaces the context's stream (for example torch's current stream). */
+int spdz_ctx_set_stream(spdz_ctx *ctx, void *stream);
+
+/* ------------------------------------------------------- preprocessing
+ * Dealer ("fake preprocessing", Sec. IV-A) on the device.  Elements follow the
+ * counter-PRG specification (SplitMix64 counter form; stream id = kind<<56 |
+ * role<<48 | party<<40 | sub), so the CPU reference can regenerate any element
+ * by index.
+ *
+ * spdz_deal_alpha: writes the n shares of the MAC key alpha (Sec. II-A.2) to
+ *   alpha_shares_dev ([n] elements, device).
+ * spdz_deal_shared: elements j0 .. j0+count-1 of the shared array (kind, sub):
+ *   secret uniform (or, when secret_dev is non-NULL, read from it), value and
+ *   MAC shares written to `out`; alpha_shares_dev are the shares it MACs under.
+ *   If secret_out_dev is non-NULL the secrets are also written there.
+ * spdz_deal_triples: Beaver triples j0 .. j0+count-1 (a, b uniform, c = a*b,
+ *   Sec. II-A.3) with MACs, written to a, b, c.
+ * Errors: SPDZ_ERR_ARG, SPDZ_ERR_ALIGN, SPDZ_ERR_CUDA. */
+int spdz_deal_alpha(spdz_ctx *ctx, uint64_t seed, void *alpha_shares_dev);
+int spdz_deal_shared(spdz_ctx *ctx, uint64_t seed, uint32_t kind, uint64_t sub, uint64_t j0,
+                     int64_t count, const void *alpha_shares_dev, const void *secret_dev,
+                     const spdz_buf *out, void *secret_out_dev);
+int spdz_deal_triples(spdz_ctx *ctx, uint64_t seed, uint64_t j0, int64_t count,
+                      const void *alpha_shares_dev, const spdz_buf *a, const spdz_buf *b,
+                      const spdz_buf *c);
+
+/* Registers the preprocessing the online phase consumes: the n alpha shares
+ * (copied into the context) and a pool of n_triples Beaver triples (a, b, c
+ * with MACs, Sec. II-A.3), which is referenced, not copied.  Triples are
+ * consumed in order by a cursor; a triple is never handed out twice
+ * (SPDZ_ERR_TRIPLES when the pool runs out).  Resets the cursor to 0. */
+int spdz_load_preproc(spdz_ctx *ctx, const void *alpha_shares_dev, const spdz_buf *a,
+                      const spdz_buf *b, const spdz_buf *c, int64_t n_triples);
+/* Number of unused triples left in the pool. */
+int spdz_triples_left(const spdz_ctx *ctx, int64_t *left);
+
+/* --------------------------------------------------------- online phase */
+
+/* Local linear gate over N elements (Sec. II-A.3, Addition): ADD/SUB add or
+ * subtract value and MAC shares; CMUL multiplies both by the public k; CADD
+ * adds k to party 0's value share and alpha_i*k to every MAC share.  k_host
+ * points to one field element in host memory (ignored for ADD/SUB); y may be
+ * NULL for CMUL/CADD.  z may alias x or y element for element.
+ * Errors: SPDZ_ERR_ARG, SPDZ_ERR_ALIGN, SPDZ_ERR_STATE (CADD before alpha is
+ * loaded), SPDZ_ERR_CUDA. */
+int spdz_linear(spdz_ctx *ctx, int op, const spdz_buf *x, const spdz_buf *y,
+                const void *k_host, const spdz_buf *z, int64_t N);
+
+/* Beaver multiplication of N element pairs (Sec. II-A.3, Multiplication):
+ * consumes the next N triples; each party masks eps_i = x_i - a_i and
+ * delta_i = y_i - b_i, the values are opened by summing over parties, and
+ *   z_i = c_i + eps*b_i + delta*a_i + [i == 0] eps*delta
+ *   gamma(z)_i = gamma(c)_i + eps*gamma(b)_i + delta*gamma(a)_i + alpha_i*eps*delta.
+ * The opened values join the current MAC-check epoch (eps_j then delta_j);
+ * their random-linear-combination terms are accumulated in the same pass.
+ * If opened_dev is non-NULL it receives the public values, [2N] elements,
+ * eps_j at 2j and delta_j at 2j+1.  z must not alias x, y or the triples.
+ * Errors: SPDZ_ERR_ARG, SPDZ_ERR_ALIGN, SPDZ_ERR_TRIPLES, SPDZ_ERR_STATE,
+ * SPDZ_ERR_CUDA. */
+int spdz_mul_batch(spdz_ctx *ctx, const spdz_buf *x, const spdz_buf *y, const spdz_buf *z,
+                   int64_t N, void *opened_dev);
+
+/* Opens N shared values (Sec. II-A.3): out_dev[j] = sum_i x_i[j] ([N]
+ * elements, device).  The values and their MAC shares join the current
+ * MAC-check epoch. */
+int spdz_open(spdz_ctx *ctx, const spdz_buf *x, void *out_dev, int64_t N);
+
+/* Sets the seed of the MAC-check coefficients and restarts the epoch count at
+ * 0.  The coefficient of the j-th value opened in epoch e is element j of the
+ * PRG stream (SPDZ_KIND_CHECK, 0, 0, e) under this seed.  Must be called with
+ * no value opened since the last check (SPDZ_ERR_STATE otherwise). */
+int spdz_set_check_seed(spdz_ctx *ctx, uint64_t seed);
+
+/* Batched MAC check (Sec. II-A.2/II-A.4, III-D.3) over every value opened in
+ * the current epoch: A = sum r_j v_j, S_i = sum r_j gamma_i(v_j),
+ * sigma_i = S_i - alpha_i*A; passes iff sum_i sigma_i == 0.  Writes *passed
+ * (1/0) and, if sigma_host is non-NULL, the n sigma_i (host, [n] elements);
+ * then starts the next epoch.  Synchronises the stream.  Returns SPDZ_ERR_MAC
+ * when the check fails (the caller must abort the computation). */
+int spdz_mac_check(spdz_ctx *ctx, int *passed, void *sigma_host);
+/* Number of values opened in the current epoch, and the epoch number. */
+int spdz_check_state(const spdz_ctx *ctx, int64_t *opened, int64_t *epoch);
+
+/* `count` secret-shared inner products of length `len` (ReduceAdd over a
+ * MultBatch, Sec. III-B): terms x[t*len + k], y[t*len + k]; each term is a
+ * Beaver product (consuming count*len triples and opening its eps, delta in
+ * one batch); the products' shares are summed locally into z[t] (value and
+ * MAC), with no further open. */
+int spdz_innerprod_batch(spdz_ctx *ctx, const spdz_buf *x, const spdz_buf *y,
+                         const spdz_buf *z, int64_t count, int64_t len);
+
+/* Public elementwise field arithmetic on device arrays: out[j] = a[j] op b[j]
+ * for op in {ADD, SUB, CMUL (= multiply)}.  Exposes the library's modular
+ * arithmetic so it can be checked against exact integer arithmetic. */
+int spdz_field_op(spdz_ctx *ctx, int op, const void *a_dev, const void *b_dev, void *out_dev,
+                  int64_t N);
+
+
+/* ------------------------------------------------------------- circuits
+ * A straight-line arithmetic circuit whose independent gates are already
+ * grouped into layers (the batched regions of Sec. III-B/III-C): gate g of
+ * layer l reads wires in0[g], in1[g] written by earlier layers (or inputs)
+ * and writes wire n_inputs + g.  The t-th MUL gate in gate order consumes
+ * the t-th triple of the run and opens eps_t, delta_t at check-log indices
+ * 2t, 2t+1; a run is one MAC-check epoch of its own. */
+#define SPDZ_MAX_GROUPS 256
+
+typedef struct {
+    int64_t n_inputs;              /* input wires 0 .. n_inputs-1 */
+    int64_t n_gates;
+    int32_t depth;                 /* number of layers */
+    const int64_t *layer_offsets;  /* host [depth+1]; layer l = gates [off[l], off[l+1]) */
+    const uint8_t *ops;            /* host [n_gates] spdz_op codes */
+    const uint32_t *in0;           /* host [n_gates] first operand wire */
+    const uint32_t *in1;           /* host [n_gates] second operand wire (ignored by CMUL/CADD) */
+    const void *kconst;            /* host [n_gates] elements: constant of CMUL/CADD gates */
+} spdz_dag_desc;
+
+typedef struct spdz_dag spdz_dag;
+
+enum spdz_sched {
+    SPDZ_SCHED_PER_LAYER = 0,  /* one kernel launch per layer and gate class (MUL, linear) */
+    SPDZ_SCHED_FUSED = 1       /* persistent kernel per layer group, device barriers between layers */
+};
+
+/* Execution plan of a circuit run.  No plan changes any result bit. */
+typedef struct {
+    int32_t mode;                          /* spdz_sched */
+    int32_t block;                         /* threads per CTA; 0 = 256 */
+    int32_t ctas_per_sm;                   /* resident CTAs per SM (fused); 0 = as many as fit */
+    int32_t use_graph;                     /* capture the run once as a CUDA graph, replay after */
+    int32_t n_groups;                      /* fused: layer groups (one launch each); 0 = one group */
+    int32_t group_end[SPDZ_MAX_GROUPS];    /* exclusive end layer of each group, increasing, last = depth */
+    uint8_t group_flush[SPDZ_MAX_GROUPS];  /* 1: partial MAC check after the group (early abort) */
+    int32_t group_ctas_per_sm[SPDZ_MAX_GROUPS]; /* per-group override of ctas_per_sm; 0 = plan value */
+    int32_t record_layer_times;            /* keep per-layer device times (spdz_dag_layer_times) */
+    uint32_t spin_limit_us;                /* bound of one device barrier wait; 0 = 200000 */
+    int32_t barrier_extra_arrivals;        /* testing: every barrier also waits for this many
+                                              arrivals that never come, so the bounded wait
+                                              runs out (SPDZ_ERR_TIMEOUT); 0 in normal use */
+} spdz_plan;
+
+typedef struct {
+    double device_ms;     /* device time of the run (CUDA events around it) */
+    int32_t passed;       /* MAC-check verdict of the run */
+    int32_t launches;     /* kernels the run executed (inside its graph, if captured) */
+    int64_t n_gates;
+    int64_t n_mul;
+} spdz_stats;
+
+/* Uploads and validates a circuit (every operand wire must come from an
+ * earlier layer or the inputs; SPDZ_ERR_ARG otherwise).  The circuit is bound
+ * to ctx's field and party count. */
+int spdz_dag_create(spdz_ctx *ctx, const spdz_dag_desc *desc, spdz_dag **out);
+int spdz_dag_destroy(spdz_dag *dag);
+
+/* Evaluates the circuit on wires (a [n][>= n_inputs + n_gates] shared array
+ * with the inputs filled in; gate outputs are written), consuming n_mul
+ * triples, then runs the MAC check over everything the run opened.  Needs an
+ * empty check epoch (SPDZ_ERR_STATE otherwise).  plan == NULL lets the
+ * scheduler choose (learned cost model, else autotuned, else a fused
+ * default).  With stats != NULL the call synchronises and fills it, and
+ * returns SPDZ_ERR_MAC if the check failed; with stats == NULL the run is
+ * only enqueued and spdz_check_result() reads the verdict later.
+ * SPDZ_ERR_TIMEOUT: a device barrier wait hit its bound (results invalid). */
+int spdz_run_dag(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan *plan, const spdz_buf *wires,
+                 spdz_stats *stats);
+/* Verdict and sigma (host, [n] elements, may be NULL) of the last completed
+ * check on the context; synchronises the stream. */
+int spdz_check_result(spdz_ctx *ctx, int *passed, void *sigma_host);
+/* Per-layer device times (microseconds, [depth]) of the last run that had
+ * record_layer_times set. */
+int spdz_dag_layer_times(const spdz_dag *dag, float *us_out);
+/* Layer-shape summary used by schedulers: for each layer l, counts[l*5 + c]
+ * is the number of gates of class c (MUL, ADD, SUB, CMUL, CADD). */
+int spdz_dag_layer_counts(const spdz_dag *dag, int32_t *counts_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPDZ_H */

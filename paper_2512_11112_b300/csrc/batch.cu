@@ -1,0 +1,493 @@
+// batch.cu -- elementwise online-phase kernels: local linear gates, Beaver
+// multiplication (mask, open and combine fused in one pass, with the
+// MAC-check random linear combination accumulated in the same pass), opens,
+// inner products and public field arithmetic.
+//
+// Layout: party-major rows (party i's shares at ptr + i*stride); for p61 a
+// thread moves two consecutive elements with one 128-bit access when every
+// row is 16-byte aligned, for p127 one element per 128-bit access.
+#include "common.cuh"
+
+namespace spdz {
+
+int launch_check(spdz_ctx *ctx, int final_check);
+
+// ------------------------------------------------------- vector access
+template <class F, int V, bool STREAM>
+__device__ __forceinline__ void vld(const typename F::T *p, typename F::T (&out)[V]) {
+    if constexpr (F::WORDS == 1) {
+        if constexpr (V == 2) {
+            const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(p);
+            ulonglong2 t = STREAM ? __ldcs(q) : *q;
+            out[0] = t.x;
+            out[1] = t.y;
+        } else {
+            const unsigned long long *q = reinterpret_cast<const unsigned long long *>(p);
+            out[0] = STREAM ? __ldcs(q) : *q;
+        }
+    } else {
+        static_assert(V == 1, "p127 moves one element per access");
+        const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(p);
+        ulonglong2 t = STREAM ? __ldcs(q) : *q;
+        out[0] = {t.x, t.y};
+    }
+}
+
+template <class F, int V>
+__device__ __forceinline__ void vst(typename F::T *p, const typename F::T (&in)[V]) {
+    if constexpr (F::WORDS == 1) {
+        if constexpr (V == 2) {
+            *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(in[0], in[1]);
+        } else {
+            *reinterpret_cast<unsigned long long *>(p) = in[0];
+        }
+    } else {
+        *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(in[0].lo, in[0].hi);
+    }
+}
+
+// --------------------------------------------------------------- linear
+template <class F> struct LinArgs {
+    using T = typename F::T;
+    const T *xv, *xm, *yv, *ym;
+    int64_t xs, ys;
+    T *zv, *zm;
+    int64_t zs;
+    int64_t N;
+    int op;
+    T k;
+    const DevState *ds;
+};
+
+template <class F, int NP, int V>
+__device__ __forceinline__ void linear_elems(const LinArgs<F> &a, int64_t e, const typename F::T (&kal)[NP]) {
+    using T = typename F::T;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        T x[V], gx[V], z[V], gz[V];
+        vld<F, V, false>(a.xv + i * a.xs + e, x);
+        vld<F, V, false>(a.xm + i * a.xs + e, gx);
+        if (a.op == SPDZ_OP_ADD || a.op == SPDZ_OP_SUB) {
+            T y[V], gy[V];
+            vld<F, V, false>(a.yv + i * a.ys + e, y);
+            vld<F, V, false>(a.ym + i * a.ys + e, gy);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                z[v] = a.op == SPDZ_OP_ADD ? F::add(x[v], y[v]) : F::sub(x[v], y[v]);
+                gz[v] = a.op == SPDZ_OP_ADD ? F::add(gx[v], gy[v]) : F::sub(gx[v], gy[v]);
+            }
+        } else if (a.op == SPDZ_OP_CMUL) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                z[v] = F::mul(a.k, x[v]);
+                gz[v] = F::mul(a.k, gx[v]);
+            }
+        } else {  // CADD: party 0 adds k, every MAC share adds alpha_i * k
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                z[v] = i == 0 ? F::add(x[v], a.k) : x[v];
+                gz[v] = F::add(gx[v], kal[i]);
+            }
+        }
+        vst<F, V>(a.zv + i * a.zs + e, z);
+        vst<F, V>(a.zm + i * a.zs + e, gz);
+    }
+}
+
+template <class F, int NP, int V>
+__global__ void __launch_bounds__(256) k_linear(LinArgs<F> a) {
+    using T = typename F::T;
+    T kal[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) kal[i] = a.op == SPDZ_OP_CADD ? F::mul(load_alpha<F>(a.ds, i), a.k) : F::zero();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t ng = a.N / V;
+    for (int64_t g = tid; g < ng; g += stride) linear_elems<F, NP, V>(a, g * V, kal);
+    for (int64_t e = ng * V + tid; e < a.N; e += stride) linear_elems<F, NP, 1>(a, e, kal);
+}
+
+// --------------------------------------------------------------- Beaver
+template <class F> struct MulArgs {
+    using T = typename F::T;
+    const T *xv, *xm, *yv, *ym;
+    int64_t xs, ys;
+    const T *av, *am, *bv, *bm, *cv, *cm;   // triple rows at the consumed cursor
+    int64_t as, bs, cs;
+    T *zv, *zm;
+    int64_t zs;
+    T *opened;        // [2N] public values or null
+    int64_t N;
+    int64_t len;      // inner-product length (innerprod kernel only)
+    uint64_t base;    // epoch index of the first opened value
+    DevState *ds;
+};
+
+// One Beaver product per vector lane v at element e: masks, opens (sum over
+// the party rows), combines, and adds the opened values' random-linear-
+// combination terms to acc (acc[0] = A, acc[1+i] = S_i).
+template <class F, int NP, int V>
+__device__ __forceinline__ void beaver_core(const MulArgs<F> &a, int64_t e, int64_t opened_idx,
+                                            uint64_t key, const typename F::T (&alpha)[NP],
+                                            typename F::T (&acc)[NP + 1], typename F::T (&z)[NP][V],
+                                            typename F::T (&gz)[NP][V], typename F::T (&eps)[V],
+                                            typename F::T (&dlt)[V]) {
+    using T = typename F::T;
+    T av[NP][V], bv[NP][V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) eps[v] = dlt[v] = F::zero();
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        T x[V], y[V];
+        vld<F, V, false>(a.xv + i * a.xs + e, x);
+        vld<F, V, false>(a.yv + i * a.ys + e, y);
+        vld<F, V, true>(a.av + i * a.as + e, av[i]);
+        vld<F, V, true>(a.bv + i * a.bs + e, bv[i]);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            eps[v] = F::add(eps[v], F::sub(x[v], av[i][v]));
+            dlt[v] = F::add(dlt[v], F::sub(y[v], bv[i][v]));
+        }
+    }
+    T de[V], re[V], rd[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        de[v] = F::mul(eps[v], dlt[v]);
+        const uint64_t j = a.base + 2 * (uint64_t)(opened_idx + v);
+        re[v] = Draw<F>::at(key, j);
+        rd[v] = Draw<F>::at(key, j + 1);
+        acc[0] = F::add(acc[0], F::add(F::mul(re[v], eps[v]), F::mul(rd[v], dlt[v])));
+    }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        T c[V], gx[V], gy[V], ga[V], gb[V], gc[V];
+        vld<F, V, true>(a.cv + i * a.cs + e, c);
+        vld<F, V, false>(a.xm + i * a.xs + e, gx);
+        vld<F, V, false>(a.ym + i * a.ys + e, gy);
+        vld<F, V, true>(a.am + i * a.as + e, ga);
+        vld<F, V, true>(a.bm + i * a.bs + e, gb);
+        vld<F, V, true>(a.cm + i * a.cs + e, gc);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            T zz = F::add(c[v], F::add(F::mul(eps[v], bv[i][v]), F::mul(dlt[v], av[i][v])));
+            z[i][v] = i == 0 ? F::add(zz, de[v]) : zz;
+            T gg = F::add(gc[v], F::add(F::mul(eps[v], gb[v]), F::mul(dlt[v], ga[v])));
+            gz[i][v] = F::add(gg, F::mul(alpha[i], de[v]));
+            acc[1 + i] = F::add(acc[1 + i], F::add(F::mul(re[v], F::sub(gx[v], ga[v])),
+                                                   F::mul(rd[v], F::sub(gy[v], gb[v]))));
+        }
+    }
+}
+
+template <class F, int NP, int V>
+__device__ __forceinline__ void mul_elems(const MulArgs<F> &a, int64_t e, uint64_t key,
+                                          const typename F::T (&alpha)[NP], typename F::T (&acc)[NP + 1]) {
+    using T = typename F::T;
+    T z[NP][V], gz[NP][V], eps[V], dlt[V];
+    beaver_core<F, NP, V>(a, e, e, key, alpha, acc, z, gz, eps, dlt);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        vst<F, V>(a.zv + i * a.zs + e, z[i]);
+        vst<F, V>(a.zm + i * a.zs + e, gz[i]);
+    }
+    if (a.opened) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            F::st(a.opened + 2 * (e + v), eps[v]);
+            F::st(a.opened + 2 * (e + v) + 1, dlt[v]);
+        }
+    }
+}
+
+template <class F, int NP, int V>
+__global__ void __launch_bounds__(256) k_mul(MulArgs<F> a) {
+    using T = typename F::T;
+    const uint64_t key = a.ds->key;
+    T alpha[NP], acc[NP + 1];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
+#pragma unroll
+    for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t ng = a.N / V;
+    for (int64_t g = tid; g < ng; g += stride) mul_elems<F, NP, V>(a, g * V, key, alpha, acc);
+    for (int64_t e = ng * V + tid; e < a.N; e += stride) mul_elems<F, NP, 1>(a, e, key, alpha, acc);
+    block_accumulate<F, NP + 1>(acc, a.ds->acc);
+}
+
+// Inner products: one warp per product t; lane l takes terms l, l+32, ...;
+// the per-party sums of the term products (value and MAC) are reduced
+// across the warp and stored by lane 0.  N = number of products.
+template <class F, int NP>
+__global__ void __launch_bounds__(256) k_innerprod(MulArgs<F> a) {
+    using T = typename F::T;
+    const uint64_t key = a.ds->key;
+    T alpha[NP], acc[NP + 1];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
+#pragma unroll
+    for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < a.N; t += wstride) {
+        T sz[NP], sg[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) sz[i] = sg[i] = F::zero();
+        for (int64_t k = lane; k < a.len; k += 32) {
+            const int64_t e = t * a.len + k;
+            T z[NP][1], gz[NP][1], eps[1], dlt[1];
+            beaver_core<F, NP, 1>(a, e, e, key, alpha, acc, z, gz, eps, dlt);
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                sz[i] = F::add(sz[i], z[i][0]);
+                sg[i] = F::add(sg[i], gz[i][0]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            sz[i] = warp_sum<F>(sz[i]);
+            sg[i] = warp_sum<F>(sg[i]);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                F::st(a.zv + i * a.zs + t, sz[i]);
+                F::st(a.zm + i * a.zs + t, sg[i]);
+            }
+        }
+    }
+    block_accumulate<F, NP + 1>(acc, a.ds->acc);
+}
+
+// ----------------------------------------------------------------- open
+template <class F, int NP>
+__global__ void __launch_bounds__(256) k_open(MulArgs<F> a) {
+    using T = typename F::T;
+    const uint64_t key = a.ds->key;
+    T acc[NP + 1];
+#pragma unroll
+    for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < a.N; j += stride) {
+        T v = F::zero(), g[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            v = F::add(v, F::ld(a.xv + i * a.xs + j));
+            g[i] = F::ld(a.xm + i * a.xs + j);
+        }
+        F::st(a.opened + j, v);
+        T r = Draw<F>::at(key, a.base + (uint64_t)j);
+        acc[0] = F::add(acc[0], F::mul(r, v));
+#pragma unroll
+        for (int i = 0; i < NP; ++i) acc[1 + i] = F::add(acc[1 + i], F::mul(r, g[i]));
+    }
+    block_accumulate<F, NP + 1>(acc, a.ds->acc);
+}
+
+// ------------------------------------------------------ public field op
+template <class F>
+__global__ void k_field_op(int op, const typename F::T *x, const typename F::T *y, typename F::T *out, int64_t N) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        typename F::T a = F::ld(x + j), b = F::ld(y + j);
+        F::st(out + j, op == SPDZ_OP_ADD ? F::add(a, b) : op == SPDZ_OP_SUB ? F::sub(a, b) : F::mul(a, b));
+    }
+}
+
+template <class F> static typename F::T host_elem(const void *k) {
+    if constexpr (F::WORDS == 1) {
+        return *(const uint64_t *)k;
+    } else {
+        const uint64_t *w = (const uint64_t *)k;
+        return typename F::T{w[0], w[1]};
+    }
+}
+
+template <class F> static bool host_canonical(const void *k) {
+    if constexpr (F::WORDS == 1) {
+        return *(const uint64_t *)k < F61::P;
+    } else {
+        const uint64_t *w = (const uint64_t *)k;
+        return w[1] < F127::PHI || (w[1] == F127::PHI && w[0] < F127::PLO);
+    }
+}
+
+
+template <class F, int NP>
+static void launch_linear(spdz_ctx *ctx, const LinArgs<F> &a, bool v2) {
+    if constexpr (F::WORDS == 1) {
+        if (v2) {
+            auto kern = k_linear<F, NP, 2>;
+            kern<<<grid_for(ctx, (const void *)kern, 256, 0, (a.N + 1) / 2), 256, 0, ctx->stream>>>(a);
+            return;
+        }
+    }
+    auto kern = k_linear<F, NP, 1>;
+    kern<<<grid_for(ctx, (const void *)kern, 256, 0, a.N), 256, 0, ctx->stream>>>(a);
+}
+
+template <class F, int NP>
+static void launch_mul(spdz_ctx *ctx, const MulArgs<F> &a, bool v2) {
+    if constexpr (F::WORDS == 1) {
+        if (v2) {
+            auto kern = k_mul<F, NP, 2>;
+            kern<<<grid_for(ctx, (const void *)kern, 256, 0, (a.N + 1) / 2), 256, 0, ctx->stream>>>(a);
+            return;
+        }
+    }
+    auto kern = k_mul<F, NP, 1>;
+    kern<<<grid_for(ctx, (const void *)kern, 256, 0, a.N), 256, 0, ctx->stream>>>(a);
+}
+
+}  // namespace spdz
+
+using namespace spdz;
+
+static int take_triples(spdz_ctx *ctx, int64_t count, int64_t *t0) {
+    if (ctx->tri_total - ctx->tri_cursor < count)
+        return set_err(ctx, SPDZ_ERR_TRIPLES, "need %lld triples, %lld left", (long long)count,
+                       (long long)(ctx->tri_total - ctx->tri_cursor));
+    *t0 = ctx->tri_cursor;
+    ctx->tri_cursor += count;
+    return SPDZ_OK;
+}
+
+template <class F>
+static void fill_mul_args(spdz_ctx *ctx, MulArgs<F> &a, const spdz_buf *x, const spdz_buf *y, const spdz_buf *z,
+                          int64_t t0) {
+    using T = typename F::T;
+    a.xv = (const T *)x->val; a.xm = (const T *)x->mac; a.xs = x->stride;
+    a.yv = (const T *)y->val; a.ym = (const T *)y->mac; a.ys = y->stride;
+    a.av = (const T *)ctx->ta.val + t0; a.am = (const T *)ctx->ta.mac + t0; a.as = ctx->ta.stride;
+    a.bv = (const T *)ctx->tb.val + t0; a.bm = (const T *)ctx->tb.mac + t0; a.bs = ctx->tb.stride;
+    a.cv = (const T *)ctx->tc.val + t0; a.cm = (const T *)ctx->tc.mac + t0; a.cs = ctx->tc.stride;
+    a.zv = (T *)z->val; a.zm = (T *)z->mac; a.zs = z->stride;
+    a.ds = ctx->ds;
+    a.base = (uint64_t)ctx->opened;
+}
+
+extern "C" {
+
+int spdz_linear(spdz_ctx *ctx, int op, const spdz_buf *x, const spdz_buf *y, const void *k_host,
+                const spdz_buf *z, int64_t N) {
+    if (!ctx) return SPDZ_ERR_ARG;
+    if (N < 0 || op < SPDZ_OP_ADD || op > SPDZ_OP_CADD) return set_err(ctx, SPDZ_ERR_ARG, "linear: bad op or size");
+    if (N == 0) return SPDZ_OK;
+    int rc;
+    const bool binary = op == SPDZ_OP_ADD || op == SPDZ_OP_SUB;
+    if ((rc = validate_buf(ctx, x, N, "linear.x")) || (binary && (rc = validate_buf(ctx, y, N, "linear.y"))) ||
+        (rc = validate_buf(ctx, z, N, "linear.z")))
+        return rc;
+    if (!binary && !k_host) return set_err(ctx, SPDZ_ERR_ARG, "linear: constant required");
+    if (op == SPDZ_OP_CADD && !ctx->alpha_loaded) return set_err(ctx, SPDZ_ERR_STATE, "linear: CADD needs alpha shares");
+    const bool v2 = ctx->field == SPDZ_F61 && buf_vec2_ok(x) && buf_vec2_ok(z) && (!binary || buf_vec2_ok(y));
+    SPDZ_FIELD_SWITCH(ctx->field, {
+        if (!binary && !host_canonical<F>(k_host)) return set_err(ctx, SPDZ_ERR_ARG, "linear: constant not in [0, p)");
+        using T = typename F::T;
+        LinArgs<F> a{};
+        a.xv = (const T *)x->val; a.xm = (const T *)x->mac; a.xs = x->stride;
+        if (binary) { a.yv = (const T *)y->val; a.ym = (const T *)y->mac; a.ys = y->stride; }
+        a.zv = (T *)z->val; a.zm = (T *)z->mac; a.zs = z->stride;
+        a.N = N; a.op = op; a.k = binary ? F::zero() : host_elem<F>(k_host); a.ds = ctx->ds;
+        SPDZ_NP_SWITCH(ctx->n, launch_linear<F, NP>(ctx, a, v2));
+    });
+    return check_launch(ctx, "linear");
+}
+
+int spdz_mul_batch(spdz_ctx *ctx, const spdz_buf *x, const spdz_buf *y, const spdz_buf *z, int64_t N,
+                   void *opened_dev) {
+    if (!ctx) return SPDZ_ERR_ARG;
+    if (N < 0) return set_err(ctx, SPDZ_ERR_ARG, "mul_batch: negative size");
+    if (N == 0) return SPDZ_OK;
+    if (!ctx->alpha_loaded) return set_err(ctx, SPDZ_ERR_STATE, "mul_batch: preprocessing not loaded");
+    int rc;
+    if ((rc = validate_buf(ctx, x, N, "mul_batch.x")) || (rc = validate_buf(ctx, y, N, "mul_batch.y")) ||
+        (rc = validate_buf(ctx, z, N, "mul_batch.z")))
+        return rc;
+    if (opened_dev && (uintptr_t)opened_dev % elem_bytes(ctx->field))
+        return set_err(ctx, SPDZ_ERR_ALIGN, "mul_batch: misaligned opened buffer");
+    int64_t t0;
+    if ((rc = take_triples(ctx, N, &t0))) return rc;
+    SPDZ_FIELD_SWITCH(ctx->field, {
+        MulArgs<F> a{};
+        fill_mul_args<F>(ctx, a, x, y, z, t0);
+        a.opened = (typename F::T *)opened_dev;
+        a.N = N;
+        spdz_buf ta = ctx->ta, tb = ctx->tb, tc = ctx->tc;
+        ta.val = (char *)ta.val + 8 * t0; ta.mac = (char *)ta.mac + 8 * t0;
+        tb.val = (char *)tb.val + 8 * t0; tb.mac = (char *)tb.mac + 8 * t0;
+        tc.val = (char *)tc.val + 8 * t0; tc.mac = (char *)tc.mac + 8 * t0;
+        const bool v2 = F::WORDS == 1 && buf_vec2_ok(x) && buf_vec2_ok(y) && buf_vec2_ok(z) && buf_vec2_ok(&ta) &&
+                        buf_vec2_ok(&tb) && buf_vec2_ok(&tc) && ((uintptr_t)opened_dev % 16 == 0);
+        SPDZ_NP_SWITCH(ctx->n, launch_mul<F, NP>(ctx, a, v2));
+    });
+    if ((rc = check_launch(ctx, "mul_batch"))) return rc;
+    ctx->opened += 2 * N;
+    return SPDZ_OK;
+}
+
+int spdz_innerprod_batch(spdz_ctx *ctx, const spdz_buf *x, const spdz_buf *y, const spdz_buf *z, int64_t count,
+                         int64_t len) {
+    if (!ctx) return SPDZ_ERR_ARG;
+    if (count < 0 || len < 0) return set_err(ctx, SPDZ_ERR_ARG, "innerprod: negative size");
+    if (count == 0) return SPDZ_OK;
+    if (!ctx->alpha_loaded) return set_err(ctx, SPDZ_ERR_STATE, "innerprod: preprocessing not loaded");
+    const int64_t T = count * len;
+    int rc;
+    if ((rc = validate_buf(ctx, x, T, "innerprod.x")) || (rc = validate_buf(ctx, y, T, "innerprod.y")) ||
+        (rc = validate_buf(ctx, z, count, "innerprod.z")))
+        return rc;
+    int64_t t0;
+    if ((rc = take_triples(ctx, T, &t0))) return rc;
+    SPDZ_FIELD_SWITCH(ctx->field, {
+        MulArgs<F> a{};
+        fill_mul_args<F>(ctx, a, x, y, z, t0);
+        a.N = count;
+        a.len = len;
+        SPDZ_NP_SWITCH(ctx->n, {
+            auto kern = k_innerprod<F, NP>;
+            kern<<<grid_for(ctx, (const void *)kern, 256, 0, count * 32), 256, 0, ctx->stream>>>(a);
+        });
+    });
+    if ((rc = check_launch(ctx, "innerprod"))) return rc;
+    ctx->opened += 2 * T;
+    return SPDZ_OK;
+}
+
+int spdz_open(spdz_ctx *ctx, const spdz_buf *x, void *out_dev, int64_t N) {
+    if (!ctx) return SPDZ_ERR_ARG;
+    if (N < 0 || !out_dev) return set_err(ctx, SPDZ_ERR_ARG, "open: bad argument");
+    if (N == 0) return SPDZ_OK;
+    int rc;
+    if ((rc = validate_buf(ctx, x, N, "open.x"))) return rc;
+    if ((uintptr_t)out_dev % elem_bytes(ctx->field)) return set_err(ctx, SPDZ_ERR_ALIGN, "open: misaligned output");
+    SPDZ_FIELD_SWITCH(ctx->field, {
+        using T = typename F::T;
+        MulArgs<F> a{};
+        a.xv = (const T *)x->val; a.xm = (const T *)x->mac; a.xs = x->stride;
+        a.opened = (T *)out_dev; a.N = N; a.ds = ctx->ds; a.base = (uint64_t)ctx->opened;
+        SPDZ_NP_SWITCH(ctx->n, {
+            auto kern = k_open<F, NP>;
+            kern<<<grid_for(ctx, (const void *)kern, 256, 0, N), 256, 0, ctx->stream>>>(a);
+        });
+    });
+    if ((rc = check_launch(ctx, "open"))) return rc;
+    ctx->opened += N;
+    return SPDZ_OK;
+}
+
+int spdz_field_op(spdz_ctx *ctx, int op, const void *a_dev, const void *b_dev, void *out_dev, int64_t N) {
+    if (!ctx) return SPDZ_ERR_ARG;
+    if (N < 0 || !a_dev || !b_dev || !out_dev || (op != SPDZ_OP_ADD && op != SPDZ_OP_SUB && op != SPDZ_OP_CMUL))
+        return set_err(ctx, SPDZ_ERR_ARG, "field_op: bad argument");
+    if (N == 0) return SPDZ_OK;
+    SPDZ_FIELD_SWITCH(ctx->field, {
+        using T = typename F::T;
+        auto kern = k_field_op<F>;
+        kern<<<grid_for(ctx, (const void *)kern, 256, 0, N), 256, 0, ctx->stream>>>(op, (const T *)a_dev,
+                                                                                    (const T *)b_dev, (T *)out_dev, N);
+    });
+    return check_launch(ctx, "field_op");
+}
+
+}  // extern "C"

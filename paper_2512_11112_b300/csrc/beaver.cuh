@@ -1,0 +1,69 @@
+// beaver.cuh -- the arithmetic of one Beaver product and of the linear gates,
+// on shares already in registers (Sec. II-A.3 of the paper).
+#pragma once
+#include "common.cuh"
+
+namespace spdz {
+
+// Inputs per party i: x_i, gamma(x)_i, y_i, gamma(y)_i and the triple shares
+// (a, b, c) with their MAC shares (read through an accessor, so they can stay
+// in shared memory until used).  Opens eps = sum(x_i - a_i) and
+// delta = sum(y_i - b_i) and combines
+//   z_i = c_i + eps*b_i + delta*a_i + [i == 0] eps*delta
+//   gamma(z)_i = gamma(c)_i + eps*gamma(b)_i + delta*gamma(a)_i + alpha_i*eps*delta.
+// The opened eps (index j) and delta (index j+1) of the check's log add
+// r_j*eps + r_{j+1}*delta to acc[0] and r_j*(gamma(x)_i - gamma(a)_i) +
+// r_{j+1}*(gamma(y)_i - gamma(b)_i) to acc[1+i].
+template <class F, int NP, class TRI>
+__device__ __forceinline__ void beaver_math_src(
+    const typename F::T (&x)[NP], const typename F::T (&gx)[NP], const typename F::T (&y)[NP],
+    const typename F::T (&gy)[NP], const TRI &tri, const typename F::T (&alpha)[NP], uint64_t key, uint64_t j,
+    typename F::T (&acc)[NP + 1], typename F::T (&z)[NP], typename F::T (&gz)[NP]) {
+    // tri(k, i): triple share k of party i, k = 0..5 for a, gamma(a), b,
+    // gamma(b), c, gamma(c)
+    using T = typename F::T;
+    T eps = F::zero(), dlt = F::zero();
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        eps = F::add(eps, F::sub(x[i], tri(0, i)));
+        dlt = F::add(dlt, F::sub(y[i], tri(2, i)));
+    }
+    const T de = F::mul(eps, dlt);
+    const T re = Draw<F>::at(key, j), rd = Draw<F>::at(key, j + 1);
+    acc[0] = F::add(acc[0], F::add(F::mul(re, eps), F::mul(rd, dlt)));
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        const T zz = F::add(tri(4, i), F::add(F::mul(eps, tri(2, i)), F::mul(dlt, tri(0, i))));
+        z[i] = i == 0 ? F::add(zz, de) : zz;
+        gz[i] = F::add(F::add(tri(5, i), F::add(F::mul(eps, tri(3, i)), F::mul(dlt, tri(1, i)))), F::mul(alpha[i], de));
+        acc[1 + i] = F::add(acc[1 + i], F::add(F::mul(re, F::sub(gx[i], tri(1, i))), F::mul(rd, F::sub(gy[i], tri(3, i)))));
+    }
+}
+
+template <class F, int NP>
+__device__ __forceinline__ void beaver_math(
+    const typename F::T (&x)[NP], const typename F::T (&gx)[NP], const typename F::T (&y)[NP],
+    const typename F::T (&gy)[NP], const typename F::T (&a)[NP], const typename F::T (&ga)[NP],
+    const typename F::T (&b)[NP], const typename F::T (&gb)[NP], const typename F::T (&c)[NP],
+    const typename F::T (&gc)[NP], const typename F::T (&alpha)[NP], uint64_t key, uint64_t j,
+    typename F::T (&acc)[NP + 1], typename F::T (&z)[NP], typename F::T (&gz)[NP]) {
+    auto tri = [&](int k, int i) -> typename F::T {
+        return k == 0 ? a[i] : k == 1 ? ga[i] : k == 2 ? b[i] : k == 3 ? gb[i] : k == 4 ? c[i] : gc[i];
+    };
+    beaver_math_src<F, NP>(x, gx, y, gy, tri, alpha, key, j, acc, z, gz);
+}
+
+// Linear gate on one party's shares.  kal = alpha_i * k (used by CADD only).
+template <class F>
+__device__ __forceinline__ void linear_math(int op, int party, typename F::T x, typename F::T gx,
+                                            typename F::T y, typename F::T gy, typename F::T k,
+                                            typename F::T kal, typename F::T &z, typename F::T &gz) {
+    switch (op) {
+        case SPDZ_OP_ADD: z = F::add(x, y); gz = F::add(gx, gy); break;
+        case SPDZ_OP_SUB: z = F::sub(x, y); gz = F::sub(gx, gy); break;
+        case SPDZ_OP_CMUL: z = F::mul(k, x); gz = F::mul(k, gx); break;
+        default: z = party == 0 ? F::add(x, k) : x; gz = F::add(gx, kal); break;
+    }
+}
+
+}  // namespace spdz

@@ -1,0 +1,772 @@
+// dag.cu -- evaluation of layered arithmetic circuits (the batched regions of
+// Sec. III-B/III-C of the paper, with the independent gates of a layer already
+// grouped).
+//
+// Two executions of the same circuit, bit-identical by construction:
+//   * per-layer: one kernel launch per layer and gate class (MUL, linear),
+//     stream-ordered -- the plain baseline;
+//   * fused: one persistent kernel per group of consecutive layers; CTAs
+//     meet at a device-wide barrier between layers (bounded wait, timeout
+//     status instead of a hang), the run is captured once as a CUDA graph and
+//     replayed.
+// In both, a MUL gate masks, opens (sum over the party rows in registers) and
+// combines in one pass, and the MAC-check terms of its opened values are
+// accumulated in registers and reduced once per kernel.
+//
+// Device layout of a circuit: 16-byte gate records sorted per layer, MUL
+// gates first (in gate order, so their triples are consecutive), then linear
+// gates:  {in0 wire, in1 wire, out wire, op << 29 | aux}, aux = the gate's
+// MUL rank (triple index within the run) or its gate id (constant index).
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "beaver.cuh"
+
+namespace spdz {
+
+int launch_check(spdz_ctx *ctx, int final_check);
+
+
+template <class F> __device__ __forceinline__ typename F::T ld_cg(const typename F::T *p);
+template <> __device__ __forceinline__ F61::T ld_cg<F61>(const F61::T *p) {
+    return __ldcg(reinterpret_cast<const unsigned long long *>(p));
+}
+template <> __device__ __forceinline__ F127::T ld_cg<F127>(const F127::T *p) {
+    ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2 *>(p));
+    return {v.x, v.y};
+}
+template <class F> __device__ __forceinline__ typename F::T ld_cs(const typename F::T *p);
+template <> __device__ __forceinline__ F61::T ld_cs<F61>(const F61::T *p) {
+    return __ldcs(reinterpret_cast<const unsigned long long *>(p));
+}
+template <> __device__ __forceinline__ F127::T ld_cs<F127>(const F127::T *p) {
+    ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2 *>(p));
+    return {v.x, v.y};
+}
+
+// One row per layer: record ranges of the five gate classes (MUL, ADD, SUB,
+// CMUL, CADD, in that order) and the MUL rank of the layer's first MUL gate.
+struct LayerRow {
+    int32_t s[6];        // s[c] = first record of class c, s[5] = end of the layer
+    int32_t mulbase;
+    int32_t pad;
+};
+
+enum : int { C_MUL = 0, C_ADD = 1, C_SUB = 2, C_CMUL = 3, C_CADD = 4 };
+
+__device__ __forceinline__ int class_of(const LayerRow &L, int32_t r) {
+    return r < L.s[1] ? C_MUL : r < L.s[2] ? C_ADD : r < L.s[3] ? C_SUB : r < L.s[4] ? C_CMUL : C_CADD;
+}
+
+__device__ __forceinline__ LayerRow load_row(const LayerRow *lay, int l) {
+    const int4 *p = reinterpret_cast<const int4 *>(lay + l);
+    int4 a = __ldg(p), b = __ldg(p + 1);
+    LayerRow L;
+    L.s[0] = a.x; L.s[1] = a.y; L.s[2] = a.z; L.s[3] = a.w;
+    L.s[4] = b.x; L.s[5] = b.y; L.mulbase = b.z; L.pad = b.w;
+    return L;
+}
+
+template <class F> struct DagArgs {
+    using T = typename F::T;
+    const uint4 *rec;                       // {in0, in1, out, 0} in execution order
+    const T *kc;                            // constants in record order (CMUL/CADD records)
+    const LayerRow *lay;                    // [depth]
+    T *wv, *wm;
+    int64_t ws;
+    const T *tp[6];                         // triple rows: a, gamma(a), b, gamma(b), c, gamma(c)
+    int64_t ts[6];                          // their party strides
+    DevState *ds;
+    int32_t l0, l1;                         // layers [l0, l1)
+    int32_t r0, r1;                         // per-layer kernels: records [r0, r1) of layer l0
+    uint32_t bar_base;                      // fused: barrier arrivals before this launch
+    uint64_t spin_ns;
+    int32_t record_ts;
+    uint32_t extra_arrivals;                // testing: arrivals that never come
+};
+
+// Operands of one gate that do not depend on earlier layers: its record,
+// its triple shares (MUL) or its constant (CMUL/CADD).
+template <class F, int NP> struct GateIn {
+    using T = typename F::T;
+    uint4 rec;
+    T tri[6][NP];
+    T k;
+};
+
+template <class F, int NP>
+__device__ __forceinline__ void gate_load_direct(const DagArgs<F> &a, const LayerRow &L, int32_t r, int cls,
+                                                 uint64_t tri_base, GateIn<F, NP> &g) {
+    g.rec = __ldg(&a.rec[r]);
+    if (cls == C_MUL) {
+        const int64_t t = (int64_t)tri_base + L.mulbase + (r - L.s[0]);
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+#pragma unroll
+            for (int i = 0; i < NP; ++i) g.tri[k][i] = ld_cs<F>(a.tp[k] + i * a.ts[k] + t);
+    } else if (cls >= C_CMUL) {
+        g.k = F::ld(a.kc + r);
+    }
+}
+
+// Masks, opens, combines (MUL) or applies the linear gate, reading the wire
+// operands (written by earlier layers: L2, never L1) and storing the output.
+template <class F, int NP, class TRI>
+__device__ __forceinline__ void gate_exec(const DagArgs<F> &a, const LayerRow &L, int32_t r, int cls, uint4 rec,
+                                          typename F::T kconst, const TRI &tri, uint64_t key,
+                                          const typename F::T (&alpha)[NP], typename F::T (&acc)[NP + 1]) {
+    using T = typename F::T;
+    const uint32_t in0 = rec.x, in1 = rec.y, out = rec.z;
+    if (cls == C_MUL) {
+        T x[NP], gx[NP], y[NP], gy[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            x[i] = ld_cg<F>(a.wv + i * a.ws + in0);
+            y[i] = ld_cg<F>(a.wv + i * a.ws + in1);
+            gx[i] = ld_cg<F>(a.wm + i * a.ws + in0);
+            gy[i] = ld_cg<F>(a.wm + i * a.ws + in1);
+        }
+        T z[NP], gz[NP];
+        const uint64_t rank = (uint64_t)(L.mulbase + (r - L.s[0]));
+        beaver_math_src<F, NP>(x, gx, y, gy, tri, alpha, key, 2 * rank, acc, z, gz);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            F::st(a.wv + i * a.ws + out, z[i]);
+            F::st(a.wm + i * a.ws + out, gz[i]);
+        }
+    } else {
+        const int op = cls == C_ADD ? SPDZ_OP_ADD : cls == C_SUB ? SPDZ_OP_SUB : cls == C_CMUL ? SPDZ_OP_CMUL : SPDZ_OP_CADD;
+        const bool binary = cls <= C_SUB;
+        const T k = binary ? F::zero() : kconst;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            const T x = ld_cg<F>(a.wv + i * a.ws + in0), gx = ld_cg<F>(a.wm + i * a.ws + in0);
+            T y = F::zero(), gy = F::zero();
+            if (binary) {
+                y = ld_cg<F>(a.wv + i * a.ws + in1);
+                gy = ld_cg<F>(a.wm + i * a.ws + in1);
+            }
+            const T kal = cls == C_CADD ? F::mul(alpha[i], k) : F::zero();
+            T z, gz;
+            linear_math<F>(op, i, x, gx, y, gy, k, kal, z, gz);
+            F::st(a.wv + i * a.ws + out, z);
+            F::st(a.wm + i * a.ws + out, gz);
+        }
+    }
+}
+
+// ----------------------------------------------- asynchronous prefetch
+// Each thread stages the layer-independent operands of its next gate in its
+// own shared-memory slots (structure of arrays across the block, so the
+// accesses are conflict-free) with cp.async; nothing is shared between
+// threads, so only the thread's own wait is needed before use.
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem, int bytes) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    if (bytes == 16)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <class F, int NP> struct Stage {
+    using T = typename F::T;
+    uint4 *rec;      // [B]
+    T *tri;          // [6*NP][B]
+    T *k;            // [B]
+    int B;
+    __device__ __forceinline__ void init(unsigned char *base, int block) {
+        B = block;
+        rec = reinterpret_cast<uint4 *>(base);
+        tri = reinterpret_cast<T *>(base + sizeof(uint4) * block);
+        k = tri + 6 * NP * block;
+    }
+    static constexpr size_t bytes_per_thread() { return sizeof(uint4) + (6 * NP + 1) * sizeof(T); }
+};
+
+template <class F, int NP>
+__device__ __forceinline__ void stage_issue(const DagArgs<F> &a, const LayerRow &L, int32_t r, int cls,
+                                            uint64_t tri_base, const Stage<F, NP> &st) {
+    using T = typename F::T;
+    const int t = threadIdx.x;
+    cp_async(&st.rec[t], &a.rec[r], 16);
+    if (cls == C_MUL) {
+        const int64_t ti = (int64_t)tri_base + L.mulbase + (r - L.s[0]);
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+#pragma unroll
+            for (int i = 0; i < NP; ++i) cp_async(&st.tri[(k * NP + i) * st.B + t], a.tp[k] + i * a.ts[k] + ti, (int)sizeof(T));
+    } else if (cls >= C_CMUL) {
+        cp_async(&st.k[t], a.kc + r, (int)sizeof(T));
+    }
+    cp_async_commit();
+}
+
+// Direct and staged sources of a gate's triple shares.
+template <class F, int NP> struct TriRegs {
+    const GateIn<F, NP> &g;
+    __device__ __forceinline__ typename F::T operator()(int k, int i) const { return g.tri[k][i]; }
+};
+template <class F, int NP> struct TriSmem {
+    const typename F::T *base;   // st.tri + threadIdx.x
+    int B;
+    __device__ __forceinline__ typename F::T operator()(int k, int i) const { return base[(k * NP + i) * B]; }
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Device-wide barrier over the CTAs of one launch.  Arrivals are counted on
+// a run-wide counter with a release reduction (no returned value to wait
+// for); thread 0 polls with acquire loads.  The wait is bounded by spin_ns,
+// after which the CTA records a timeout, raises the abort flag and returns
+// false (every later barrier of the run then returns false at once).
+__device__ __forceinline__ bool grid_barrier(DevState *ds, unsigned int target, uint64_t spin_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ds->bar_count) : "memory");
+        const unsigned long long t0 = gtimer();
+        while (true) {
+            unsigned int v, ab;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ds->bar_count) : "memory");
+            if ((int)(v - target) >= 0) break;
+            asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(ab) : "l"(&ds->bar_abort) : "memory");
+            if (ab) { ok = 0; break; }
+            if (gtimer() - t0 > spin_ns) {
+                atomicOr(&ds->err_flags, ERR_TIMEOUT);
+                atomicExch(&ds->bar_abort, 1u);
+                ok = 0;
+                break;
+            }
+            __nanosleep(20);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Start of a run: the triple cursor the run consumes from, fresh barrier
+// counters and error flags.  Its argument is updated before every replay of
+// a captured run.
+__global__ void k_run_begin(DevState *ds, uint64_t tri_base) {
+    ds->tri_cursor = tri_base;
+    ds->bar_count = 0;
+    ds->bar_abort = 0;
+    ds->err_flags = 0;
+}
+
+// Per-layer form: records [r0, r1) of layer l0 (one gate class range).
+template <class F, int NP>
+__global__ void __launch_bounds__(256) k_dag_segment(DagArgs<F> a) {
+    using T = typename F::T;
+    const uint64_t key = a.ds->key, tri_base = a.ds->tri_cursor;
+    T alpha[NP], acc[NP + 1];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
+#pragma unroll
+    for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
+    const LayerRow L = load_row(a.lay, a.l0);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = a.r0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.r1; r += stride) {
+        const int cls = class_of(L, (int32_t)r);
+        GateIn<F, NP> g;
+        gate_load_direct<F, NP>(a, L, (int32_t)r, cls, tri_base, g);
+        gate_exec<F, NP>(a, L, (int32_t)r, cls, g.rec, g.k, TriRegs<F, NP>{g}, key, alpha, acc);
+    }
+    block_accumulate<F, NP + 1>(acc, a.ds->acc);
+}
+
+// Fused form: layers [l0, l1) in one persistent launch.  Thread t owns
+// gates t, t + nthreads, ... of every layer; the operands of its first gate
+// of layer l+1 are staged in shared memory while the CTA waits at the
+// barrier that ends layer l.
+template <class F, int NP>
+__device__ __forceinline__ void dag_fused_body(const DagArgs<F> &a) {
+    using T = typename F::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    Stage<F, NP> st;
+    st.init(smem, blockDim.x);
+    const uint64_t key = a.ds->key, tri_base = a.ds->tri_cursor;
+    T alpha[NP], acc[NP + 1];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
+#pragma unroll
+    for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
+    const int32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t nthreads = gridDim.x * blockDim.x;
+    const bool stamp = a.record_ts && blockIdx.x == 0 && threadIdx.x == 0;
+    if (stamp) a.ds->layer_ts[a.l0] = gtimer();
+    LayerRow L = load_row(a.lay, a.l0);
+    int32_t r = L.s[0] + tid;
+    bool staged = r < L.s[5];
+    if (staged) stage_issue<F, NP>(a, L, r, class_of(L, r), tri_base, st);
+    bool ok = true;
+    unsigned int nb = 0;
+    for (int32_t l = a.l0; l < a.l1; ++l) {
+        if (ok) {
+            if (staged) {
+                const int cls = class_of(L, r);
+                cp_async_wait_all();
+                const uint4 rec = st.rec[threadIdx.x];
+                const T kk = cls >= C_CMUL ? st.k[threadIdx.x] : F::zero();
+                gate_exec<F, NP>(a, L, r, cls, rec, kk, TriSmem<F, NP>{st.tri + threadIdx.x, st.B}, key, alpha, acc);
+            }
+            for (int32_t q = r + nthreads; q < L.s[5]; q += nthreads) {
+                const int cls = class_of(L, q);
+                GateIn<F, NP> g;
+                gate_load_direct<F, NP>(a, L, q, cls, tri_base, g);
+                gate_exec<F, NP>(a, L, q, cls, g.rec, g.k, TriRegs<F, NP>{g}, key, alpha, acc);
+            }
+        }
+        staged = false;
+        if (l + 1 < a.l1) {
+            L = load_row(a.lay, l + 1);
+            r = L.s[0] + tid;
+            staged = ok && r < L.s[5];
+            if (staged) stage_issue<F, NP>(a, L, r, class_of(L, r), tri_base, st);
+        }
+        if (l + 1 < a.l1 || a.record_ts) {
+            ++nb;
+            ok = grid_barrier(a.ds, a.bar_base + nb * gridDim.x + a.extra_arrivals, a.spin_ns) && ok;
+            if (stamp) a.ds->layer_ts[l + 1] = gtimer();
+        }
+    }
+    cp_async_wait_all();
+    block_accumulate<F, NP + 1>(acc, a.ds->acc);
+}
+
+// Two CTAs of 256 threads per SM for p61 (128 registers); p127 operands are
+// twice as wide, so its kernel is bounded for one CTA per SM instead.
+template <class F, int NP>
+__global__ void __launch_bounds__(256, 2) k_dag_fused(DagArgs<F> a) {
+    dag_fused_body<F, NP>(a);
+}
+template <class F, int NP>
+__global__ void __launch_bounds__(256, 1) k_dag_fused_wide(DagArgs<F> a) {
+    dag_fused_body<F, NP>(a);
+}
+
+template <class F, int NP> constexpr size_t fused_smem(int block) {
+    return Stage<F, NP>::bytes_per_thread() * (size_t)block;
+}
+
+}  // namespace spdz
+
+using namespace spdz;
+
+struct spdz_dag {
+    spdz_ctx *ctx = nullptr;
+    int field = 0, n = 0;
+    int64_t n_inputs = 0, n_gates = 0, n_mul = 0;
+    int depth = 0;
+    std::vector<LayerRow> lay;            // host copy of the layer table
+    std::vector<int32_t> counts;          // [depth][5] gates per class
+    uint4 *d_rec = nullptr;
+    LayerRow *d_lay = nullptr;
+    void *d_kc = nullptr;
+    // captured run
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraphNode_t gbegin = nullptr;
+    cudaKernelNodeParams gbegin_params{};
+    spdz_plan gplan{};
+    spdz_buf gwires{};
+    int glaunches = 0;
+    cudaStream_t cap_stream = nullptr;
+    // timing
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<cudaEvent_t> lev;
+    std::vector<float> layer_us;
+};
+
+namespace spdz {
+
+static void default_plan(spdz_plan &p) {
+    memset(&p, 0, sizeof p);
+    p.mode = SPDZ_SCHED_FUSED;
+    p.block = 256;
+    p.use_graph = 1;
+}
+
+// Plan choice when the caller passes none (defined by the scheduler).
+int scheduler_plan(spdz_ctx *ctx, spdz_dag *dag, spdz_plan *out);
+
+template <class F>
+static DagArgs<F> base_args(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *w) {
+    using T = typename F::T;
+    DagArgs<F> a{};
+    a.rec = dag->d_rec;
+    a.kc = (const T *)dag->d_kc;
+    a.lay = dag->d_lay;
+    a.wv = (T *)w->val; a.wm = (T *)w->mac; a.ws = w->stride;
+    const spdz_buf *tb[3] = {&ctx->ta, &ctx->tb, &ctx->tc};
+    for (int k = 0; k < 3; ++k) {
+        a.tp[2 * k] = (const T *)tb[k]->val;
+        a.tp[2 * k + 1] = (const T *)tb[k]->mac;
+        a.ts[2 * k] = a.ts[2 * k + 1] = tb[k]->stride;
+    }
+    a.ds = ctx->ds;
+    return a;
+}
+
+static int occupancy(const void *kern, int block, size_t smem = 0) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem) != cudaSuccess) occ = 1;
+    return occ < 1 ? 1 : occ;
+}
+
+// Enqueues every kernel of one run on stream s (begin, layers, checks).
+// Returns the number of launches, or -status.
+template <class F, int NP>
+static int enqueue_run(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, const spdz_buf *w, cudaStream_t s,
+                       uint64_t tri_base, bool layer_events) {
+    int launches = 0;
+    k_run_begin<<<1, 1, 0, s>>>(ctx->ds, tri_base);
+    ++launches;
+    const int block = plan.block > 0 ? plan.block : 256;
+    DagArgs<F> a = base_args<F>(ctx, dag, w);
+    a.spin_ns = (uint64_t)(plan.spin_limit_us ? plan.spin_limit_us : 200000u) * 1000ull;
+    a.extra_arrivals = plan.barrier_extra_arrivals > 0 ? (uint32_t)plan.barrier_extra_arrivals : 0u;
+    cudaStream_t saved = ctx->stream;
+    ctx->stream = s;
+    if (plan.mode == SPDZ_SCHED_PER_LAYER) {
+        auto kern = k_dag_segment<F, NP>;
+        const int cap = occupancy((const void *)kern, block) * ctx->sm_count;
+        for (int l = 0; l < dag->depth; ++l) {
+            if (layer_events) cudaEventRecord(dag->lev[l], s);
+            // one launch for the MUL gates, one for the linear gates
+            const int32_t segs[3] = {dag->lay[l].s[0], dag->lay[l].s[1], dag->lay[l].s[5]};
+            a.l0 = l;
+            for (int c = 0; c < 2; ++c) {
+                a.r0 = segs[c];
+                a.r1 = segs[c + 1];
+                if (a.r1 <= a.r0) continue;
+                int grid = (int)std::min<int64_t>((a.r1 - a.r0 + block - 1) / block, cap);
+                kern<<<grid, block, 0, s>>>(a);
+                ++launches;
+                if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) {
+                    ctx->stream = saved;
+                    return -set_err(ctx, SPDZ_ERR_CUDA, "per-layer launch: %s", cudaGetErrorString(e));
+                }
+            }
+        }
+        if (layer_events) cudaEventRecord(dag->lev[dag->depth], s);
+    } else {
+        auto kern = F::WORDS == 1 ? k_dag_fused<F, NP> : k_dag_fused_wide<F, NP>;
+        const size_t smem = fused_smem<F, NP>(block);
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) {
+                ctx->stream = saved;
+                return -set_err(ctx, SPDZ_ERR_CUDA, "fused kernel shared memory (%zu bytes): %s", smem, cudaGetErrorString(e));
+            }
+        }
+        const int occ = occupancy((const void *)kern, block, smem);
+        const int ng = plan.n_groups > 0 ? plan.n_groups : 1;
+        uint32_t bar_base = 0;
+        int l0 = 0;
+        a.record_ts = layer_events ? 1 : 0;
+        for (int g = 0; g < ng; ++g) {
+            const int l1 = plan.n_groups > 0 ? plan.group_end[g] : dag->depth;
+            int cpsm = plan.group_ctas_per_sm[g] > 0 ? plan.group_ctas_per_sm[g] : plan.ctas_per_sm;
+            if (cpsm <= 0 || cpsm > occ) cpsm = occ;
+            // no more CTAs than the widest layer of the group can use
+            int64_t wmax = 1;
+            for (int l = l0; l < l1; ++l) wmax = std::max<int64_t>(wmax, dag->lay[l].s[5] - dag->lay[l].s[0]);
+            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)cpsm * ctx->sm_count,
+                                                                         (wmax + block - 1) / block));
+            a.l0 = l0;
+            a.l1 = l1;
+            a.bar_base = bar_base;
+            kern<<<grid, block, smem, s>>>(a);
+            ++launches;
+            if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) {
+                ctx->stream = saved;
+                return -set_err(ctx, SPDZ_ERR_CUDA, "fused circuit launch: %s", cudaGetErrorString(e));
+            }
+            const int nbar = (l1 - l0 - 1) + (layer_events ? 1 : 0);
+            bar_base += (uint32_t)grid * (uint32_t)nbar;
+            if (g + 1 < ng && plan.group_flush[g]) {
+                if (int rc = launch_check(ctx, 0)) {
+                    ctx->stream = saved;
+                    return -rc;
+                }
+                ++launches;
+            }
+            l0 = l1;
+        }
+    }
+    int rc = launch_check(ctx, 1);
+    ++launches;
+    ctx->stream = saved;
+    if (rc) return -rc;
+    return launches;
+}
+
+static int enqueue_dispatch(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, const spdz_buf *w, cudaStream_t s,
+                            uint64_t tri_base, bool layer_events) {
+    int r = -SPDZ_ERR_ARG;
+    SPDZ_FIELD_SWITCH(ctx->field, SPDZ_NP_SWITCH(ctx->n, r = (enqueue_run<F, NP>(ctx, dag, plan, w, s, tri_base, layer_events))));
+    return r;
+}
+
+static bool same_plan(const spdz_plan &a, const spdz_plan &b) { return memcmp(&a, &b, sizeof a) == 0; }
+
+static int validate_plan(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &p) {
+    if (p.mode != SPDZ_SCHED_PER_LAYER && p.mode != SPDZ_SCHED_FUSED) return set_err(ctx, SPDZ_ERR_ARG, "plan: bad mode");
+    if (p.block != 0 && (p.block < 32 || p.block > 256 || p.block % 32)) return set_err(ctx, SPDZ_ERR_ARG, "plan: block must be 32..256, a multiple of 32");
+    if (p.n_groups < 0 || p.n_groups > SPDZ_MAX_GROUPS) return set_err(ctx, SPDZ_ERR_ARG, "plan: bad group count");
+    if (p.barrier_extra_arrivals < 0 || p.barrier_extra_arrivals > 1024) return set_err(ctx, SPDZ_ERR_ARG, "plan: bad extra arrivals");
+    int prev = 0;
+    for (int g = 0; g < p.n_groups; ++g) {
+        if (p.group_end[g] <= prev || p.group_end[g] > dag->depth) return set_err(ctx, SPDZ_ERR_ARG, "plan: group ends must increase");
+        prev = p.group_end[g];
+    }
+    if (p.n_groups > 0 && prev != dag->depth) return set_err(ctx, SPDZ_ERR_ARG, "plan: last group must end at depth");
+    return SPDZ_OK;
+}
+
+}  // namespace spdz
+
+extern "C" {
+
+int spdz_dag_create(spdz_ctx *ctx, const spdz_dag_desc *d, spdz_dag **out) {
+    if (!ctx || !d || !out) return set_err(ctx, SPDZ_ERR_ARG, "dag_create: null argument");
+    *out = nullptr;
+    if (d->n_inputs < 0 || d->n_gates < 0 || d->depth < 0 || !d->layer_offsets ||
+        (d->n_gates > 0 && (!d->ops || !d->in0 || !d->in1 || !d->kconst)))
+        return set_err(ctx, SPDZ_ERR_ARG, "dag_create: bad descriptor");
+    if (d->n_gates >= (int64_t)INT32_MAX || d->n_inputs + d->n_gates > (int64_t)UINT32_MAX || d->depth > 1020)
+        return set_err(ctx, SPDZ_ERR_ARG, "dag_create: circuit too large");
+    const int64_t *off = d->layer_offsets;
+    if (off[0] != 0 || off[d->depth] != d->n_gates)
+        return set_err(ctx, SPDZ_ERR_ARG, "dag_create: layer offsets must span the gates");
+    for (int l = 0; l < d->depth; ++l)
+        if (off[l + 1] < off[l]) return set_err(ctx, SPDZ_ERR_ARG, "dag_create: layer offsets decrease");
+    const size_t eb = elem_bytes(ctx->field);
+    spdz_dag *g = new spdz_dag();
+    g->ctx = ctx;
+    g->field = ctx->field;
+    g->n = ctx->n;
+    g->n_inputs = d->n_inputs;
+    g->n_gates = d->n_gates;
+    g->depth = d->depth;
+    std::vector<uint4> rec((size_t)d->n_gates);
+    std::vector<unsigned char> kc((size_t)d->n_gates * eb, 0);
+    g->lay.assign(d->depth, LayerRow{});
+    g->counts.assign((size_t)d->depth * 5, 0);
+    // records per layer in class order MUL, ADD, SUB, CMUL, CADD (gate order
+    // within a class); MUL ranks follow gate order, so a layer's MUL ranks are
+    // consecutive and start at the number of MUL gates in earlier layers
+    static const int cls_op[5] = {SPDZ_OP_MUL, SPDZ_OP_ADD, SPDZ_OP_SUB, SPDZ_OP_CMUL, SPDZ_OP_CADD};
+    size_t pos = 0;
+    int64_t mul_before = 0;
+    for (int l = 0; l < d->depth; ++l) {
+        const uint64_t limit = (uint64_t)d->n_inputs + (uint64_t)off[l];   // wires written before layer l
+        LayerRow &L = g->lay[l];
+        L.mulbase = (int32_t)mul_before;
+        for (int c = 0; c < 5; ++c) {
+            L.s[c] = (int32_t)pos;
+            for (int64_t i = off[l]; i < off[l + 1]; ++i) {
+                const uint8_t op = d->ops[i];
+                if (op > SPDZ_OP_MUL) {
+                    spdz_dag_destroy(g);
+                    return set_err(ctx, SPDZ_ERR_ARG, "dag_create: gate %lld has bad op", (long long)i);
+                }
+                if (op != cls_op[c]) continue;
+                const bool binary = op == SPDZ_OP_ADD || op == SPDZ_OP_SUB || op == SPDZ_OP_MUL;
+                if (d->in0[i] >= limit || (binary && d->in1[i] >= limit)) {
+                    spdz_dag_destroy(g);
+                    return set_err(ctx, SPDZ_ERR_ARG, "dag_create: gate %lld reads a wire not written before its layer",
+                                   (long long)i);
+                }
+                rec[pos] = make_uint4(d->in0[i], binary ? d->in1[i] : d->in0[i], (uint32_t)(d->n_inputs + i), 0u);
+                if (op == SPDZ_OP_CMUL || op == SPDZ_OP_CADD)
+                    memcpy(&kc[pos * eb], (const unsigned char *)d->kconst + (size_t)i * eb, eb);
+                ++pos;
+                g->counts[(size_t)l * 5 + c]++;
+            }
+        }
+        L.s[5] = (int32_t)pos;
+        mul_before += L.s[1] - L.s[0];
+    }
+    g->n_mul = mul_before;
+    int rc = SPDZ_OK;
+    if (cudaMalloc(&g->d_rec, std::max<size_t>(16, rec.size() * 16)) != cudaSuccess ||
+        cudaMalloc(&g->d_lay, std::max<size_t>(32, (size_t)d->depth * sizeof(LayerRow))) != cudaSuccess ||
+        cudaMalloc(&g->d_kc, std::max<size_t>(16, kc.size())) != cudaSuccess) {
+        spdz_dag_destroy(g);
+        return set_err(ctx, SPDZ_ERR_OOM, "dag_create: device allocation failed");
+    }
+    if ((rc = check_cuda(ctx, cudaMemcpy(g->d_rec, rec.data(), rec.size() * 16, cudaMemcpyHostToDevice), "dag upload")) ||
+        (rc = check_cuda(ctx, cudaMemcpy(g->d_lay, g->lay.data(), (size_t)d->depth * sizeof(LayerRow), cudaMemcpyHostToDevice), "dag upload")) ||
+        (rc = check_cuda(ctx, cudaMemcpy(g->d_kc, kc.data(), kc.size(), cudaMemcpyHostToDevice), "dag upload"))) {
+        spdz_dag_destroy(g);
+        return rc;
+    }
+    cudaEventCreate(&g->ev0);
+    cudaEventCreate(&g->ev1);
+    g->lev.resize(d->depth + 1);
+    for (auto &e : g->lev) cudaEventCreate(&e);
+    g->layer_us.assign(d->depth, 0.f);
+    *out = g;
+    return SPDZ_OK;
+}
+
+int spdz_dag_destroy(spdz_dag *g) {
+    if (!g) return SPDZ_OK;
+    cudaDeviceSynchronize();
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    if (g->d_rec) cudaFree(g->d_rec);
+    if (g->d_lay) cudaFree(g->d_lay);
+    if (g->d_kc) cudaFree(g->d_kc);
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+    for (auto &e : g->lev) cudaEventDestroy(e);
+    delete g;
+    return SPDZ_OK;
+}
+
+int spdz_run_dag(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan *plan_in, const spdz_buf *wires, spdz_stats *stats) {
+    if (!ctx || !dag || !wires) return set_err(ctx, SPDZ_ERR_ARG, "run_dag: null argument");
+    if (dag->ctx != ctx && (dag->field != ctx->field || dag->n != ctx->n))
+        return set_err(ctx, SPDZ_ERR_ARG, "run_dag: circuit built for another field or party count");
+    if (!ctx->alpha_loaded) return set_err(ctx, SPDZ_ERR_STATE, "run_dag: preprocessing not loaded");
+    if (ctx->opened != 0) return set_err(ctx, SPDZ_ERR_STATE, "run_dag: values opened since the last check");
+    int rc = validate_buf(ctx, wires, dag->n_inputs + dag->n_gates, "run_dag.wires");
+    if (rc) return rc;
+    if (ctx->tri_total - ctx->tri_cursor < dag->n_mul)
+        return set_err(ctx, SPDZ_ERR_TRIPLES, "run_dag: need %lld triples, %lld left", (long long)dag->n_mul,
+                       (long long)(ctx->tri_total - ctx->tri_cursor));
+    spdz_plan plan;
+    if (plan_in) {
+        plan = *plan_in;
+    } else if (scheduler_plan(ctx, dag, &plan) != SPDZ_OK) {
+        default_plan(plan);
+    }
+    if ((rc = validate_plan(ctx, dag, plan))) return rc;
+    const uint64_t tri_base = (uint64_t)ctx->tri_cursor;
+    const bool layer_events = plan.record_layer_times != 0;
+    if (stats) cudaEventRecord(dag->ev0, ctx->stream);
+    int launches = 0;
+    if (plan.use_graph && !layer_events) {
+        const bool reuse = dag->gexec && same_plan(dag->gplan, plan) && dag->gwires.val == wires->val &&
+                           dag->gwires.mac == wires->mac && dag->gwires.stride == wires->stride;
+        if (!reuse) {
+            if (dag->gexec) { cudaGraphExecDestroy(dag->gexec); dag->gexec = nullptr; }
+            if (dag->graph) { cudaGraphDestroy(dag->graph); dag->graph = nullptr; }
+            if (!dag->cap_stream && (rc = check_cuda(ctx, cudaStreamCreateWithFlags(&dag->cap_stream, cudaStreamNonBlocking), "stream")))
+                return rc;
+            cudaGraph_t graph;
+            if ((rc = check_cuda(ctx, cudaStreamBeginCapture(dag->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture")))
+                return rc;
+            int n = enqueue_dispatch(ctx, dag, plan, wires, dag->cap_stream, tri_base, false);
+            cudaError_t ce = cudaStreamEndCapture(dag->cap_stream, &graph);
+            if (n < 0) return -n;
+            if ((rc = check_cuda(ctx, ce, "end capture"))) return rc;
+            size_t nroots = 1;
+            cudaGraphNode_t root;
+            if ((rc = check_cuda(ctx, cudaGraphGetRootNodes(graph, &root, &nroots), "graph roots")) ||
+                (rc = check_cuda(ctx, cudaGraphKernelNodeGetParams(root, &dag->gbegin_params), "begin node"))) {
+                cudaGraphDestroy(graph);
+                return rc;
+            }
+            rc = check_cuda(ctx, cudaGraphInstantiate(&dag->gexec, graph, 0), "graph instantiate");
+            if (rc) {
+                cudaGraphDestroy(graph);
+                return rc;
+            }
+            dag->graph = graph;   // kept alive: the begin node is updated through it
+            dag->gbegin = root;
+            dag->gplan = plan;
+            dag->gwires = *wires;
+            dag->glaunches = n;
+        }
+        DevState *ds = ctx->ds;
+        uint64_t tb = tri_base;
+        void *args[2] = {&ds, &tb};
+        cudaKernelNodeParams kp = dag->gbegin_params;
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        if ((rc = check_cuda(ctx, cudaGraphExecKernelNodeSetParams(dag->gexec, dag->gbegin, &kp), "update begin node")) ||
+            (rc = check_cuda(ctx, cudaGraphLaunch(dag->gexec, ctx->stream), "graph launch")))
+            return rc;
+        launches = dag->glaunches;
+    } else {
+        int n = enqueue_dispatch(ctx, dag, plan, wires, ctx->stream, tri_base, layer_events);
+        if (n < 0) return -n;
+        launches = n;
+    }
+    ctx->tri_cursor += dag->n_mul;
+    ctx->epoch += 1;
+    if (!stats) return SPDZ_OK;
+    cudaEventRecord(dag->ev1, ctx->stream);
+    if ((rc = check_cuda(ctx, cudaMemcpyAsync(ctx->hres, ctx->ds, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream), "readback")) ||
+        (rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "run sync")))
+        return rc;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, dag->ev0, dag->ev1);
+    stats->device_ms = ms;
+    stats->passed = (int32_t)ctx->hres->res_passed;
+    stats->launches = launches;
+    stats->n_gates = dag->n_gates;
+    stats->n_mul = dag->n_mul;
+    if (layer_events) {
+        if (plan.mode == SPDZ_SCHED_PER_LAYER) {
+            for (int l = 0; l < dag->depth; ++l) cudaEventElapsedTime(&dag->layer_us[l], dag->lev[l], dag->lev[l + 1]);
+            for (auto &v : dag->layer_us) v *= 1000.f;
+        } else {
+            for (int l = 0; l < dag->depth; ++l)
+                dag->layer_us[l] = (float)((double)(ctx->hres->layer_ts[l + 1] - ctx->hres->layer_ts[l]) * 1e-3);
+        }
+    }
+    if (ctx->hres->err_flags & ERR_TIMEOUT) return set_err(ctx, SPDZ_ERR_TIMEOUT, "run_dag: a device barrier wait timed out");
+    if (!stats->passed) return set_err(ctx, SPDZ_ERR_MAC, "run_dag: MAC check failed");
+    return SPDZ_OK;
+}
+
+int spdz_check_result(spdz_ctx *ctx, int *passed, void *sigma_host) {
+    if (!ctx || !passed) return set_err(ctx, SPDZ_ERR_ARG, "check_result: null argument");
+    int rc;
+    if ((rc = check_cuda(ctx, cudaMemcpyAsync(ctx->hres, ctx->ds, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->stream), "readback")) ||
+        (rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "sync")))
+        return rc;
+    *passed = (int)ctx->hres->res_passed;
+    if (sigma_host) {
+        uint64_t *s = (uint64_t *)sigma_host;
+        for (int i = 0; i < ctx->n; ++i) {
+            if (ctx->field == SPDZ_F61) {
+                s[i] = ctx->hres->res_sigma[i][0];
+            } else {
+                s[2 * i] = ctx->hres->res_sigma[i][0];
+                s[2 * i + 1] = ctx->hres->res_sigma[i][1];
+            }
+        }
+    }
+    if (ctx->hres->err_flags & ERR_TIMEOUT) return set_err(ctx, SPDZ_ERR_TIMEOUT, "a device barrier wait timed out");
+    return *passed ? SPDZ_OK : set_err(ctx, SPDZ_ERR_MAC, "MAC check failed");
+}
+
+int spdz_dag_layer_times(const spdz_dag *dag, float *us_out) {
+    if (!dag || !us_out) return SPDZ_ERR_ARG;
+    std::copy(dag->layer_us.begin(), dag->layer_us.end(), us_out);
+    return SPDZ_OK;
+}
+
+int spdz_dag_layer_counts(const spdz_dag *dag, int32_t *counts_out) {
+    if (!dag || !counts_out) return SPDZ_ERR_ARG;
+    std::copy(dag->counts.begin(), dag->counts.end(), counts_out);
+    return SPDZ_OK;
+}
+
+}  // extern "C"

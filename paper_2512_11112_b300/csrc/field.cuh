@@ -1,0 +1,135 @@
+// field.cuh -- exact arithmetic modulo the Mersenne primes 2^61-1 and 2^127-1.
+//
+// Every function takes canonical operands in [0, p) and returns a canonical
+// result.  Products are reduced with the Mersenne identity 2^k == 1 (mod
+// 2^k - 1): the double-width product is split at bit k and the halves are
+// added, followed by one conditional subtract.  Device products use 64-bit
+// mul.lo / mul.hi (lowered to 32-bit IMAD sequences by the compiler).
+#pragma once
+#include <cstdint>
+
+namespace spdz {
+
+// ------------------------------------------------------------------ p61
+struct F61 {
+    using T = uint64_t;
+    static constexpr int WORDS = 1;
+    static constexpr uint64_t P = (1ull << 61) - 1;
+
+    __host__ __device__ __forceinline__ static T zero() { return 0; }
+    __host__ __device__ __forceinline__ static bool is_zero(T a) { return a == 0; }
+    __host__ __device__ __forceinline__ static T add(T a, T b) {
+        T s = a + b;                 // < 2^62
+        return s >= P ? s - P : s;
+    }
+    __host__ __device__ __forceinline__ static T sub(T a, T b) {
+        T d = a - b;
+        return a >= b ? d : d + P;
+    }
+    __host__ __device__ __forceinline__ static T neg(T a) { return a == 0 ? 0 : P - a; }
+    // (hi:lo) < 2^122  ->  (hi:lo) mod p
+    __device__ __forceinline__ static T reduce122(uint64_t lo, uint64_t hi) {
+        // x = (x >> 61) * 2^61 + (x & p), and 2^61 == 1: both halves are <= p
+        // for x <= (p-1)^2, and their sum is < 2p.
+        T s = (lo & P) + ((hi << 3) | (lo >> 61));
+        return s >= P ? s - P : s;
+    }
+    __device__ __forceinline__ static T mul(T a, T b) {
+        return reduce122(a * b, __umul64hi(a, b));
+    }
+    // Field element from a 64-bit PRG word: the top 61 bits, p maps to 0.
+    __host__ __device__ __forceinline__ static T from_draw(uint64_t d) {
+        T v = d >> 3;
+        return v == P ? 0 : v;
+    }
+    __device__ __forceinline__ static T ld(const T *p) { return *p; }
+    __device__ __forceinline__ static void st(T *p, T v) { *p = v; }
+};
+
+// ----------------------------------------------------------------- p127
+struct u128v {
+    uint64_t lo, hi;
+};
+
+struct F127 {
+    using T = u128v;
+    static constexpr int WORDS = 2;
+    static constexpr uint64_t PLO = ~0ull;
+    static constexpr uint64_t PHI = (1ull << 63) - 1;
+
+    __host__ __device__ __forceinline__ static T zero() { return {0, 0}; }
+    __host__ __device__ __forceinline__ static bool is_zero(T a) { return (a.lo | a.hi) == 0; }
+    __host__ __device__ __forceinline__ static bool is_p(T a) { return a.lo == PLO && a.hi == PHI; }
+
+    // s < 2^128 -> s mod p, by one fold of bit 127 and one compare with p.
+    __host__ __device__ __forceinline__ static T fold128(uint64_t lo, uint64_t hi) {
+        uint64_t top = hi >> 63;
+        hi &= PHI;
+        uint64_t nlo = lo + top;
+        hi += (nlo < lo);
+        lo = nlo;
+        // now (hi:lo) <= p
+        if (lo == PLO && hi == PHI) return {0, 0};
+        return {lo, hi};
+    }
+    __host__ __device__ __forceinline__ static T add(T a, T b) {
+        uint64_t lo = a.lo + b.lo;
+        uint64_t hi = a.hi + b.hi + (lo < a.lo);   // < 2^128
+        return fold128(lo, hi);
+    }
+    __host__ __device__ __forceinline__ static T sub(T a, T b) {
+        uint64_t lo = a.lo - b.lo;
+        uint64_t borrow = a.lo < b.lo;
+        uint64_t hi = a.hi - b.hi - borrow;
+        bool neg = (a.hi < b.hi) || (a.hi == b.hi && borrow);
+        if (neg) {                                  // add p (mod 2^128)
+            uint64_t nlo = lo + PLO;
+            hi = hi + PHI + (nlo < lo);
+            lo = nlo;
+        }
+        return {lo, hi};
+    }
+    __host__ __device__ __forceinline__ static T neg(T a) { return sub(zero(), a); }
+
+    // 256-bit product of a, b < 2^127 reduced mod p: x = H*2^127 + L,
+    // 2^127 == 1, so x == H + L with H, L < 2^127.
+    __device__ __forceinline__ static T mul(T a, T b) {
+        uint64_t p00l = a.lo * b.lo, p00h = __umul64hi(a.lo, b.lo);
+        uint64_t p01l = a.lo * b.hi, p01h = __umul64hi(a.lo, b.hi);
+        uint64_t p10l = a.hi * b.lo, p10h = __umul64hi(a.hi, b.lo);
+        uint64_t p11l = a.hi * b.hi, p11h = __umul64hi(a.hi, b.hi);
+        uint64_t w0 = p00l, w1, w2, w3;
+        asm("add.cc.u64  %0, %3, %4;\n\t"
+            "addc.cc.u64 %1, %5, %6;\n\t"
+            "addc.u64    %2, %7, 0;\n\t"
+            : "=l"(w1), "=l"(w2), "=l"(w3)
+            : "l"(p00h), "l"(p01l), "l"(p01h), "l"(p11l), "l"(p11h));
+        asm("add.cc.u64  %0, %0, %3;\n\t"
+            "addc.cc.u64 %1, %1, %4;\n\t"
+            "addc.u64    %2, %2, 0;\n\t"
+            : "+l"(w1), "+l"(w2), "+l"(w3)
+            : "l"(p10l), "l"(p10h));
+        // L = bits 0..126, H = bits 127..253
+        uint64_t Llo = w0, Lhi = w1 & PHI;
+        uint64_t Hlo = (w1 >> 63) | (w2 << 1);
+        uint64_t Hhi = (w2 >> 63) | (w3 << 1);
+        uint64_t lo = Llo + Hlo;
+        uint64_t hi = Lhi + Hhi + (lo < Llo);       // < 2^128
+        return fold128(lo, hi);
+    }
+    // Field element from two PRG words: low word, then the top 63 bits of the
+    // second word as the high word; p maps to 0.
+    __host__ __device__ __forceinline__ static T from_draws(uint64_t d0, uint64_t d1) {
+        T v{d0, d1 >> 1};
+        return is_p(v) ? zero() : v;
+    }
+    __device__ __forceinline__ static T ld(const T *p) {
+        ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(p);
+        return {v.x, v.y};
+    }
+    __device__ __forceinline__ static void st(T *p, T v) {
+        *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(v.lo, v.hi);
+    }
+};
+
+}  // namespace spdz

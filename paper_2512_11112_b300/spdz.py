@@ -1,0 +1,286 @@
+"""Thin ctypes binding of ``include/spdz.h`` (libspdz.so).
+
+Every function here has the name of the C entry point it wraps and only
+marshals arguments: device buffers are torch tensors (int64 storage holding
+the uint64 words of each field element), host buffers are numpy arrays.  A
+non-OK status raises :class:`SpdzError` carrying the code and the library's
+message.  There is no fallback: if the CUDA library is missing the import
+fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspdz.so")
+
+SPDZ_OK, SPDZ_ERR_ARG, SPDZ_ERR_ALIGN, SPDZ_ERR_OOM, SPDZ_ERR_TRIPLES = 0, 1, 2, 3, 4
+SPDZ_ERR_MAC, SPDZ_ERR_TIMEOUT, SPDZ_ERR_CUDA, SPDZ_ERR_STATE = 5, 6, 7, 8
+SPDZ_F61, SPDZ_F127 = 0, 1
+SPDZ_OP_ADD, SPDZ_OP_SUB, SPDZ_OP_CMUL, SPDZ_OP_CADD, SPDZ_OP_MUL = 0, 1, 2, 3, 4
+SPDZ_KIND_ALPHA, SPDZ_KIND_TRIPLE_A, SPDZ_KIND_TRIPLE_B, SPDZ_KIND_TRIPLE_C = 1, 2, 3, 4
+SPDZ_KIND_INPUT, SPDZ_KIND_CHECK = 5, 6
+SPDZ_KIND_MTRIPLE_A, SPDZ_KIND_MTRIPLE_B, SPDZ_KIND_MTRIPLE_C = 7, 8, 9
+SPDZ_MAX_PARTIES = 8
+P61 = (1 << 61) - 1
+P127 = (1 << 127) - 1
+
+
+class SpdzError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"spdz error {code}: {msg}")
+        self.code = code
+
+
+class spdz_buf(C.Structure):
+    _fields_ = [("val", C.c_void_p), ("mac", C.c_void_p), ("stride", C.c_int64)]
+
+
+SPDZ_SCHED_PER_LAYER, SPDZ_SCHED_FUSED = 0, 1
+SPDZ_MAX_GROUPS = 256
+
+
+class spdz_dag_desc(C.Structure):
+    _fields_ = [("n_inputs", C.c_int64), ("n_gates", C.c_int64), ("depth", C.c_int32),
+                ("layer_offsets", C.c_void_p), ("ops", C.c_void_p), ("in0", C.c_void_p),
+                ("in1", C.c_void_p), ("kconst", C.c_void_p)]
+
+
+class spdz_plan(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("block", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("use_graph", C.c_int32), ("n_groups", C.c_int32),
+                ("group_end", C.c_int32 * SPDZ_MAX_GROUPS),
+                ("group_flush", C.c_uint8 * SPDZ_MAX_GROUPS),
+                ("group_ctas_per_sm", C.c_int32 * SPDZ_MAX_GROUPS),
+                ("record_layer_times", C.c_int32), ("spin_limit_us", C.c_uint32),
+                ("barrier_extra_arrivals", C.c_int32)]
+
+
+class spdz_stats(C.Structure):
+    _fields_ = [("device_ms", C.c_double), ("passed", C.c_int32), ("launches", C.c_int32),
+                ("n_gates", C.c_int64), ("n_mul", C.c_int64)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libspdz.so is not built ({LIB_PATH}); run paper_2512_11112_b300/build.py")
+
+lib = C.CDLL(LIB_PATH)
+_vp, _i64, _u64, _int = C.c_void_p, C.c_int64, C.c_uint64, C.c_int
+_bufp = C.POINTER(spdz_buf)
+
+_SIGS = {
+    "spdz_ctx_create": [C.POINTER(_vp), _int, _int, _vp],
+    "spdz_ctx_destroy": [_vp],
+    "spdz_ctx_set_stream": [_vp, _vp],
+    "spdz_deal_alpha": [_vp, _u64, _vp],
+    "spdz_deal_shared": [_vp, _u64, C.c_uint32, _u64, _u64, _i64, _vp, _vp, _bufp, _vp],
+    "spdz_deal_triples": [_vp, _u64, _u64, _i64, _vp, _bufp, _bufp, _bufp],
+    "spdz_load_preproc": [_vp, _vp, _bufp, _bufp, _bufp, _i64],
+    "spdz_triples_left": [_vp, C.POINTER(_i64)],
+    "spdz_linear": [_vp, _int, _bufp, _bufp, _vp, _bufp, _i64],
+    "spdz_mul_batch": [_vp, _bufp, _bufp, _bufp, _i64, _vp],
+    "spdz_open": [_vp, _bufp, _vp, _i64],
+    "spdz_set_check_seed": [_vp, _u64],
+    "spdz_mac_check": [_vp, C.POINTER(_int), _vp],
+    "spdz_check_state": [_vp, C.POINTER(_i64), C.POINTER(_i64)],
+    "spdz_innerprod_batch": [_vp, _bufp, _bufp, _bufp, _i64, _i64],
+    "spdz_field_op": [_vp, _int, _vp, _vp, _vp, _i64],
+    "spdz_dag_create": [_vp, C.POINTER(spdz_dag_desc), C.POINTER(_vp)],
+    "spdz_dag_destroy": [_vp],
+    "spdz_run_dag": [_vp, _vp, C.POINTER(spdz_plan), _bufp, C.POINTER(spdz_stats)],
+    "spdz_check_result": [_vp, C.POINTER(_int), _vp],
+    "spdz_dag_layer_times": [_vp, _vp],
+    "spdz_dag_layer_counts": [_vp, _vp],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = _int
+lib.spdz_last_error.argtypes = [_vp]
+lib.spdz_last_error.restype = C.c_char_p
+
+HEADER_SYMBOLS = sorted(list(_SIGS) + ["spdz_last_error"])
+
+
+def spdz_last_error(ctx) -> str:
+    return lib.spdz_last_error(ctx).decode(errors="replace")
+
+
+def _chk(ctx, rc: int) -> int:
+    if rc != SPDZ_OK:
+        raise SpdzError(rc, spdz_last_error(ctx) if ctx else "")
+    return rc
+
+
+def ptr(t) -> int | None:
+    """Device (or host) address of a torch tensor / numpy array, or None."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def buf(val, mac, stride: int | None = None, offset: int = 0, words: int = 1) -> spdz_buf:
+    """spdz_buf over party-major tensors [n, stride(, 2)], starting at element offset."""
+    if stride is None:
+        stride = val.shape[1]
+    eb = 8 * words
+    return spdz_buf(val.data_ptr() + offset * eb, mac.data_ptr() + offset * eb, stride)
+
+
+def _b(b):
+    return None if b is None else C.byref(b)
+
+
+def spdz_ctx_create(n_parties: int, field: int, stream: int | None = None):
+    h = _vp()
+    rc = lib.spdz_ctx_create(C.byref(h), n_parties, field, stream)
+    if rc != SPDZ_OK:
+        raise SpdzError(rc, "context creation failed")
+    return h
+
+
+def spdz_ctx_destroy(ctx) -> None:
+    lib.spdz_ctx_destroy(ctx)
+
+
+def spdz_ctx_set_stream(ctx, stream: int | None) -> None:
+    _chk(ctx, lib.spdz_ctx_set_stream(ctx, stream))
+
+
+def spdz_deal_alpha(ctx, seed: int, alpha_shares) -> None:
+    _chk(ctx, lib.spdz_deal_alpha(ctx, seed, ptr(alpha_shares)))
+
+
+def spdz_deal_shared(ctx, seed, kind, sub, j0, count, alpha_shares, secret, out: spdz_buf,
+                     secret_out=None) -> None:
+    _chk(ctx, lib.spdz_deal_shared(ctx, seed, kind, sub, j0, count, ptr(alpha_shares), ptr(secret),
+                                   C.byref(out), ptr(secret_out)))
+
+
+def spdz_deal_triples(ctx, seed, j0, count, alpha_shares, a: spdz_buf, b: spdz_buf, c: spdz_buf) -> None:
+    _chk(ctx, lib.spdz_deal_triples(ctx, seed, j0, count, ptr(alpha_shares), C.byref(a), C.byref(b),
+                                    C.byref(c)))
+
+
+def spdz_load_preproc(ctx, alpha_shares, a, b, c, n_triples: int) -> None:
+    _chk(ctx, lib.spdz_load_preproc(ctx, ptr(alpha_shares), _b(a), _b(b), _b(c), n_triples))
+
+
+def spdz_triples_left(ctx) -> int:
+    v = _i64()
+    _chk(ctx, lib.spdz_triples_left(ctx, C.byref(v)))
+    return v.value
+
+
+def spdz_linear(ctx, op: int, x: spdz_buf, y: spdz_buf | None, k_host, z: spdz_buf, N: int) -> None:
+    _chk(ctx, lib.spdz_linear(ctx, op, C.byref(x), _b(y), ptr(k_host), C.byref(z), N))
+
+
+def spdz_mul_batch(ctx, x: spdz_buf, y: spdz_buf, z: spdz_buf, N: int, opened=None) -> None:
+    _chk(ctx, lib.spdz_mul_batch(ctx, C.byref(x), C.byref(y), C.byref(z), N, ptr(opened)))
+
+
+def spdz_open(ctx, x: spdz_buf, out, N: int) -> None:
+    _chk(ctx, lib.spdz_open(ctx, C.byref(x), ptr(out), N))
+
+
+def spdz_set_check_seed(ctx, seed: int) -> None:
+    _chk(ctx, lib.spdz_set_check_seed(ctx, seed))
+
+
+def spdz_mac_check(ctx, sigma_host: np.ndarray | None = None) -> bool:
+    """Runs the check; returns True/False (False is SPDZ_ERR_MAC: abort)."""
+    ok = _int(0)
+    rc = lib.spdz_mac_check(ctx, C.byref(ok), ptr(sigma_host))
+    if rc not in (SPDZ_OK, SPDZ_ERR_MAC):
+        _chk(ctx, rc)
+    return bool(ok.value)
+
+
+def spdz_check_state(ctx):
+    o, e = _i64(), _i64()
+    _chk(ctx, lib.spdz_check_state(ctx, C.byref(o), C.byref(e)))
+    return o.value, e.value
+
+
+def spdz_innerprod_batch(ctx, x: spdz_buf, y: spdz_buf, z: spdz_buf, count: int, length: int) -> None:
+    _chk(ctx, lib.spdz_innerprod_batch(ctx, C.byref(x), C.byref(y), C.byref(z), count, length))
+
+
+def spdz_field_op(ctx, op: int, a, b, out, N: int) -> None:
+    _chk(ctx, lib.spdz_field_op(ctx, op, ptr(a), ptr(b), ptr(out), N))
+
+
+def plan(mode: int = SPDZ_SCHED_FUSED, block: int = 256, ctas_per_sm: int = 0, use_graph: int = 1,
+         groups=None, flush=None, group_ctas=None, record_layer_times: int = 0,
+         spin_limit_us: int = 0, barrier_extra_arrivals: int = 0) -> spdz_plan:
+    """Builds a spdz_plan; groups = list of exclusive end layers."""
+    p = spdz_plan()
+    p.mode, p.block, p.ctas_per_sm, p.use_graph = mode, block, ctas_per_sm, use_graph
+    groups = list(groups or [])
+    p.n_groups = len(groups)
+    for g, e in enumerate(groups):
+        p.group_end[g] = int(e)
+        p.group_flush[g] = int(flush[g]) if flush else 0
+        p.group_ctas_per_sm[g] = int(group_ctas[g]) if group_ctas else 0
+    p.record_layer_times, p.spin_limit_us = record_layer_times, spin_limit_us
+    p.barrier_extra_arrivals = barrier_extra_arrivals
+    return p
+
+
+def spdz_dag_create(ctx, n_inputs: int, layer_offsets, ops, in0, in1, kconst):
+    """Uploads a layered circuit given as numpy arrays (int64 offsets, uint8
+    ops, uint32 operand wires, uint64 constants [G] or [G, 2])."""
+    off = np.ascontiguousarray(layer_offsets, dtype=np.int64)
+    ops = np.ascontiguousarray(ops, dtype=np.uint8)
+    in0 = np.ascontiguousarray(in0, dtype=np.uint32)
+    in1 = np.ascontiguousarray(in1, dtype=np.uint32)
+    k = np.ascontiguousarray(kconst, dtype=np.uint64)
+    d = spdz_dag_desc(n_inputs, ops.size, off.size - 1, off.ctypes.data, ops.ctypes.data,
+                      in0.ctypes.data, in1.ctypes.data, k.ctypes.data)
+    h = _vp()
+    _chk(ctx, lib.spdz_dag_create(ctx, C.byref(d), C.byref(h)))
+    return h
+
+
+def spdz_dag_destroy(dag) -> None:
+    lib.spdz_dag_destroy(dag)
+
+
+def spdz_run_dag(ctx, dag, plan_: spdz_plan | None, wires: spdz_buf, want_stats: bool = True):
+    """Runs the circuit; returns spdz_stats (want_stats) or None (enqueued
+    only).  A failed MAC check returns stats with passed == 0."""
+    st = spdz_stats() if want_stats else None
+    rc = lib.spdz_run_dag(ctx, dag, _b(plan_), C.byref(wires), _b(st))
+    if rc not in (SPDZ_OK, SPDZ_ERR_MAC):
+        _chk(ctx, rc)
+    return st
+
+
+def spdz_check_result(ctx, sigma_host: np.ndarray | None = None) -> bool:
+    ok = _int(0)
+    rc = lib.spdz_check_result(ctx, C.byref(ok), ptr(sigma_host))
+    if rc not in (SPDZ_OK, SPDZ_ERR_MAC):
+        _chk(ctx, rc)
+    return bool(ok.value)
+
+
+def spdz_dag_layer_times(dag, depth: int) -> np.ndarray:
+    out = np.zeros(depth, dtype=np.float32)
+    rc = lib.spdz_dag_layer_times(dag, out.ctypes.data)
+    if rc != SPDZ_OK:
+        raise SpdzError(rc, "layer times")
+    return out
+
+
+def spdz_dag_layer_counts(dag, depth: int) -> np.ndarray:
+    out = np.zeros((depth, 5), dtype=np.int32)
+    rc = lib.spdz_dag_layer_counts(dag, out.ctypes.data)
+    if rc != SPDZ_OK:
+        raise SpdzError(rc, "layer counts")
+    return out

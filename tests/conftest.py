@@ -17,3 +17,15 @@ def pytest_configure(config):
 def have_gpu():
     import torch
     return torch.cuda.is_available()
+
+
+def pytest_sessionstart(session):
+    # build the oracle and, where nvcc exists, the CUDA library (no-ops when
+    # they are up to date); a missing CUDA library makes the GPU tests fail
+    # loudly on import rather than fall back to anything
+    import shutil
+    from oracle import build as ob
+    ob.build()
+    if shutil.which("nvcc"):
+        from paper_2512_11112_b300 import build as pb
+        pb.build()

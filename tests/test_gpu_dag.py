@@ -1,0 +1,226 @@
+"""Layered-circuit runs on the GPU against the CPU oracle: every wire share
+and MAC share, the opened values' check sigma and the verdict, bit-exact, for
+every execution form (per-layer launches, fused persistent kernels with one or
+several groups and partial checks, CUDA-graph replay)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import spdz_workloads as W
+
+pytestmark = pytest.mark.gpu
+
+from gpu_helpers import assert_equal, ctx_for  # noqa: E402
+
+INPUT_SUB = 16
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    global S, SH
+    from paper_2512_11112_b300 import shares as SH  # noqa: F401
+    from paper_2512_11112_b300 import spdz as S  # noqa: F401
+    yield
+    torch.cuda.synchronize()
+
+
+class DeviceCircuit:
+    def __init__(self, dag, n, seed, runs=1, check_seed=7):
+        self.dag, self.n, self.seed = dag, n, seed
+        self.field = SH.field_of(dag.p)
+        self.ctx = ctx_for(n, dag.p)
+        self.alpha_sh = SH.zeros(self.field, n)
+        S.spdz_deal_alpha(self.ctx, seed, self.alpha_sh)
+        self.wires = SH.alloc(self.field, n, dag.n_wires)
+        self.deal_inputs()
+        T = runs * dag.n_mul
+        self.tri = [SH.alloc(self.field, n, max(T, 1)) for _ in range(3)]
+        if T:
+            S.spdz_deal_triples(self.ctx, seed, 0, T, self.alpha_sh, *[t.buf() for t in self.tri])
+        S.spdz_load_preproc(self.ctx, self.alpha_sh, *[t.buf() for t in self.tri], T)
+        S.spdz_set_check_seed(self.ctx, check_seed)
+        self.h = S.spdz_dag_create(self.ctx, dag.n_inputs, dag.layer_offsets, dag.ops, dag.in0,
+                                   dag.in1, dag.kconst)
+
+    def deal_inputs(self):
+        S.spdz_deal_shared(self.ctx, self.seed, S.SPDZ_KIND_INPUT, INPUT_SUB, 0, self.dag.n_inputs,
+                           self.alpha_sh, None, self.wires.buf())
+
+    def run(self, plan):
+        st = S.spdz_run_dag(self.ctx, self.h, plan, self.wires.buf())
+        sig = O.zeros(self.dag.p, self.n)
+        passed = S.spdz_check_result(self.ctx, sig)
+        return st, passed, sig
+
+    def close(self):
+        S.spdz_dag_destroy(self.h)
+        S.spdz_ctx_destroy(self.ctx)
+
+
+def oracle_run(dag, n, seed, run_index=0, check_seed=7):
+    p = dag.p
+    alpha, ash = O.deal_alpha(p, n, seed)
+    iv, im, _ = O.deal_shared(p, n, seed, O.K_INPUT, INPUT_SUB, 0, dag.n_inputs, alpha)
+    wv, wm = O.zeros(p, n, dag.n_wires), O.zeros(p, n, dag.n_wires)
+    wv[:, :dag.n_inputs], wm[:, :dag.n_inputs] = iv, im
+    tri = O.deal_triples(p, n, seed, run_index * dag.n_mul, dag.n_mul, alpha)
+    _, _, log = O.dag_eval(p, dag, wv, wm, tri, ash)
+    ok, sigma, _, _ = O.mac_check(p, [log], ash, check_seed, run_index)
+    return wv, wm, ok, sigma
+
+
+def plans(depth):
+    mid = max(1, depth // 2)
+    out = {
+        "per_layer": S.plan(mode=S.SPDZ_SCHED_PER_LAYER, use_graph=0),
+        "per_layer_graph": S.plan(mode=S.SPDZ_SCHED_PER_LAYER, use_graph=1),
+        "fused": S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=0),
+        "fused_graph": S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=1),
+        "fused_1cta": S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=0, ctas_per_sm=1, block=64),
+    }
+    if depth > 1:
+        out["groups_flush"] = S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=1, groups=[mid, depth],
+                                     flush=[1, 0], group_ctas=[1, 0])
+    if depth > 2:
+        out["every_layer_group"] = S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=0,
+                                          groups=list(range(1, depth + 1)), flush=[1] * depth)
+    return out
+
+
+SMALL = [
+    (O.P61, 3, [30, 17, 1, 25, 9, 300, 2]),
+    (O.P127, 2, [64, 3, 129, 40]),
+    (O.P61, 2, [1]),
+    (O.P127, 3, [5, 1000, 77]),
+]
+
+
+@pytest.mark.parametrize("p,n,widths", SMALL)
+def test_small_circuits_every_plan_matches_oracle(p, n, widths):
+    dag = W.small_dag(seed=len(widths) * 7 + n, p=p, n_inputs=50, widths=widths)
+    n_plans = len(plans(dag.depth))
+    dc = DeviceCircuit(dag, n, seed=3, runs=n_plans)
+    try:
+        for r, (name, plan) in enumerate(plans(dag.depth).items()):
+            st, passed, sig = dc.run(plan)
+            ev, em, ok, osig = oracle_run(dag, n, seed=3, run_index=r)
+            gv, gm = dc.wires.host()
+            assert_equal(gv, ev, f"{name}: wire values")
+            assert_equal(gm, em, f"{name}: wire MACs")
+            assert passed and ok and st.passed == 1, name
+            assert_equal(sig, osig, f"{name}: sigma")
+            assert st.n_mul == dag.n_mul
+    finally:
+        dc.close()
+
+
+def test_benchmark_sized_circuit_matches_oracle():
+    """The 2^20-gate, 32-layer, 3-party p61 circuit: the fused graph run and
+    the per-layer run both equal the oracle on every wire."""
+    dag = W.layered_dag(seed=2)
+    n = 3
+    dc = DeviceCircuit(dag, n, seed=2, runs=2)
+    try:
+        O.set_threads(8)
+        ev, em, ok, osig = oracle_run(dag, n, seed=2, run_index=0)
+        st, passed, sig = dc.run(S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=1))
+        gv, gm = dc.wires.host()
+        assert_equal(gv, ev, "fused values")
+        assert_equal(gm, em, "fused MACs")
+        assert passed and ok
+        assert_equal(sig, osig, "fused sigma")
+        ev1, em1, ok1, osig1 = oracle_run(dag, n, seed=2, run_index=1)
+        st, passed, sig = dc.run(S.plan(mode=S.SPDZ_SCHED_PER_LAYER, use_graph=0))
+        gv, gm = dc.wires.host()
+        assert_equal(gv, ev1, "per-layer values")
+        assert_equal(gm, em1, "per-layer MACs")
+        assert passed and ok1
+        assert_equal(sig, osig1, "per-layer sigma")
+    finally:
+        dc.close()
+
+
+def test_graph_replays_consume_fresh_triples():
+    dag = W.layered_dag(seed=11, total_gates=2**14, depth=12, wmin=64, wmax=4096, n_inputs=1024)
+    n = 3
+    dc = DeviceCircuit(dag, n, seed=5, runs=3)
+    try:
+        plan = S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=1)
+        for r in range(3):
+            st, passed, sig = dc.run(plan)
+            ev, em, ok, osig = oracle_run(dag, n, seed=5, run_index=r)
+            gv, gm = dc.wires.host()
+            assert_equal(gv, ev, f"replay {r}")
+            assert_equal(gm, em, f"replay {r} macs")
+            assert_equal(sig, osig, f"replay {r} sigma")
+        assert S.spdz_triples_left(dc.ctx) == 0
+        with pytest.raises(S.SpdzError) as e:
+            dc.run(plan)
+        assert e.value.code == S.SPDZ_ERR_TRIPLES
+    finally:
+        dc.close()
+
+
+def test_layer_times_recorded():
+    dag = W.layered_dag(seed=4, total_gates=2**15, depth=16, wmin=256, wmax=8192, n_inputs=2048)
+    dc = DeviceCircuit(dag, 3, seed=4, runs=2)
+    try:
+        for mode in (S.SPDZ_SCHED_PER_LAYER, S.SPDZ_SCHED_FUSED):
+            st, passed, _ = dc.run(S.plan(mode=mode, use_graph=0, record_layer_times=1))
+            t = S.spdz_dag_layer_times(dc.h, dag.depth)
+            assert passed and np.all(t > 0) and np.all(t < 1e5)
+        counts = S.spdz_dag_layer_counts(dc.h, dag.depth)
+        assert counts.sum() == dag.n_gates and counts[:, 0].sum() == dag.n_mul
+    finally:
+        dc.close()
+
+
+def test_barrier_timeout_is_a_status_not_a_hang():
+    """Every barrier waits for one arrival that never comes; the bounded wait
+    runs out, the run reports SPDZ_ERR_TIMEOUT, and the context stays usable."""
+    dag = W.small_dag(seed=9, p=O.P61, n_inputs=64, widths=[200, 100, 50])
+    dc = DeviceCircuit(dag, 3, seed=9, runs=2)
+    try:
+        plan = S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=0, spin_limit_us=2000, barrier_extra_arrivals=1)
+        with pytest.raises(S.SpdzError) as e:
+            S.spdz_run_dag(dc.ctx, dc.h, plan, dc.wires.buf())
+        assert e.value.code == S.SPDZ_ERR_TIMEOUT
+        dc.deal_inputs()
+        st, passed, sig = dc.run(S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=0))
+        ev, em, ok, osig = oracle_run(dag, 3, seed=9, run_index=1)
+        assert passed and ok
+        assert_equal(dc.wires.host()[0], ev, "after timeout")
+    finally:
+        dc.close()
+
+
+def test_tampered_input_share_fails_circuit_check():
+    dag = W.small_dag(seed=1, p=O.P61, n_inputs=40, widths=[50, 50, 50])
+    dc = DeviceCircuit(dag, 3, seed=1, runs=1)
+    try:
+        # party 1 shifts its share of the first operand of the first MUL gate
+        g = int(np.flatnonzero(dag.ops == O.OP_MUL)[0])
+        w = int(dag.in0[g])
+        v = O.to_ints(dag.p, SH.to_host(dc.wires.val[1, w:w + 1]))[0]
+        dc.wires.val[1, w] = int(np.array([(v + 1) % dag.p], dtype=np.uint64).view(np.int64)[0])
+        st, passed, sig = dc.run(S.plan(mode=S.SPDZ_SCHED_FUSED))
+        assert not passed and st.passed == 0
+    finally:
+        dc.close()
+
+
+def test_invalid_circuit_rejected():
+    ctx = ctx_for(2, O.P61)
+    try:
+        off = np.array([0, 2], dtype=np.int64)
+        ops = np.array([O.OP_ADD, O.OP_MUL], dtype=np.uint8)
+        in0 = np.array([0, 3], dtype=np.uint32)     # gate 1 reads gate 0's output, same layer
+        in1 = np.array([1, 1], dtype=np.uint32)
+        with pytest.raises(S.SpdzError) as e:
+            S.spdz_dag_create(ctx, 3, off, ops, in0, in1, np.zeros(2, np.uint64))
+        assert e.value.code == S.SPDZ_ERR_ARG
+    finally:
+        S.spdz_ctx_destroy(ctx)
