@@ -266,6 +266,44 @@ int spdz_dag_layer_times(const spdz_dag *dag, float *us_out);
  * is the number of gates of class c (MUL, ADD, SUB, CMUL, CADD). */
 int spdz_dag_layer_counts(const spdz_dag *dag, int32_t *counts_out);
 
+/* ------------------------------------------------ allocation-free batch
+ * No counterpart in the paper: an interface addition for callers that cannot
+ * allocate device memory -- for example a host program whose own memory
+ * manager has reserved the whole device, a plugin that is handed buffers but
+ * no right to allocate, or a loop that cannot afford the device-wide
+ * synchronisation cudaMalloc may cause.  Such callers cannot create a context
+ * (which owns a small device workspace), so this call runs a Beaver batch
+ * (same formulas and results as spdz_mul_batch) and the MAC check of its
+ * opened values (same sigma as spdz_mac_check) without a context and without
+ * allocating: it calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Arguments: n_parties (2..SPDZ_MAX_PARTIES), field, stream (cudaStream_t);
+ * x, y: the N input pairs; a, b, c: the triples to consume, each view starting
+ * at the first triple used (the caller tracks which triples are spent; a
+ * triple must never be used twice); alpha_shares_dev: [n] alpha shares; z:
+ * the N products (written); check_seed and epoch select the check's
+ * coefficients exactly as a context's epoch `epoch` under spdz_set_check_seed
+ * (opened eps_j at index 2j, delta_j at 2j+1); result_dev: [n + 1] elements,
+ * written on the device: sigma_0 .. sigma_{n-1}, then 1 if the check passed and
+ * 0 if it failed (the caller must then abort).  All device pointers are the
+ * caller's; the call only enqueues work on `stream` and does not synchronise.
+ *
+ * Scratch: a fixed 4096-byte array compiled into the library (one per device
+ * that loads it, held until the process exits), sized for the accumulators
+ * of at most SPDZ_MAX_PARTIES parties; more parties are rejected with
+ * SPDZ_ERR_ARG.  The first call on a device looks up the array's device
+ * address (one cudaGetSymbolAddress, with that device current); make that
+ * first call before any stream capture.  Every call shares the array and
+ * clears it at its start: calls that overlap on the GPU (on different
+ * streams, or from several host threads) race and give wrong results, so
+ * order them on one stream.
+ * Errors: SPDZ_ERR_ARG, SPDZ_ERR_ALIGN, SPDZ_ERR_CUDA (no message string: there
+ * is no context). */
+int spdz_mul_check_noalloc(int n_parties, int field, void *stream, const spdz_buf *x,
+                           const spdz_buf *y, const spdz_buf *a, const spdz_buf *b,
+                           const spdz_buf *c, const void *alpha_shares_dev, const spdz_buf *z,
+                           int64_t N, uint64_t check_seed, uint64_t epoch, void *result_dev);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,6 +94,8 @@ _SIGS = {
     "spdz_check_result": [_vp, C.POINTER(_int), _vp],
     "spdz_dag_layer_times": [_vp, _vp],
     "spdz_dag_layer_counts": [_vp, _vp],
+    "spdz_mul_check_noalloc": [_int, _int, _vp, _bufp, _bufp, _bufp, _bufp, _bufp, _vp, _bufp, _i64, _u64,
+                               _u64, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
@@ -284,3 +286,15 @@ def spdz_dag_layer_counts(dag, depth: int) -> np.ndarray:
     if rc != SPDZ_OK:
         raise SpdzError(rc, "layer counts")
     return out
+
+
+def spdz_mul_check_noalloc(n_parties: int, field: int, stream, x: spdz_buf, y: spdz_buf, a: spdz_buf,
+                           b: spdz_buf, c: spdz_buf, alpha_shares, z: spdz_buf, N: int, check_seed: int,
+                           epoch: int, result) -> None:
+    """Allocation-free Beaver batch plus MAC check (no context): result
+    receives [n + 1] elements on the device, sigma_i then the pass flag."""
+    rc = lib.spdz_mul_check_noalloc(n_parties, field, stream, C.byref(x), C.byref(y), C.byref(a),
+                                    C.byref(b), C.byref(c), ptr(alpha_shares), C.byref(z), N,
+                                    check_seed, epoch, ptr(result))
+    if rc != SPDZ_OK:
+        raise SpdzError(rc, "spdz_mul_check_noalloc failed")
