@@ -229,6 +229,11 @@ typedef struct {
     int32_t barrier_extra_arrivals;        /* testing: every barrier also waits for this many
                                               arrivals that never come, so the bounded wait
                                               runs out (SPDZ_ERR_TIMEOUT); 0 in normal use */
+    int32_t group_cluster[SPDZ_MAX_GROUPS];/* fused: 0 = the group runs on the whole grid with
+                                              device barriers; k in 1..16 = the group runs in one
+                                              thread-block cluster of k CTAs with cluster
+                                              barriers (for narrow layers) */
+    int32_t group_block[SPDZ_MAX_GROUPS];  /* per-group threads per CTA; 0 = plan value */
 } spdz_plan;
 
 typedef struct {
@@ -303,6 +308,84 @@ int spdz_mul_check_noalloc(int n_parties, int field, void *stream, const spdz_bu
                            const spdz_buf *y, const spdz_buf *a, const spdz_buf *b,
                            const spdz_buf *c, const void *alpha_shares_dev, const spdz_buf *z,
                            int64_t N, uint64_t check_seed, uint64_t epoch, void *result_dev);
+
+/* ------------------------------------------------------ learned cost model
+ * The scheduler's cost model (the autotuning the paper leaves to future work,
+ * Sec. V-C): a fully connected network n_in -> hidden x hidden_layers -> 1
+ * with ReLU, FP32, trained on the device by the library's own forward,
+ * backward (mean squared error) and Adam kernels.  Parameters are one flat
+ * float array: per layer, W[out][in] row-major then b[out].  Initial weights
+ * are He-uniform from the counter PRG under `seed`, biases zero.
+ * X is [B][n_in] and targets/outputs [B], all float32 on the device. */
+typedef struct spdz_mlp spdz_mlp;
+int spdz_mlp_create(spdz_mlp **out, int32_t n_in, int32_t hidden, int32_t hidden_layers, uint64_t seed,
+                    void *stream);
+int spdz_mlp_destroy(spdz_mlp *m);
+int spdz_mlp_num_params(const spdz_mlp *m, int64_t *count);
+/* Copy the parameters out / in (host float arrays of spdz_mlp_num_params
+ * entries); setting them also resets the Adam state.  Synchronise. */
+int spdz_mlp_get_params(const spdz_mlp *m, float *host_out);
+int spdz_mlp_set_params(spdz_mlp *m, const float *host_in);
+int spdz_mlp_forward(spdz_mlp *m, const float *X_dev, int64_t B, float *Y_dev);
+/* Mean squared error over the batch and its gradient (host outputs, either
+ * may be NULL); synchronises. */
+int spdz_mlp_loss_grad(spdz_mlp *m, const float *X_dev, const float *T_dev, int64_t B, float *loss_host,
+                       float *grad_host);
+/* Adam (beta1 0.9, beta2 0.999, eps 1e-8, step lr) for `epochs` passes over
+ * consecutive mini-batches of `batch` rows; *loss_host (optional) receives the
+ * final mean squared error over all B rows. */
+int spdz_mlp_train(spdz_mlp *m, const float *X_dev, const float *T_dev, int64_t B, int32_t epochs,
+                   int32_t batch, float lr, float *loss_host);
+
+/* ---------------------------------------------------------- scheduling
+ * Execution plans for circuit runs (the slice/batch-size autotuning and
+ * profile-guided selection the paper leaves to future work, Sec. V-C).  A
+ * plan never changes a result bit.  Every call below that runs the circuit
+ * consumes triples from the context's pool (one run's worth per run) and needs
+ * an empty check epoch, like spdz_run_dag.
+ *
+ * Candidate group configurations (index 0..count-1, spdz_sched_num_configs):
+ * whole-grid groups with device barriers at several block sizes and CTAs per
+ * SM, and single-cluster groups (cluster barriers) for narrow layers. */
+typedef struct {
+    double default_ms;     /* measured makespan of the default fused plan */
+    double autotuned_ms;   /* best measured makespan over the uniform configurations */
+    double learned_ms;     /* measured makespan of the learned plan (-1: model not trained) */
+    double predicted_ms;   /* the cost model's prediction for the learned plan (-1: none) */
+    double switch_us;      /* measured cost of one extra layer group */
+    int32_t chosen;        /* plan kept for plan == NULL runs: 0 default, 1 autotuned, 2 learned */
+    int32_t learned_groups;
+    int32_t samples;       /* training samples recorded so far */
+    float train_loss;      /* final training loss (mean squared error of ln microseconds) */
+} spdz_sched_report;
+
+int spdz_sched_num_configs(int32_t *count, int32_t *n_features);
+/* The plan that runs the whole circuit as one group in configuration cfg. */
+int spdz_sched_config_plan(const spdz_dag *dag, int32_t cfg, spdz_plan *out);
+/* Runs the circuit under every configuration (1 + reps runs each) with
+ * per-layer device timing and adds one sample per layer and configuration
+ * (features -> ln of the median layer microseconds) to the context's training
+ * set; the first call also measures the cost of one extra layer group. */
+int spdz_sched_record(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int32_t reps);
+/* The recorded samples (host arrays of count x n_features and count floats,
+ * either may be NULL) and the measured group-switch cost. */
+int spdz_sched_samples(spdz_ctx *ctx, float *X_host, float *Y_host, int64_t *count, double *switch_us);
+/* Trains the context's cost model on the GPU (Adam, mini-batches of 128,
+ * `epochs` passes, step lr) on every recorded sample; seed fixes the initial
+ * weights and the sample order. */
+int spdz_sched_train(spdz_ctx *ctx, int32_t epochs, float lr, uint64_t seed, float *loss_out);
+/* Predicted microseconds of every layer ([depth]) under configuration cfg. */
+int spdz_sched_predict(spdz_ctx *ctx, spdz_dag *dag, int32_t cfg, float *us_out);
+/* The learned plan: group boundaries and per-group configurations that
+ * minimise the predicted makespan (dynamic programming over the layers). */
+int spdz_sched_learned_plan(spdz_ctx *ctx, spdz_dag *dag, spdz_plan *out, double *predicted_ms);
+/* The autotuned plan: the fastest measured uniform configuration. */
+int spdz_sched_autotune(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int32_t reps, spdz_plan *out,
+                        double *best_ms);
+/* Measures the default, autotuned and (if trained) learned plans, keeps the
+ * fastest for this circuit's plan == NULL runs, and reports all three. */
+int spdz_sched_choose(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int32_t reps, spdz_plan *out,
+                      spdz_sched_report *rep);
 
 #ifdef __cplusplus
 }

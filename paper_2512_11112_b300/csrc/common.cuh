@@ -187,8 +187,7 @@ struct spdz_ctx {
     int64_t epoch = 0;
     uint64_t check_seed = 0;
     std::string err;
-    void *scratch = nullptr;             // growable device scratch (circuit runs)
-    size_t scratch_bytes = 0;
+    void *sched = nullptr;               // scheduler state (sched.cu)
 };
 
 namespace spdz {
@@ -201,5 +200,7 @@ int check_launch(spdz_ctx *ctx, const char *what);
 int validate_buf(spdz_ctx *ctx, const spdz_buf *b, int64_t N, const char *name);
 bool buf_vec2_ok(const spdz_buf *b);    // 16-byte aligned rows (p61 vector path)
 int grid_for(spdz_ctx *ctx, const void *kernel, int block, size_t smem, int64_t work_items);
+void sched_destroy(spdz_ctx *ctx);
+void sched_forget(spdz_ctx *ctx, const spdz_dag *dag);
 
 }  // namespace spdz

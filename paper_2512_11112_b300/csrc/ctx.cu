@@ -293,7 +293,7 @@ int spdz_ctx_destroy(spdz_ctx *ctx) {
     else cudaDeviceSynchronize();
     if (ctx->ds) cudaFree(ctx->ds);
     if (ctx->hres) cudaFreeHost(ctx->hres);
-    if (ctx->scratch) cudaFree(ctx->scratch);
+    sched_destroy(ctx);
     delete ctx;
     return SPDZ_OK;
 }

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "beaver.cuh"
+#include "dag.cuh"
 
 namespace spdz {
 
@@ -44,14 +45,6 @@ template <> __device__ __forceinline__ F127::T ld_cs<F127>(const F127::T *p) {
     ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2 *>(p));
     return {v.x, v.y};
 }
-
-// One row per layer: record ranges of the five gate classes (MUL, ADD, SUB,
-// CMUL, CADD, in that order) and the MUL rank of the layer's first MUL gate.
-struct LayerRow {
-    int32_t s[6];        // s[c] = first record of class c, s[5] = end of the layer
-    int32_t mulbase;
-    int32_t pad;
-};
 
 enum : int { C_MUL = 0, C_ADD = 1, C_SUB = 2, C_CMUL = 3, C_CADD = 4 };
 
@@ -284,11 +277,24 @@ __global__ void __launch_bounds__(256) k_dag_segment(DagArgs<F> a) {
     block_accumulate<F, NP + 1>(acc, a.ds->acc);
 }
 
-// Fused form: layers [l0, l1) in one persistent launch.  Thread t owns
-// gates t, t + nthreads, ... of every layer; the operands of its first gate
-// of layer l+1 are staged in shared memory while the CTA waits at the
-// barrier that ends layer l.
-template <class F, int NP>
+// Fused form: layers [l0, l1) in one persistent launch.  Each thread owns
+// gates tid, tid + nthreads, ... of every layer (tid: see below); the
+// operands of its first gate of layer l+1 are staged in shared memory while
+// the CTA waits at the barrier that ends layer l.
+// Cluster-scope barrier between layers of a group run by one thread-block
+// cluster: a hardware barrier (every CTA of a cluster is co-resident, so it
+// cannot wait forever); release/acquire order the wire writes at cluster
+// scope, which covers global memory read through L2.
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ unsigned int cluster_rank() {
+    unsigned int r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+template <class F, int NP, bool CLUSTER>
 __device__ __forceinline__ void dag_fused_body(const DagArgs<F> &a) {
     using T = typename F::T;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -300,9 +306,13 @@ __device__ __forceinline__ void dag_fused_body(const DagArgs<F> &a) {
     for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
 #pragma unroll
     for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
-    const int32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    // 32-gate tiles are dealt round-robin over the CTAs (tile t -> CTA
+    // t mod G, then warp), so even a narrow layer spreads over every SM while
+    // each warp still reads 32 consecutive records and triples
+    const int32_t cta = CLUSTER ? (int32_t)cluster_rank() : (int32_t)blockIdx.x;
+    const int32_t tid = 32 * (cta + gridDim.x * (threadIdx.x >> 5)) + (threadIdx.x & 31);
     const int32_t nthreads = gridDim.x * blockDim.x;
-    const bool stamp = a.record_ts && blockIdx.x == 0 && threadIdx.x == 0;
+    const bool stamp = a.record_ts && cta == 0 && threadIdx.x == 0;
     if (stamp) a.ds->layer_ts[a.l0] = gtimer();
     LayerRow L = load_row(a.lay, a.l0);
     int32_t r = L.s[0] + tid;
@@ -334,8 +344,12 @@ __device__ __forceinline__ void dag_fused_body(const DagArgs<F> &a) {
             if (staged) stage_issue<F, NP>(a, L, r, class_of(L, r), tri_base, st);
         }
         if (l + 1 < a.l1 || a.record_ts) {
-            ++nb;
-            ok = grid_barrier(a.ds, a.bar_base + nb * gridDim.x + a.extra_arrivals, a.spin_ns) && ok;
+            if constexpr (CLUSTER) {
+                cluster_barrier();
+            } else {
+                ++nb;
+                ok = grid_barrier(a.ds, a.bar_base + nb * gridDim.x + a.extra_arrivals, a.spin_ns) && ok;
+            }
             if (stamp) a.ds->layer_ts[l + 1] = gtimer();
         }
     }
@@ -347,11 +361,16 @@ __device__ __forceinline__ void dag_fused_body(const DagArgs<F> &a) {
 // twice as wide, so its kernel is bounded for one CTA per SM instead.
 template <class F, int NP>
 __global__ void __launch_bounds__(256, 2) k_dag_fused(DagArgs<F> a) {
-    dag_fused_body<F, NP>(a);
+    dag_fused_body<F, NP, false>(a);
 }
 template <class F, int NP>
 __global__ void __launch_bounds__(256, 1) k_dag_fused_wide(DagArgs<F> a) {
-    dag_fused_body<F, NP>(a);
+    dag_fused_body<F, NP, false>(a);
+}
+// One cluster of CTAs for a group of narrow layers (grid = the cluster).
+template <class F, int NP>
+__global__ void __launch_bounds__(256, 1) k_dag_cluster(DagArgs<F> a) {
+    dag_fused_body<F, NP, true>(a);
 }
 
 template <class F, int NP> constexpr size_t fused_smem(int block) {
@@ -362,30 +381,6 @@ template <class F, int NP> constexpr size_t fused_smem(int block) {
 
 using namespace spdz;
 
-struct spdz_dag {
-    spdz_ctx *ctx = nullptr;
-    int field = 0, n = 0;
-    int64_t n_inputs = 0, n_gates = 0, n_mul = 0;
-    int depth = 0;
-    std::vector<LayerRow> lay;            // host copy of the layer table
-    std::vector<int32_t> counts;          // [depth][5] gates per class
-    uint4 *d_rec = nullptr;
-    LayerRow *d_lay = nullptr;
-    void *d_kc = nullptr;
-    // captured run
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    cudaGraphNode_t gbegin = nullptr;
-    cudaKernelNodeParams gbegin_params{};
-    spdz_plan gplan{};
-    spdz_buf gwires{};
-    int glaunches = 0;
-    cudaStream_t cap_stream = nullptr;
-    // timing
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    std::vector<cudaEvent_t> lev;
-    std::vector<float> layer_us;
-};
 
 namespace spdz {
 
@@ -461,32 +456,74 @@ static int enqueue_run(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, cons
         if (layer_events) cudaEventRecord(dag->lev[dag->depth], s);
     } else {
         auto kern = F::WORDS == 1 ? k_dag_fused<F, NP> : k_dag_fused_wide<F, NP>;
-        const size_t smem = fused_smem<F, NP>(block);
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) {
-                ctx->stream = saved;
-                return -set_err(ctx, SPDZ_ERR_CUDA, "fused kernel shared memory (%zu bytes): %s", smem, cudaGetErrorString(e));
-            }
-        }
-        const int occ = occupancy((const void *)kern, block, smem);
         const int ng = plan.n_groups > 0 ? plan.n_groups : 1;
         uint32_t bar_base = 0;
         int l0 = 0;
         a.record_ts = layer_events ? 1 : 0;
         for (int g = 0; g < ng; ++g) {
             const int l1 = plan.n_groups > 0 ? plan.group_end[g] : dag->depth;
+            const int ncl = plan.n_groups > 0 ? plan.group_cluster[g] : 0;
+            const int gblock = plan.n_groups > 0 && plan.group_block[g] > 0 ? plan.group_block[g] : block;
+            const size_t smem = fused_smem<F, NP>(gblock);
+            if (ncl > 0) {
+                // the whole group inside one cluster of ncl CTAs
+                auto ck = k_dag_cluster<F, NP>;
+                static bool cattr = false;   // one flag per <F, NP> instantiation
+                if (!cattr) {
+                    cudaFuncSetAttribute((const void *)ck, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+                    cattr = true;
+                }
+                if (smem > 48 * 1024)
+                    cudaFuncSetAttribute((const void *)ck, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                a.l0 = l0;
+                a.l1 = l1;
+                cudaLaunchConfig_t cfg{};
+                cfg.gridDim = dim3((unsigned)ncl);
+                cfg.blockDim = dim3((unsigned)gblock);
+                cfg.dynamicSmemBytes = smem;
+                cfg.stream = s;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = (unsigned)ncl;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                cudaError_t e = cudaLaunchKernelEx(&cfg, ck, a);
+                ++launches;
+                if (e != cudaSuccess) {
+                    ctx->stream = saved;
+                    return -set_err(ctx, SPDZ_ERR_CUDA, "cluster circuit launch (%d CTAs): %s", ncl, cudaGetErrorString(e));
+                }
+                if (g + 1 < ng && plan.group_flush[g]) {
+                    if (int rc = launch_check(ctx, 0)) {
+                        ctx->stream = saved;
+                        return -rc;
+                    }
+                    ++launches;
+                }
+                l0 = l1;
+                continue;
+            }
+            if (smem > 48 * 1024) {
+                cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) {
+                    ctx->stream = saved;
+                    return -set_err(ctx, SPDZ_ERR_CUDA, "fused kernel shared memory (%zu bytes): %s", smem, cudaGetErrorString(e));
+                }
+            }
+            const int occ = occupancy((const void *)kern, gblock, smem);
             int cpsm = plan.group_ctas_per_sm[g] > 0 ? plan.group_ctas_per_sm[g] : plan.ctas_per_sm;
             if (cpsm <= 0 || cpsm > occ) cpsm = occ;
-            // no more CTAs than the widest layer of the group can use
+            // no more CTAs than the widest layer of the group has 32-gate tiles
             int64_t wmax = 1;
             for (int l = l0; l < l1; ++l) wmax = std::max<int64_t>(wmax, dag->lay[l].s[5] - dag->lay[l].s[0]);
             const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)cpsm * ctx->sm_count,
-                                                                         (wmax + block - 1) / block));
+                                                                         (wmax + 31) / 32));
             a.l0 = l0;
             a.l1 = l1;
             a.bar_base = bar_base;
-            kern<<<grid, block, smem, s>>>(a);
+            kern<<<grid, gblock, smem, s>>>(a);
             ++launches;
             if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) {
                 ctx->stream = saved;
@@ -525,6 +562,12 @@ static int validate_plan(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &p) {
     if (p.block != 0 && (p.block < 32 || p.block > 256 || p.block % 32)) return set_err(ctx, SPDZ_ERR_ARG, "plan: block must be 32..256, a multiple of 32");
     if (p.n_groups < 0 || p.n_groups > SPDZ_MAX_GROUPS) return set_err(ctx, SPDZ_ERR_ARG, "plan: bad group count");
     if (p.barrier_extra_arrivals < 0 || p.barrier_extra_arrivals > 1024) return set_err(ctx, SPDZ_ERR_ARG, "plan: bad extra arrivals");
+    for (int g = 0; g < p.n_groups; ++g) {
+        if (p.group_cluster[g] < 0 || p.group_cluster[g] > 16 || (p.group_cluster[g] > 0 && p.mode != SPDZ_SCHED_FUSED))
+            return set_err(ctx, SPDZ_ERR_ARG, "plan: cluster size must be 0..16 (fused mode)");
+        const int b = p.group_block[g];
+        if (b != 0 && (b < 32 || b > 256 || b % 32)) return set_err(ctx, SPDZ_ERR_ARG, "plan: group block must be 32..256, a multiple of 32");
+    }
     int prev = 0;
     for (int g = 0; g < p.n_groups; ++g) {
         if (p.group_end[g] <= prev || p.group_end[g] > dag->depth) return set_err(ctx, SPDZ_ERR_ARG, "plan: group ends must increase");
@@ -624,6 +667,7 @@ int spdz_dag_create(spdz_ctx *ctx, const spdz_dag_desc *d, spdz_dag **out) {
 int spdz_dag_destroy(spdz_dag *g) {
     if (!g) return SPDZ_OK;
     cudaDeviceSynchronize();
+    sched_forget(g->ctx, g);
     if (g->gexec) cudaGraphExecDestroy(g->gexec);
     if (g->graph) cudaGraphDestroy(g->graph);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);

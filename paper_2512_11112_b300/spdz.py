@@ -56,12 +56,20 @@ class spdz_plan(C.Structure):
                 ("group_flush", C.c_uint8 * SPDZ_MAX_GROUPS),
                 ("group_ctas_per_sm", C.c_int32 * SPDZ_MAX_GROUPS),
                 ("record_layer_times", C.c_int32), ("spin_limit_us", C.c_uint32),
-                ("barrier_extra_arrivals", C.c_int32)]
+                ("barrier_extra_arrivals", C.c_int32),
+                ("group_cluster", C.c_int32 * SPDZ_MAX_GROUPS),
+                ("group_block", C.c_int32 * SPDZ_MAX_GROUPS)]
 
 
 class spdz_stats(C.Structure):
     _fields_ = [("device_ms", C.c_double), ("passed", C.c_int32), ("launches", C.c_int32),
                 ("n_gates", C.c_int64), ("n_mul", C.c_int64)]
+
+
+class spdz_sched_report(C.Structure):
+    _fields_ = [("default_ms", C.c_double), ("autotuned_ms", C.c_double), ("learned_ms", C.c_double),
+                ("predicted_ms", C.c_double), ("switch_us", C.c_double), ("chosen", C.c_int32),
+                ("learned_groups", C.c_int32), ("samples", C.c_int32), ("train_loss", C.c_float)]
 
 
 if not os.path.exists(LIB_PATH):
@@ -96,6 +104,23 @@ _SIGS = {
     "spdz_dag_layer_counts": [_vp, _vp],
     "spdz_mul_check_noalloc": [_int, _int, _vp, _bufp, _bufp, _bufp, _bufp, _bufp, _vp, _bufp, _i64, _u64,
                                _u64, _vp],
+    "spdz_mlp_create": [C.POINTER(_vp), C.c_int32, C.c_int32, C.c_int32, _u64, _vp],
+    "spdz_mlp_destroy": [_vp],
+    "spdz_mlp_num_params": [_vp, C.POINTER(_i64)],
+    "spdz_mlp_get_params": [_vp, _vp],
+    "spdz_mlp_set_params": [_vp, _vp],
+    "spdz_mlp_forward": [_vp, _vp, _i64, _vp],
+    "spdz_mlp_loss_grad": [_vp, _vp, _vp, _i64, _vp, _vp],
+    "spdz_mlp_train": [_vp, _vp, _vp, _i64, C.c_int32, C.c_int32, C.c_float, _vp],
+    "spdz_sched_num_configs": [C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
+    "spdz_sched_config_plan": [_vp, C.c_int32, C.POINTER(spdz_plan)],
+    "spdz_sched_record": [_vp, _vp, _bufp, C.c_int32],
+    "spdz_sched_samples": [_vp, _vp, _vp, C.POINTER(_i64), C.POINTER(C.c_double)],
+    "spdz_sched_train": [_vp, C.c_int32, C.c_float, _u64, C.POINTER(C.c_float)],
+    "spdz_sched_predict": [_vp, _vp, C.c_int32, _vp],
+    "spdz_sched_learned_plan": [_vp, _vp, C.POINTER(spdz_plan), C.POINTER(C.c_double)],
+    "spdz_sched_autotune": [_vp, _vp, _bufp, C.c_int32, C.POINTER(spdz_plan), C.POINTER(C.c_double)],
+    "spdz_sched_choose": [_vp, _vp, _bufp, C.c_int32, C.POINTER(spdz_plan), C.POINTER(spdz_sched_report)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
@@ -220,8 +245,10 @@ def spdz_field_op(ctx, op: int, a, b, out, N: int) -> None:
 
 def plan(mode: int = SPDZ_SCHED_FUSED, block: int = 256, ctas_per_sm: int = 0, use_graph: int = 1,
          groups=None, flush=None, group_ctas=None, record_layer_times: int = 0,
-         spin_limit_us: int = 0, barrier_extra_arrivals: int = 0) -> spdz_plan:
-    """Builds a spdz_plan; groups = list of exclusive end layers."""
+         spin_limit_us: int = 0, barrier_extra_arrivals: int = 0, group_cluster=None,
+         group_block=None) -> spdz_plan:
+    """Builds a spdz_plan; groups = list of exclusive end layers;
+    group_cluster[g] > 0 runs group g inside one cluster of that many CTAs."""
     p = spdz_plan()
     p.mode, p.block, p.ctas_per_sm, p.use_graph = mode, block, ctas_per_sm, use_graph
     groups = list(groups or [])
@@ -230,6 +257,8 @@ def plan(mode: int = SPDZ_SCHED_FUSED, block: int = 256, ctas_per_sm: int = 0, u
         p.group_end[g] = int(e)
         p.group_flush[g] = int(flush[g]) if flush else 0
         p.group_ctas_per_sm[g] = int(group_ctas[g]) if group_ctas else 0
+        p.group_cluster[g] = int(group_cluster[g]) if group_cluster else 0
+        p.group_block[g] = int(group_block[g]) if group_block else 0
     p.record_layer_times, p.spin_limit_us = record_layer_times, spin_limit_us
     p.barrier_extra_arrivals = barrier_extra_arrivals
     return p
@@ -298,3 +327,111 @@ def spdz_mul_check_noalloc(n_parties: int, field: int, stream, x: spdz_buf, y: s
                                     check_seed, epoch, ptr(result))
     if rc != SPDZ_OK:
         raise SpdzError(rc, "spdz_mul_check_noalloc failed")
+
+
+# --------------------------------------------------------- cost model (MLP)
+
+def spdz_mlp_create(n_in: int, hidden: int, hidden_layers: int, seed: int, stream=None):
+    h = _vp()
+    rc = lib.spdz_mlp_create(C.byref(h), n_in, hidden, hidden_layers, seed, stream)
+    if rc != SPDZ_OK:
+        raise SpdzError(rc, "mlp create")
+    return h
+
+
+def spdz_mlp_destroy(m) -> None:
+    lib.spdz_mlp_destroy(m)
+
+
+def spdz_mlp_num_params(m) -> int:
+    c = _i64()
+    _chk(None, lib.spdz_mlp_num_params(m, C.byref(c)))
+    return c.value
+
+
+def spdz_mlp_get_params(m) -> np.ndarray:
+    out = np.zeros(spdz_mlp_num_params(m), dtype=np.float32)
+    _chk(None, lib.spdz_mlp_get_params(m, out.ctypes.data))
+    return out
+
+
+def spdz_mlp_set_params(m, params: np.ndarray) -> None:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == spdz_mlp_num_params(m)
+    _chk(None, lib.spdz_mlp_set_params(m, p.ctypes.data))
+
+
+def spdz_mlp_forward(m, X, Y, B: int) -> None:
+    _chk(None, lib.spdz_mlp_forward(m, ptr(X), B, ptr(Y)))
+
+
+def spdz_mlp_loss_grad(m, X, T, B: int):
+    loss = np.zeros(1, dtype=np.float32)
+    grad = np.zeros(spdz_mlp_num_params(m), dtype=np.float32)
+    _chk(None, lib.spdz_mlp_loss_grad(m, ptr(X), ptr(T), B, loss.ctypes.data, grad.ctypes.data))
+    return float(loss[0]), grad
+
+
+def spdz_mlp_train(m, X, T, B: int, epochs: int, batch: int, lr: float) -> float:
+    loss = np.zeros(1, dtype=np.float32)
+    _chk(None, lib.spdz_mlp_train(m, ptr(X), ptr(T), B, epochs, batch, lr, loss.ctypes.data))
+    return float(loss[0])
+
+
+# ------------------------------------------------------------- scheduling
+
+def spdz_sched_num_configs():
+    c, f = C.c_int32(), C.c_int32()
+    lib.spdz_sched_num_configs(C.byref(c), C.byref(f))
+    return c.value, f.value
+
+
+def spdz_sched_config_plan(dag, cfg: int) -> spdz_plan:
+    p = spdz_plan()
+    _chk(None, lib.spdz_sched_config_plan(dag, cfg, C.byref(p)))
+    return p
+
+
+def spdz_sched_record(ctx, dag, wires: spdz_buf, reps: int) -> None:
+    _chk(ctx, lib.spdz_sched_record(ctx, dag, C.byref(wires), reps))
+
+
+def spdz_sched_samples(ctx):
+    n = _i64()
+    sw = C.c_double()
+    _chk(ctx, lib.spdz_sched_samples(ctx, None, None, C.byref(n), C.byref(sw)))
+    _, nf = spdz_sched_num_configs()
+    X = np.zeros((n.value, nf), dtype=np.float32)
+    Y = np.zeros(n.value, dtype=np.float32)
+    _chk(ctx, lib.spdz_sched_samples(ctx, X.ctypes.data, Y.ctypes.data, C.byref(n), C.byref(sw)))
+    return X, Y, sw.value
+
+
+def spdz_sched_train(ctx, epochs: int, lr: float, seed: int = 1) -> float:
+    loss = C.c_float()
+    _chk(ctx, lib.spdz_sched_train(ctx, epochs, lr, seed, C.byref(loss)))
+    return loss.value
+
+
+def spdz_sched_predict(ctx, dag, cfg: int, depth: int) -> np.ndarray:
+    out = np.zeros(depth, dtype=np.float32)
+    _chk(ctx, lib.spdz_sched_predict(ctx, dag, cfg, out.ctypes.data))
+    return out
+
+
+def spdz_sched_learned_plan(ctx, dag):
+    p, ms = spdz_plan(), C.c_double()
+    _chk(ctx, lib.spdz_sched_learned_plan(ctx, dag, C.byref(p), C.byref(ms)))
+    return p, ms.value
+
+
+def spdz_sched_autotune(ctx, dag, wires: spdz_buf, reps: int):
+    p, ms = spdz_plan(), C.c_double()
+    _chk(ctx, lib.spdz_sched_autotune(ctx, dag, C.byref(wires), reps, C.byref(p), C.byref(ms)))
+    return p, ms.value
+
+
+def spdz_sched_choose(ctx, dag, wires: spdz_buf, reps: int):
+    p, r = spdz_plan(), spdz_sched_report()
+    _chk(ctx, lib.spdz_sched_choose(ctx, dag, C.byref(wires), reps, C.byref(p), C.byref(r)))
+    return p, r

@@ -292,3 +292,17 @@ def request_dag(req: Request, n_inputs: int | None = None) -> Dag:
         n_inputs = int(max(1, min(65536, wi[0])))
     return dag_from_widths(req.seed, req.p, n_inputs, wi,
                            {"mul": 60, "add": 15, "sub": 15, "cmul": 10})
+
+
+def calibration_dags(p: int, seed: int = 77, depth: int = 12):
+    """Circuits whose per-layer timings train the scheduler's cost model:
+    uniform widths from 1 to 32k, and mixed circuits with log-uniform widths,
+    each with the benchmark's gate mix."""
+    mix = {"mul": 60, "add": 15, "sub": 15, "cmul": 10}
+    out = []
+    for k, w in enumerate((1, 8, 64, 256, 1024, 4096, 16384, 32768)):
+        out.append(dag_from_widths(seed + k, p, max(64, w), np.full(depth, w), mix))
+    for k in range(3):
+        w = layer_widths(seed + 100 + k, total=depth * 3000, depth=depth, wmin=16, wmax=16384)
+        out.append(dag_from_widths(seed + 200 + k, p, 4096, w, mix))
+    return out

@@ -87,6 +87,12 @@ def plans(depth):
     if depth > 2:
         out["every_layer_group"] = S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=0,
                                           groups=list(range(1, depth + 1)), flush=[1] * depth)
+    out["one_cluster16"] = S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=1, groups=[depth], group_cluster=[16])
+    if depth > 1:
+        out["cluster_then_grid"] = S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=1, groups=[mid, depth],
+                                          group_cluster=[8, 0], flush=[1, 0])
+        out["grid_then_cluster_small_block"] = S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=0, block=64,
+                                                      groups=[mid, depth], group_cluster=[0, 3])
     return out
 
 
