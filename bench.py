@@ -172,12 +172,52 @@ class Circuit:
         self.next_j0 += self.T
 
     def ensure(self, runs=1):
-        if self.S.spdz_triples_left(self.ctx) < runs * self.dag.n_mul:
+        self.ensure_triples(runs * self.dag.n_mul)
+
+    def ensure_triples(self, count):
+        if count > self.T:
+            raise ValueError("triple pool smaller than one request")
+        if self.S.spdz_triples_left(self.ctx) < count:
             self.refill()
 
     def run(self, plan):
         self.S.spdz_run_dag(self.ctx, self.h, plan, self.wires.buf(), want_stats=False)
         self.used += 1
+
+
+def schedule(circ, reps=2, epochs=400):
+    """Offline scheduling phase: per-layer timings of the calibration circuits
+    and of the benchmark circuit itself, recorded by the pipeline, train the
+    cost model on the GPU; spdz_sched_choose then measures the default,
+    autotuned and learned plans and keeps the fastest for plan-less runs."""
+    S, SH = circ.S, circ.SH
+    ncfg, _ = S.spdz_sched_num_configs()
+    record_runs = ncfg * (reps + 1) + 2 * (reps + 1)
+    items = []
+    for d in W.calibration_dags(circ.dag.p):
+        w = SH.alloc(circ.field, N_PARTIES, d.n_wires)
+        S.spdz_deal_shared(circ.ctx, circ.seed, S.SPDZ_KIND_INPUT, INPUT_SUB, 0, d.n_inputs, circ.alpha_sh, None,
+                           w.buf())
+        items.append((d, S.spdz_dag_create(circ.ctx, d.n_inputs, d.layer_offsets, d.ops, d.in0, d.in1, d.kconst), w))
+    items.append((circ.dag, circ.h, circ.wires))
+    t0 = time.perf_counter()
+    for d, h, w in items:
+        circ.ensure_triples(record_runs * d.n_mul)
+        S.spdz_sched_record(circ.ctx, h, w.buf(), reps)
+    loss = S.spdz_sched_train(circ.ctx, epochs=epochs, lr=2e-3, seed=1)
+    circ.ensure_triples((ncfg + 2) * 6 * circ.dag.n_mul)
+    plan, rep = S.spdz_sched_choose(circ.ctx, circ.h, circ.wires.buf(), 5)
+    for d, h, w in items[:-1]:
+        S.spdz_dag_destroy(h)
+    names = {0: "default fused plan", 1: "autotuned uniform plan", 2: "learned plan"}
+    groups = [{"end": int(plan.group_end[g]), "cluster": int(plan.group_cluster[g]),
+               "block": int(plan.group_block[g]), "ctas_per_sm": int(plan.group_ctas_per_sm[g])}
+              for g in range(plan.n_groups)]
+    return {"chosen": names.get(rep.chosen, "?"), "default_ms": rep.default_ms, "autotuned_ms": rep.autotuned_ms,
+            "learned_ms": rep.learned_ms, "learned_predicted_ms": rep.predicted_ms,
+            "learned_groups": rep.learned_groups, "switch_us": rep.switch_us, "samples": rep.samples,
+            "train_loss_ln_us": rep.train_loss, "scheduling_s": round(time.perf_counter() - t0, 2),
+            "chosen_groups": groups}
 
 
 def time_steps(circ, plan, steps, warmup, flush):
@@ -307,8 +347,9 @@ def run_ours(args, rank, world, local_rank):
     e2e_n = min(steps, 5)
     circ = Circuit(dag, seed=2 + 1000 * rank, runs=2 * (steps + warmup) + e2e_n, pool_runs=64)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
-    fused = S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=1)
     per_layer = S.plan(mode=S.SPDZ_SCHED_PER_LAYER, use_graph=0)
+    sched = schedule(circ)
+    scheduled = None          # plan-less runs use the plan the scheduler chose
 
     def barrier():
         if world > 1:
@@ -317,12 +358,12 @@ def run_ours(args, rank, world, local_rank):
 
     barrier()
     with ClockSampler(local_rank) as clk:
-        t_f, ok_f = time_steps(circ, fused, steps, warmup, flush)
+        t_f, ok_f = time_steps(circ, scheduled, steps, warmup, flush)
     barrier()
     t_p, ok_p = time_steps(circ, per_layer, steps, warmup, flush)
     barrier()
     tot_f, tot_p = max_over_ranks([sum(t_f), sum(t_p)], world)
-    e2e_dt, bi, bo, ok_e = e2e_steps(circ, fused, e2e_n)
+    e2e_dt, bi, bo, ok_e = e2e_steps(circ, scheduled, e2e_n)
     (e2e_dt,) = max_over_ranks([e2e_dt], world)
     if rank != 0:
         return
@@ -359,18 +400,21 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": "layered circuit: 2^20 gates, 32 layers, widths log-uniform [1k,64k], "
                                "60% mul / 15% add / 15% sub / 10% const-mul, n=3, p=2^61-1",
                    "gates": dag.n_gates, "beaver_mults": nm, "parties": N_PARTIES, "field": "p61",
-                   "scheduler": "fused persistent kernel + CUDA graph", "l2": "flushed between steps (256 MB write)",
+                   "scheduler": "fused persistent kernels + CUDA graph, plan chosen by the learned scheduler "
+                                "(judged against the autotuned plan)", "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}", "widths": dag.meta["widths"]},
         "mac_check_passed": bool(ok_f and ok_p and ok_e),
         "per_layer": {"value": per_layer_value, "ms_per_step": tot_p / steps,
                       "speedup_of_scheduled_form": tot_p / tot_f},
+        "scheduler": sched,
         "e2e": {"value": world * nm * e2e_n / e2e_dt, "unit": "Beaver mults/s",
                 "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
-        "roofline": {"bound": "hbm", "kernel": "k_dag_fused<F61,3>", "achieved": round(achieved, 1),
+        "roofline": {"bound": "hbm", "kernel": "k_dag_fused<F61,3> (scheduled circuit run)", "achieved": round(achieved, 1),
                      "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
                      "peak_source": peak_src, "algorithmic_bytes_per_launch": bytes_run},
         "beaver_batch_roofline": beaver,
-        "gpu_launches": 3 * steps,   # begin, fused circuit and check kernel per step
+        # per step: the run's begin kernel, one kernel per layer group, the check kernel
+        "gpu_launches": steps * (2 + max(1, len(sched["chosen_groups"]))),
         "clocks": clk.summary(),
     }
     if cpu:
@@ -420,6 +464,92 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def calibrate_both_fields(torch, S, SH, reps=2, epochs=400):
+    """A context whose cost model is trained on per-layer timings of the
+    calibration circuits in both fields (recorded on one context per field)."""
+    ctxs = {}
+    for p in (W.P61, W.P127):
+        field = SH.field_of(p)
+        ctx = S.spdz_ctx_create(N_PARTIES, field, torch.cuda.current_stream().cuda_stream)
+        ash = SH.zeros(field, N_PARTIES)
+        S.spdz_deal_alpha(ctx, 3, ash)
+        dags = W.calibration_dags(p)
+        ncfg, _ = S.spdz_sched_num_configs()
+        T = sum(d.n_mul for d in dags) * (ncfg + 2) * (reps + 1)
+        tri = [SH.alloc(field, N_PARTIES, T) for _ in range(3)]
+        S.spdz_deal_triples(ctx, 3, 0, T, ash, *[t.buf() for t in tri])
+        S.spdz_load_preproc(ctx, ash, *[t.buf() for t in tri], T)
+        for d in dags:
+            w = SH.alloc(field, N_PARTIES, d.n_wires)
+            S.spdz_deal_shared(ctx, 3, S.SPDZ_KIND_INPUT, INPUT_SUB, 0, d.n_inputs, ash, None, w.buf())
+            h = S.spdz_dag_create(ctx, d.n_inputs, d.layer_offsets, d.ops, d.in0, d.in1, d.kconst)
+            S.spdz_sched_record(ctx, h, w.buf(), reps)
+            S.spdz_dag_destroy(h)
+        del tri
+        ctxs[p] = ctx
+    X, Y, _ = S.spdz_sched_samples(ctxs[W.P127])
+    S.spdz_sched_add_samples(ctxs[W.P61], X, Y)
+    loss = S.spdz_sched_train(ctxs[W.P61], epochs=epochs, lr=2e-3, seed=1)
+    S.spdz_ctx_destroy(ctxs[W.P127])
+    return ctxs[W.P61], loss
+
+
+def run_serve(args):
+    """The serving workload: 10,000 circuit requests with Poisson arrivals,
+    gate counts log-uniform in [2^10, 2^22], depths uniform in [4, 64], p61 or
+    p127; a 100 GB budget of shares and triples.  Requests draw their circuit
+    from 64 shapes of that distribution (each request keeps its own seed and
+    arrival time).  The arrival rate puts the offered load at 0.7 of the
+    sequential form's measured capacity."""
+    import torch
+    from paper_2512_11112_b300 import shares as SH
+    from paper_2512_11112_b300 import spdz as S
+    count, nshape = args.serve_requests, 64
+    base = W.serving_requests(seed=5, count=count, rate_per_s=1.0)
+    shapes = [W.request_dag(r) for r in base[:nshape]]
+    fields = [S.SPDZ_F61 if r.p == W.P61 else S.SPDZ_F127 for r in base[:nshape]]
+    mean_gates = float(np.mean([shapes[k % nshape].n_gates for k in range(count)]))
+    model_ctx, loss = calibrate_both_fields(torch, S, SH)
+    budget = 100 << 30
+
+    def trace(rate, n, burst=False):
+        t = [0.0] * n if burst else [r.arrival_s / rate for r in base[:n]]   # base was drawn at rate 1
+        return [(shapes[k % nshape], fields[k % nshape], base[k].seed, t[k], None, None) for k in range(n)]
+
+    srv = S.spdz_serve_create(N_PARTIES, budget, 512, S.SPDZ_SERVE_BATCHED, None, 0, 4096)
+    S.spdz_serve_prepare(srv, list(zip(shapes, fields)))       # deployment: upload the circuits once
+
+    def run(mode, items):
+        S.spdz_serve_set_mode(srv, mode, model_ctx if mode == S.SPDZ_SERVE_LEARNED else None, 4096)
+        res, st = S.spdz_serve_run(srv, items)
+        ok = all(r.passed == 1 for r in res)
+        return {"p50_ms": st.p50_s * 1e3, "p99_ms": st.p99_s * 1e3, "mean_ms": st.mean_s * 1e3,
+                "gates_per_s": st.gates_per_s, "wall_s": st.wall_s, "ticks": st.ticks,
+                "cluster_requests": st.cluster_requests, "dealer_s": st.dealer_s,
+                "peak_gb": st.peak_bytes / 2**30, "max_active": st.max_active, "all_checks_passed": ok,
+                "host_s": {"admit": st.host_admit_s, "tick": st.host_tick_s, "complete": st.host_complete_s,
+                           "idle": st.host_idle_s, "ring_wait": st.host_ring_wait_s}}
+
+    # capacity of the sequential form on a burst of requests
+    cap = run(S.SPDZ_SERVE_SEQUENTIAL, trace(1.0, min(200, count), burst=True))
+    rate = 0.7 * cap["gates_per_s"] / mean_gates
+    items = trace(rate, count)
+    modes = {"sequential": S.SPDZ_SERVE_SEQUENTIAL, "batched": S.SPDZ_SERVE_BATCHED,
+             "heuristic": S.SPDZ_SERVE_HEURISTIC, "learned": S.SPDZ_SERVE_LEARNED}
+    out = {name: run(m, items) for name, m in modes.items()}
+    S.spdz_serve_destroy(srv)
+    S.spdz_ctx_destroy(model_ctx)
+    line = {"metric": "served p99 latency and gates/s, continuous batching + learned scheduler vs sequential",
+            "value": out["learned"]["p99_ms"], "unit": "ms (p99 latency)", "higher_is_better": False,
+            "n_gpus": 1, "data": "synthetic", "dtype": "u64",
+            "config": {"workload": f"{count} circuit requests, Poisson arrivals at {rate:.1f}/s (0.7 x sequential "
+                                   f"capacity), gates log-uniform [2^10, 2^22], depth [4, 64], p61/p127, n=3, "
+                                   f"budget 100 GB, {nshape} circuit shapes", "mean_gates": mean_gates,
+                       "sequential_capacity_gates_per_s": cap["gates_per_s"], "cost_model_loss": loss},
+            "modes": out}
+    print(json.dumps(line), flush=True)
+
+
 def run_profile(args):
     """A few launches of one kernel, for ncu: 'dag' runs the benchmark
     circuit (fused, no graph) `steps` times; 'beaver' runs spdz_mul_batch on
@@ -445,6 +575,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="circuit", choices=["circuit", "serve"],
+                    help="circuit: the benchmark circuit (default); serve: the serving workload")
+    ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--profile", default=None, choices=["dag", "beaver"],
                     help="small run of one kernel for an ncu capture (prints nothing)")
     args = ap.parse_args()
@@ -457,6 +590,9 @@ def main():
         return
     if args.profile:
         run_profile(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
     if world > 1:
         import torch

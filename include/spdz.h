@@ -370,6 +370,9 @@ int spdz_sched_record(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int32
 /* The recorded samples (host arrays of count x n_features and count floats,
  * either may be NULL) and the measured group-switch cost. */
 int spdz_sched_samples(spdz_ctx *ctx, float *X_host, float *Y_host, int64_t *count, double *switch_us);
+/* Adds samples (for example recorded on a context of the other field) to the
+ * context's training set: X_host [count][n_features], Y_host [count]. */
+int spdz_sched_add_samples(spdz_ctx *ctx, const float *X_host, const float *Y_host, int64_t count);
 /* Trains the context's cost model on the GPU (Adam, mini-batches of 128,
  * `epochs` passes, step lr) on every recorded sample; seed fixes the initial
  * weights and the sample order. */
@@ -386,6 +389,102 @@ int spdz_sched_autotune(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int
  * fastest for this circuit's plan == NULL runs, and reports all three. */
 int spdz_sched_choose(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int32_t reps, spdz_plan *out,
                       spdz_sched_report *rep);
+
+/* ------------------------------------------------------------- serving
+ * A serving loop over circuit requests (configuration: n parties, mixed
+ * fields).  Requests arrive at their arrival times (seconds after the start
+ * of spdz_serve_run) and are admitted first come, first served while the
+ * device-memory budget (one arena of budget_bytes for every admitted
+ * request's wire shares and triples) and max_active slots allow; each
+ * admitted request's preprocessing is dealt on the device from its seed
+ * (dealer kinds as spdz_deal_*, circuit inputs with sub 16) on an offline
+ * stream, and its shares stay on the device until it completes.  Execution:
+ *   SPDZ_SERVE_SEQUENTIAL: one request at a time, one launch per layer;
+ *   SPDZ_SERVE_BATCHED: continuous batching -- each tick is one launch per
+ *     field evaluating the next layer of every active request, and requests
+ *     that arrive while others run join at the next tick;
+ *   SPDZ_SERVE_HEURISTIC: as BATCHED, but a request whose widest layer has at
+ *     most cluster_width gates runs all its layers in one cluster launch on a
+ *     side stream, overlapping the ticks;
+ *   SPDZ_SERVE_LEARNED: as HEURISTIC, but the cluster launch is chosen when
+ *     the cost model of model_ctx (trained with spdz_sched_train) predicts it
+ *     faster than ticking.
+ * Every request is its own MAC-check epoch (key of epoch 0 under
+ * check_seed); its result does not depend on the mode or on the other
+ * requests.  Requests that pass the same spdz_dag_desc share one device copy
+ * of its gate records (uploaded at first use, kept until the server is
+ * destroyed, outside the budget).  After an error the server must be
+ * destroyed. */
+enum spdz_serve_mode { SPDZ_SERVE_SEQUENTIAL = 0, SPDZ_SERVE_BATCHED = 1, SPDZ_SERVE_HEURISTIC = 2,
+                       SPDZ_SERVE_LEARNED = 3 };
+
+typedef struct spdz_server spdz_server;
+
+typedef struct {
+    const spdz_dag_desc *dag;   /* host circuit (read at its first admission) */
+    int32_t field;
+    uint64_t seed;              /* dealer seed of the request */
+    double arrival_s;           /* arrival time, seconds after the run starts (non-decreasing) */
+    void *out_val_host;         /* optional: receives the request's wire value shares [n][W] */
+    void *out_mac_host;         /* optional: receives its wire MAC shares [n][W] */
+} spdz_serve_request;
+
+typedef struct {
+    double latency_s;           /* arrival -> result available on the host */
+    double online_s;            /* preprocessing dealt -> result */
+    int32_t passed;             /* MAC-check verdict */
+    int32_t mode;               /* 0 ticks, 1 cluster launch */
+} spdz_serve_result;
+
+typedef struct {
+    double wall_s, gates_per_s, p50_s, p99_s, mean_s;
+    int64_t requests, gates, ticks, cluster_requests;
+    double dealer_s;            /* device time spent dealing preprocessing (offline) */
+    int64_t peak_bytes;         /* peak arena use */
+    int32_t max_active;
+    /* host time of the serving loop by phase (tracing) */
+    double host_admit_s, host_tick_s, host_complete_s, host_idle_s, host_ring_wait_s;
+} spdz_serve_stats;
+
+int spdz_serve_create(spdz_server **out, int n_parties, uint64_t budget_bytes, int32_t max_active, int32_t mode,
+                      spdz_ctx *model_ctx, uint64_t check_seed, int64_t cluster_width);
+/* Builds and uploads circuits ahead of a run (their preparation is then not
+ * part of any request's latency); fields[k] is the field of dags[k]. */
+int spdz_serve_prepare(spdz_server *s, const spdz_dag_desc *const *dags, const int32_t *fields, int64_t count);
+/* Changes the execution mode for the next run (circuits stay prepared). */
+int spdz_serve_set_mode(spdz_server *s, int32_t mode, spdz_ctx *model_ctx, int64_t cluster_width);
+/* Serves the trace (blocking); results [count] may be NULL. */
+int spdz_serve_run(spdz_server *s, const spdz_serve_request *reqs, int64_t count, spdz_serve_result *results,
+                   spdz_serve_stats *stats);
+int spdz_serve_destroy(spdz_server *s);
+
+/* ------------------------------------------------------- matrix products
+ * Secret-shared matrix products with Beaver matrix triples (Sec. III-D.3:
+ * one triple (A, B, C = A*B) per product).  Matrices are row-major inside
+ * each party row of a spdz_buf (element (r, c) of party i at ptr + i*stride +
+ * r*cols + c).  p = 2^61 - 1 only. */
+enum spdz_matmul_path {
+    SPDZ_MATMUL_CUDA_CORE = 0,   /* 64-bit modular multiply-accumulate on the CUDA cores */
+    SPDZ_MATMUL_TENSOR = 1       /* exact small-digit products on the tensor cores */
+};
+/* Dealer for one matrix triple: A (m x k) and B (k x n) uniform (kinds
+ * MTRIPLE_A/B, element index = row-major position, stream sub `sub`),
+ * C = A*B (kind MTRIPLE_C), each shared with MACs under alpha_shares_dev. */
+int spdz_deal_matrix_triple(spdz_ctx *ctx, uint64_t seed, uint64_t sub, int64_t m, int64_t k, int64_t n,
+                            const void *alpha_shares_dev, const spdz_buf *A, const spdz_buf *B, const spdz_buf *C);
+/* Registers one matrix triple (referenced, not copied) for the next
+ * spdz_matmul of the same shape; a triple is consumed by one product. */
+int spdz_load_matrix_preproc(spdz_ctx *ctx, const spdz_buf *A, const spdz_buf *B, const spdz_buf *C, int64_t m,
+                             int64_t k, int64_t n);
+/* Z = X * Y on shares: opens E = X - A and F = Y - B (their MAC shares join
+ * the current check epoch, E row-major first, then F), then
+ *   Z_i = C_i + E*B_i + A_i*F + [i == 0] E*F,
+ *   gamma(Z)_i = gamma(C)_i + E*gamma(B)_i + gamma(A)_i*F + alpha_i E*F.
+ * E_out_dev / F_out_dev (device, m*k and k*n elements, may be NULL) receive
+ * the opened matrices.  SPDZ_ERR_TRIPLES without a registered triple of this
+ * shape. */
+int spdz_matmul(spdz_ctx *ctx, const spdz_buf *X, const spdz_buf *Y, const spdz_buf *Z, int64_t m, int64_t k,
+                int64_t n, int path, void *E_out_dev, void *F_out_dev);
 
 #ifdef __cplusplus
 }

@@ -188,6 +188,7 @@ struct spdz_ctx {
     uint64_t check_seed = 0;
     std::string err;
     void *sched = nullptr;               // scheduler state (sched.cu)
+    void *mat = nullptr;                 // matrix-product state (matmul.cu)
 };
 
 namespace spdz {
@@ -201,6 +202,7 @@ int validate_buf(spdz_ctx *ctx, const spdz_buf *b, int64_t N, const char *name);
 bool buf_vec2_ok(const spdz_buf *b);    // 16-byte aligned rows (p61 vector path)
 int grid_for(spdz_ctx *ctx, const void *kernel, int block, size_t smem, int64_t work_items);
 void sched_destroy(spdz_ctx *ctx);
+void mat_destroy(spdz_ctx *ctx);
 void sched_forget(spdz_ctx *ctx, const spdz_dag *dag);
 
 }  // namespace spdz

@@ -5,7 +5,8 @@
 #include <unordered_map>
 #include <mutex>
 
-#include "common.cuh"
+#include "check.cuh"
+#include "dealer.cuh"
 
 namespace spdz {
 
@@ -96,57 +97,10 @@ __global__ void k_load_alpha(DevState *ds, const typename F::T *alpha, int n) {
     }
 }
 
-// Batched MAC check over the accumulated random linear combination:
-// sigma_i = S_i - alpha_i * A; a check passes iff sum_i sigma_i == 0.  A
-// partial check (final == 0) adds its sigma to the epoch's running sigma and
-// records a failure; the final check publishes the epoch's result and moves
-// to the next epoch's coefficient key.
 template <class F, int NP>
 __global__ void k_check(DevState *ds, int final_check) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    using T = typename F::T;
-    T A = acc_reduce<F>(ds->acc[0]);
-    T tot = F::zero();
-    for (int i = 0; i < NP; ++i) {
-        T S = acc_reduce<F>(ds->acc[1 + i]);
-        T sig = F::sub(S, F::mul(load_alpha<F>(ds, i), A));
-        tot = F::add(tot, sig);
-        T run;
-        if constexpr (F::WORDS == 1) {
-            run = F::add(ds->sig_run[i][0], sig);
-            ds->sig_run[i][0] = run;
-            ds->res_S[i][0] = S;
-            ds->res_S[i][1] = 0;
-        } else {
-            run = F::add(T{ds->sig_run[i][0], ds->sig_run[i][1]}, sig);
-            ds->sig_run[i][0] = run.lo;
-            ds->sig_run[i][1] = run.hi;
-            ds->res_S[i][0] = S.lo;
-            ds->res_S[i][1] = S.hi;
-        }
-    }
-    if constexpr (F::WORDS == 1) {
-        ds->res_A[0] = A;
-        ds->res_A[1] = 0;
-    } else {
-        ds->res_A[0] = A.lo;
-        ds->res_A[1] = A.hi;
-    }
-    if (!F::is_zero(tot)) ds->partial_fail = 1;
-    for (int k = 0; k < NP + 1; ++k)
-        for (int w = 0; w < 4; ++w) ds->acc[k][w] = 0;
-    if (final_check) {
-        for (int i = 0; i < NP; ++i) {
-            ds->res_sigma[i][0] = ds->sig_run[i][0];
-            ds->res_sigma[i][1] = ds->sig_run[i][1];
-            ds->sig_run[i][0] = ds->sig_run[i][1] = 0;
-        }
-        ds->res_passed = ds->partial_fail ? 0u : 1u;
-        ds->res_epoch = (uint32_t)ds->epoch;
-        ds->partial_fail = 0;
-        ds->epoch += 1;
-        ds->key = stream_key(ds->check_seed, stream_id(SPDZ_KIND_CHECK, 0, 0, ds->epoch));
-    }
+    check_epoch<F, NP>(ds, final_check);
 }
 
 // Launches the check kernel on the context's stream (used by spdz_mac_check
@@ -154,100 +108,6 @@ __global__ void k_check(DevState *ds, int final_check) {
 int launch_check(spdz_ctx *ctx, int final_check) {
     SPDZ_FIELD_SWITCH(ctx->field, SPDZ_NP_SWITCH(ctx->n, (k_check<F, NP><<<1, 32, 0, ctx->stream>>>(ctx->ds, final_check))));
     return check_launch(ctx, "check kernel");
-}
-
-// ---------------------------------------------------------------- dealer
-
-template <class F>
-__global__ void k_deal_alpha(uint64_t seed, int n, typename F::T *out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    using T = typename F::T;
-    T alpha = Draw<F>::at(stream_key(seed, stream_id(SPDZ_KIND_ALPHA, ROLE_SECRET, 0, 0)), 0);
-    T sum = F::zero();
-    for (int i = 0; i < n - 1; ++i) {
-        T s = Draw<F>::at(stream_key(seed, stream_id(SPDZ_KIND_ALPHA, ROLE_VAL_SHARE, i, 0)), 0);
-        F::st(out + i, s);
-        sum = F::add(sum, s);
-    }
-    F::st(out + n - 1, F::sub(alpha, sum));
-}
-
-template <int NP> struct ShareKeys {
-    uint64_t secret;
-    uint64_t v[NP];
-    uint64_t m[NP];
-};
-
-template <int NP>
-static ShareKeys<NP> make_keys(uint64_t seed, uint64_t kind, uint64_t sub) {
-    ShareKeys<NP> k{};
-    k.secret = stream_key(seed, stream_id(kind, ROLE_SECRET, 0, sub));
-    for (int i = 0; i < NP - 1; ++i) {
-        k.v[i] = stream_key(seed, stream_id(kind, ROLE_VAL_SHARE, i, sub));
-        k.m[i] = stream_key(seed, stream_id(kind, ROLE_MAC_SHARE, i, sub));
-    }
-    return k;
-}
-
-template <class F, int NP>
-__device__ __forceinline__ void share_store(const ShareKeys<NP> &k, typename F::T alpha, uint64_t gj,
-                                            typename F::T v, typename F::T *val, typename F::T *mac,
-                                            int64_t stride, int64_t j) {
-    using T = typename F::T;
-    T m = F::mul(alpha, v);
-    T sv = F::zero(), sm = F::zero();
-#pragma unroll
-    for (int i = 0; i < NP - 1; ++i) {
-        T vi = Draw<F>::at(k.v[i], gj), mi = Draw<F>::at(k.m[i], gj);
-        F::st(val + i * stride + j, vi);
-        F::st(mac + i * stride + j, mi);
-        sv = F::add(sv, vi);
-        sm = F::add(sm, mi);
-    }
-    F::st(val + (NP - 1) * stride + j, F::sub(v, sv));
-    F::st(mac + (NP - 1) * stride + j, F::sub(m, sm));
-}
-
-template <class F, int NP>
-__device__ __forceinline__ typename F::T sum_alpha(const typename F::T *alpha_sh) {
-    typename F::T a = F::zero();
-#pragma unroll
-    for (int i = 0; i < NP; ++i) a = F::add(a, F::ld(alpha_sh + i));
-    return a;
-}
-
-template <class F, int NP>
-__global__ void k_deal_shared(ShareKeys<NP> keys, uint64_t j0, int64_t count,
-                              const typename F::T *alpha_sh, const typename F::T *secret_in,
-                              typename F::T *val, typename F::T *mac, int64_t stride,
-                              typename F::T *secret_out) {
-    using T = typename F::T;
-    T alpha = sum_alpha<F, NP>(alpha_sh);
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t gj = j0 + (uint64_t)j;
-        T v = secret_in ? F::ld(secret_in + j) : Draw<F>::at(keys.secret, gj);
-        if (secret_out) F::st(secret_out + j, v);
-        share_store<F, NP>(keys, alpha, gj, v, val, mac, stride, j);
-    }
-}
-
-template <class F, int NP>
-__global__ void k_deal_triples(ShareKeys<NP> ka, ShareKeys<NP> kb, ShareKeys<NP> kc, uint64_t j0,
-                               int64_t count, const typename F::T *alpha_sh,
-                               typename F::T *av, typename F::T *am, int64_t as,
-                               typename F::T *bv, typename F::T *bm, int64_t bs,
-                               typename F::T *cv, typename F::T *cm, int64_t cs) {
-    using T = typename F::T;
-    T alpha = sum_alpha<F, NP>(alpha_sh);
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t gj = j0 + (uint64_t)j;
-        T a = Draw<F>::at(ka.secret, gj), b = Draw<F>::at(kb.secret, gj);
-        share_store<F, NP>(ka, alpha, gj, a, av, am, as, j);
-        share_store<F, NP>(kb, alpha, gj, b, bv, bm, bs, j);
-        share_store<F, NP>(kc, alpha, gj, F::mul(a, b), cv, cm, cs, j);
-    }
 }
 
 }  // namespace spdz
@@ -294,6 +154,7 @@ int spdz_ctx_destroy(spdz_ctx *ctx) {
     if (ctx->ds) cudaFree(ctx->ds);
     if (ctx->hres) cudaFreeHost(ctx->hres);
     sched_destroy(ctx);
+    mat_destroy(ctx);
     delete ctx;
     return SPDZ_OK;
 }

@@ -194,6 +194,20 @@ int scheduler_plan(spdz_ctx *ctx, spdz_dag *dag, spdz_plan *out) {
     return SPDZ_ERR_STATE;
 }
 
+// Helpers of the serving loop: per-layer predictions of one configuration
+// for a circuit described only by its layer counts, and the configurations
+// it compares (a single 16-CTA cluster vs the default whole-grid group).
+int sched_predict_config(spdz_ctx *ctx, const spdz_dag *dag, int cfg, std::vector<double> &us) {
+    std::vector<double> pred;
+    if (int rc = predict_layers(ctx, const_cast<spdz_dag *>(dag), pred)) return rc;
+    us.resize((size_t)dag->depth);
+    for (int l = 0; l < dag->depth; ++l) us[(size_t)l] = pred[(size_t)l * NCFG + cfg];
+    return SPDZ_OK;
+}
+int sched_cluster_config() { return 4; }   // {16, 256, 0}
+int sched_grid_config() { return DEFAULT_CFG; }
+double sched_switch_us(spdz_ctx *ctx) { return ctx->sched ? ((Sched *)ctx->sched)->switch_us : 3.0; }
+
 void sched_forget(spdz_ctx *ctx, const spdz_dag *dag) {
     if (ctx && ctx->sched) ((Sched *)ctx->sched)->chosen.erase(dag);
 }
@@ -271,6 +285,14 @@ int spdz_sched_samples(spdz_ctx *ctx, float *X_host, float *Y_host, int64_t *cou
     if (X_host) std::copy(s->X.begin(), s->X.end(), X_host);
     if (Y_host) std::copy(s->Y.begin(), s->Y.end(), Y_host);
     if (switch_us) *switch_us = s->switch_us;
+    return SPDZ_OK;
+}
+
+int spdz_sched_add_samples(spdz_ctx *ctx, const float *X_host, const float *Y_host, int64_t count) {
+    if (!ctx || count < 0 || (count > 0 && (!X_host || !Y_host))) return set_err(ctx, SPDZ_ERR_ARG, "sched_add_samples: bad argument");
+    Sched *s = sched_of(ctx);
+    s->X.insert(s->X.end(), X_host, X_host + count * NFEAT);
+    s->Y.insert(s->Y.end(), Y_host, Y_host + count);
     return SPDZ_OK;
 }
 

@@ -72,6 +72,27 @@ class spdz_sched_report(C.Structure):
                 ("learned_groups", C.c_int32), ("samples", C.c_int32), ("train_loss", C.c_float)]
 
 
+SPDZ_SERVE_SEQUENTIAL, SPDZ_SERVE_BATCHED, SPDZ_SERVE_HEURISTIC, SPDZ_SERVE_LEARNED = 0, 1, 2, 3
+SPDZ_MATMUL_CUDA_CORE, SPDZ_MATMUL_TENSOR = 0, 1
+
+
+class spdz_serve_request(C.Structure):
+    _fields_ = [("dag", C.POINTER(spdz_dag_desc)), ("field", C.c_int32), ("seed", C.c_uint64),
+                ("arrival_s", C.c_double), ("out_val_host", C.c_void_p), ("out_mac_host", C.c_void_p)]
+
+
+class spdz_serve_result(C.Structure):
+    _fields_ = [("latency_s", C.c_double), ("online_s", C.c_double), ("passed", C.c_int32), ("mode", C.c_int32)]
+
+
+class spdz_serve_stats(C.Structure):
+    _fields_ = [("wall_s", C.c_double), ("gates_per_s", C.c_double), ("p50_s", C.c_double), ("p99_s", C.c_double),
+                ("mean_s", C.c_double), ("requests", C.c_int64), ("gates", C.c_int64), ("ticks", C.c_int64),
+                ("cluster_requests", C.c_int64), ("dealer_s", C.c_double), ("peak_bytes", C.c_int64),
+                ("max_active", C.c_int32), ("host_admit_s", C.c_double), ("host_tick_s", C.c_double),
+                ("host_complete_s", C.c_double), ("host_idle_s", C.c_double), ("host_ring_wait_s", C.c_double)]
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libspdz.so is not built ({LIB_PATH}); run paper_2512_11112_b300/build.py")
 
@@ -117,10 +138,20 @@ _SIGS = {
     "spdz_sched_record": [_vp, _vp, _bufp, C.c_int32],
     "spdz_sched_samples": [_vp, _vp, _vp, C.POINTER(_i64), C.POINTER(C.c_double)],
     "spdz_sched_train": [_vp, C.c_int32, C.c_float, _u64, C.POINTER(C.c_float)],
+    "spdz_sched_add_samples": [_vp, _vp, _vp, _i64],
     "spdz_sched_predict": [_vp, _vp, C.c_int32, _vp],
     "spdz_sched_learned_plan": [_vp, _vp, C.POINTER(spdz_plan), C.POINTER(C.c_double)],
     "spdz_sched_autotune": [_vp, _vp, _bufp, C.c_int32, C.POINTER(spdz_plan), C.POINTER(C.c_double)],
     "spdz_sched_choose": [_vp, _vp, _bufp, C.c_int32, C.POINTER(spdz_plan), C.POINTER(spdz_sched_report)],
+    "spdz_serve_create": [C.POINTER(_vp), _int, _u64, C.c_int32, C.c_int32, _vp, _u64, _i64],
+    "spdz_serve_run": [_vp, C.POINTER(spdz_serve_request), _i64, C.POINTER(spdz_serve_result),
+                       C.POINTER(spdz_serve_stats)],
+    "spdz_serve_destroy": [_vp],
+    "spdz_serve_prepare": [_vp, _vp, _vp, _i64],
+    "spdz_deal_matrix_triple": [_vp, _u64, _u64, _i64, _i64, _i64, _vp, _bufp, _bufp, _bufp],
+    "spdz_load_matrix_preproc": [_vp, _bufp, _bufp, _bufp, _i64, _i64, _i64],
+    "spdz_matmul": [_vp, _bufp, _bufp, _bufp, _i64, _i64, _i64, _int, _vp, _vp],
+    "spdz_serve_set_mode": [_vp, C.c_int32, _vp, _i64],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
@@ -407,6 +438,12 @@ def spdz_sched_samples(ctx):
     return X, Y, sw.value
 
 
+def spdz_sched_add_samples(ctx, X: np.ndarray, Y: np.ndarray) -> None:
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    Y = np.ascontiguousarray(Y, dtype=np.float32)
+    _chk(ctx, lib.spdz_sched_add_samples(ctx, X.ctypes.data, Y.ctypes.data, Y.size))
+
+
 def spdz_sched_train(ctx, epochs: int, lr: float, seed: int = 1) -> float:
     loss = C.c_float()
     _chk(ctx, lib.spdz_sched_train(ctx, epochs, lr, seed, C.byref(loss)))
@@ -435,3 +472,91 @@ def spdz_sched_choose(ctx, dag, wires: spdz_buf, reps: int):
     p, r = spdz_plan(), spdz_sched_report()
     _chk(ctx, lib.spdz_sched_choose(ctx, dag, C.byref(wires), reps, C.byref(p), C.byref(r)))
     return p, r
+
+
+# ------------------------------------------------------------------ serving
+
+def spdz_serve_create(n_parties: int, budget_bytes: int, max_active: int, mode: int, model_ctx=None,
+                      check_seed: int = 0, cluster_width: int = 0):
+    h = _vp()
+    rc = lib.spdz_serve_create(C.byref(h), n_parties, budget_bytes, max_active, mode, model_ctx, check_seed,
+                               cluster_width)
+    if rc != SPDZ_OK:
+        raise SpdzError(rc, "serve create")
+    return h
+
+
+def spdz_serve_destroy(server) -> None:
+    lib.spdz_serve_destroy(server)
+
+
+def dag_desc(dag):
+    """spdz_dag_desc over a circuit's numpy arrays (kept alive on the result)."""
+    arrs = (np.ascontiguousarray(dag.layer_offsets, dtype=np.int64), np.ascontiguousarray(dag.ops, dtype=np.uint8),
+            np.ascontiguousarray(dag.in0, dtype=np.uint32), np.ascontiguousarray(dag.in1, dtype=np.uint32),
+            np.ascontiguousarray(dag.kconst, dtype=np.uint64))
+    d = spdz_dag_desc(dag.n_inputs, arrs[1].size, arrs[0].size - 1, *[a.ctypes.data for a in arrs])
+    d._keep = arrs
+    return d
+
+
+_DESC_CACHE = {}
+
+
+def dag_desc_cached(dag):
+    """One spdz_dag_desc per circuit object, so that requests sharing a
+    circuit share the server's uploaded copy of it."""
+    d = _DESC_CACHE.get(id(dag))
+    if d is None or d[0] is not dag:
+        d = (dag, dag_desc(dag))
+        _DESC_CACHE[id(dag)] = d
+    return d[1]
+
+
+def spdz_serve_prepare(server, dags_fields) -> None:
+    descs = [dag_desc_cached(d) for d, _ in dags_fields]
+    arr = (C.c_void_p * max(1, len(descs)))(*[C.addressof(d) for d in descs])
+    fields = np.array([f for _, f in dags_fields], dtype=np.int32)
+    _chk(None, lib.spdz_serve_prepare(server, arr, fields.ctypes.data, len(descs)))
+
+
+def spdz_serve_set_mode(server, mode: int, model_ctx=None, cluster_width: int = 0) -> None:
+    _chk(None, lib.spdz_serve_set_mode(server, mode, model_ctx, cluster_width))
+
+
+def spdz_serve_run(server, requests):
+    """requests: list of (dag, field, seed, arrival_s, out_val or None,
+    out_mac or None).  Returns (results list, spdz_serve_stats)."""
+    n = len(requests)
+    arr = (spdz_serve_request * max(1, n))()
+    keep = []
+    for k, (dag, field, seed, t, ov, om) in enumerate(requests):
+        d = dag_desc_cached(dag)
+        keep.append(d)
+        arr[k].dag = C.pointer(d)
+        arr[k].field, arr[k].seed, arr[k].arrival_s = field, seed, t
+        arr[k].out_val_host = None if ov is None else ov.ctypes.data
+        arr[k].out_mac_host = None if om is None else om.ctypes.data
+    res = (spdz_serve_result * max(1, n))()
+    st = spdz_serve_stats()
+    rc = lib.spdz_serve_run(server, arr, n, res, C.byref(st))
+    if rc != SPDZ_OK:
+        raise SpdzError(rc, "serve run")
+    return [res[k] for k in range(n)], st
+
+
+# --------------------------------------------------------- matrix products
+
+def spdz_deal_matrix_triple(ctx, seed: int, sub: int, m: int, k: int, n: int, alpha_shares, A: spdz_buf,
+                            B: spdz_buf, Cb: spdz_buf) -> None:
+    _chk(ctx, lib.spdz_deal_matrix_triple(ctx, seed, sub, m, k, n, ptr(alpha_shares), C.byref(A), C.byref(B),
+                                          C.byref(Cb)))
+
+
+def spdz_load_matrix_preproc(ctx, A: spdz_buf, B: spdz_buf, Cb: spdz_buf, m: int, k: int, n: int) -> None:
+    _chk(ctx, lib.spdz_load_matrix_preproc(ctx, C.byref(A), C.byref(B), C.byref(Cb), m, k, n))
+
+
+def spdz_matmul(ctx, X: spdz_buf, Y: spdz_buf, Z: spdz_buf, m: int, k: int, n: int, path: int,
+                E_out=None, F_out=None) -> None:
+    _chk(ctx, lib.spdz_matmul(ctx, C.byref(X), C.byref(Y), C.byref(Z), m, k, n, path, ptr(E_out), ptr(F_out)))

@@ -1,0 +1,116 @@
+"""The serving loop: requests of both fields arrive over time, are admitted by
+a device-memory budget and served by continuous batching (and by cluster
+launches for narrow requests).  Every request's shares must equal the CPU
+oracle's evaluation of that request alone -- the same alone and in the mix,
+in every mode."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import spdz_workloads as W
+
+pytestmark = pytest.mark.gpu
+
+from gpu_helpers import assert_equal  # noqa: E402
+
+N = 3
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    global S, SH
+    from paper_2512_11112_b300 import shares as SH  # noqa: F401
+    from paper_2512_11112_b300 import spdz as S  # noqa: F401
+    yield
+
+
+def small_trace(count=10, seed=31, rate=2000.0):
+    reqs = W.serving_requests(seed=seed, count=count, rate_per_s=rate, gmin=64, gmax=3000, dmin=2, dmax=9)
+    return [(r, W.request_dag(r)) for r in reqs]
+
+
+def oracle_wires(req, dag):
+    p = req.p
+    alpha, ash = O.deal_alpha(p, N, req.seed)
+    iv, im, _ = O.deal_shared(p, N, req.seed, O.K_INPUT, 16, 0, dag.n_inputs, alpha)
+    wv, wm = O.zeros(p, N, dag.n_wires), O.zeros(p, N, dag.n_wires)
+    wv[:, :dag.n_inputs], wm[:, :dag.n_inputs] = iv, im
+    tri = O.deal_triples(p, N, req.seed, 0, dag.n_mul, alpha)
+    O.dag_eval(p, dag, wv, wm, tri, ash)
+    return wv, wm
+
+
+def serve(trace, mode, budget=1 << 30, max_active=64, arrivals=True, model_ctx=None, cluster_width=0):
+    server = S.spdz_serve_create(N, budget, max_active, mode, model_ctx, 0, cluster_width)
+    try:
+        outs, items = [], []
+        for r, dag in trace:
+            ov, om = O.zeros(r.p, N, dag.n_wires), O.zeros(r.p, N, dag.n_wires)
+            outs.append((ov, om))
+            field = S.SPDZ_F61 if r.p == O.P61 else S.SPDZ_F127
+            items.append((dag, field, r.seed, r.arrival_s if arrivals else 0.0, ov, om))
+        res, st = S.spdz_serve_run(server, items)
+        return outs, res, st
+    finally:
+        S.spdz_serve_destroy(server)
+
+
+def test_served_results_equal_oracle_alone_and_in_the_mix():
+    trace = small_trace()
+    expect = [oracle_wires(r, d) for r, d in trace]
+    for mode, kw in ((S.SPDZ_SERVE_BATCHED, {}), (S.SPDZ_SERVE_HEURISTIC, {"cluster_width": 1024}),
+                     (S.SPDZ_SERVE_SEQUENTIAL, {})):
+        outs, res, st = serve(trace, mode, **kw)
+        assert st.requests == len(trace) and st.gates == sum(d.n_gates for _, d in trace)
+        for k, ((ov, om), (ev, em)) in enumerate(zip(outs, expect)):
+            assert res[k].passed == 1, (mode, k)
+            assert_equal(ov, ev, f"mode {mode} request {k} values")
+            assert_equal(om, em, f"mode {mode} request {k} MACs")
+        if mode == S.SPDZ_SERVE_HEURISTIC:
+            assert st.cluster_requests > 0
+        if mode == S.SPDZ_SERVE_SEQUENTIAL:
+            assert st.max_active == 1
+    # each request alone gives the same shares as in the mix
+    for k in (0, 3):
+        outs, res, st = serve([trace[k]], S.SPDZ_SERVE_BATCHED, arrivals=False)
+        assert_equal(outs[0][0], expect[k][0], f"request {k} alone")
+
+
+def test_admission_respects_the_memory_budget():
+    trace = small_trace(count=12, seed=8, rate=1e6)     # all arrive at once
+    per = []
+    for r, d in trace:
+        eb = 8 if r.p == O.P61 else 16
+        per.append(2 * N * d.n_wires * eb + 6 * N * max(1, d.n_mul) * eb + 16 * d.n_gates)
+    budget = int(max(per) * 2.5) + (1 << 20)
+    outs, res, st = serve(trace, S.SPDZ_SERVE_BATCHED, budget=budget)
+    assert st.peak_bytes <= budget
+    assert st.max_active < len(trace)                   # the budget held requests back
+    assert all(r.passed == 1 for r in res)
+    expect = oracle_wires(*trace[-1])
+    assert_equal(outs[-1][0], expect[0], "last request values")
+    # a request that can never fit is refused
+    r = W.Request(rid=0, arrival_s=0.0, p=O.P127, gates=200000, depth=4, seed=5)
+    big = [(r, W.request_dag(r))]
+    with pytest.raises(S.SpdzError) as e:
+        serve(big, S.SPDZ_SERVE_BATCHED, budget=1 << 20)
+    assert e.value.code == S.SPDZ_ERR_OOM
+
+
+def test_two_hundred_request_trace_every_result_equals_oracle():
+    """200 requests of both fields (gate counts 2^6..2^12, depths 2..16),
+    arriving over time, served with continuous batching and cluster launches
+    for narrow requests: every request's wires equal the oracle's."""
+    reqs = W.serving_requests(seed=77, count=200, rate_per_s=20000.0, gmin=64, gmax=4096, dmin=2, dmax=16)
+    trace = [(r, W.request_dag(r)) for r in reqs]
+    outs, res, st = serve(trace, S.SPDZ_SERVE_HEURISTIC, max_active=32, cluster_width=512)
+    assert st.requests == 200 and st.cluster_requests > 0 and st.max_active > 1
+    O.set_threads(8)
+    for k, (r, d) in enumerate(trace):
+        ev, em = oracle_wires(r, d)
+        assert res[k].passed == 1, k
+        assert_equal(outs[k][0], ev, f"request {k} values")
+        assert_equal(outs[k][1], em, f"request {k} MACs")
