@@ -550,6 +550,157 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_matmul(args):
+    """Secret-shared matrix product X[2048x2048] * Y[2048x2048], 3 parties,
+    p61, with a Beaver matrix triple: CUDA-core path (and tensor path when
+    available).  The unit of work is a modular multiply-accumulate: 12
+    modular GEMMs of 2048^3 (4 per party) per product."""
+    import torch
+    from paper_2512_11112_b300 import shares as SH
+    from paper_2512_11112_b300 import spdz as S
+    dim, n, f = 2048, N_PARTIES, S.SPDZ_F61
+    ctx = S.spdz_ctx_create(n, f, torch.cuda.current_stream().cuda_stream)
+    ash = SH.zeros(f, n)
+    S.spdz_deal_alpha(ctx, 4, ash)
+    S.spdz_load_preproc(ctx, ash, None, None, None, 0)
+    X, Y, Z = (SH.alloc(f, n, dim * dim) for _ in range(3))
+    S.spdz_deal_shared(ctx, 4, S.SPDZ_KIND_INPUT, 10, 0, dim * dim, ash, None, X.buf())
+    S.spdz_deal_shared(ctx, 4, S.SPDZ_KIND_INPUT, 11, 0, dim * dim, ash, None, Y.buf())
+    A, B, Cm = (SH.alloc(f, n, dim * dim) for _ in range(3))
+    macs = 4 * n * dim ** 3
+    out = {}
+    for name, path in (("cuda_core", S.SPDZ_MATMUL_CUDA_CORE), ("tensor", S.SPDZ_MATMUL_TENSOR)):
+        ts = []
+        try:
+            for rep in range(args.warmup + 3):
+                S.spdz_deal_matrix_triple(ctx, 4, rep, dim, dim, dim, ash, A.buf(), B.buf(), Cm.buf())
+                S.spdz_load_matrix_preproc(ctx, A.buf(), B.buf(), Cm.buf(), dim, dim, dim)
+                torch.cuda.synchronize()
+                e0, e1 = _events(torch)
+                e0.record()
+                S.spdz_matmul(ctx, X.buf(), Y.buf(), Z.buf(), dim, dim, dim, path)
+                e1.record()
+                torch.cuda.synchronize()
+                ok = S.spdz_mac_check(ctx)
+                if rep >= args.warmup:
+                    ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            out[name] = {"ms": ms, "modular_macs_per_s": macs / (ms * 1e-3), "mac_check_passed": ok}
+        except Exception as e:   # noqa: BLE001
+            out[name] = {"unavailable": str(e)}
+    S.spdz_ctx_destroy(ctx)
+    line = {"metric": "secret-shared 2048^3 matrix product time (Beaver matrix triple, 3 parties, p=2^61-1)",
+            "value": min(v.get("ms", 1e9) for v in out.values()), "unit": "ms", "higher_is_better": False,
+            "n_gpus": 1, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "X, Y 2048x2048 uniform, 3 parties, p61, dealer matrix triple",
+                       "modular_macs": macs}, "paths": out}
+    print(json.dumps(line), flush=True)
+
+
+def run_heavy(args):
+    """p127, 3 parties: 2^24 Beaver multiplications, then 16,384 inner products
+    of length 1024, one MAC check over all 2^26 opened values."""
+    import torch
+    from paper_2512_11112_b300 import shares as SH
+    from paper_2512_11112_b300 import spdz as S
+    n, f, N, P, L = N_PARTIES, S.SPDZ_F127, 2**24, 16384, 1024
+    ctx = S.spdz_ctx_create(n, f, torch.cuda.current_stream().cuda_stream)
+    ash = SH.zeros(f, n)
+    S.spdz_deal_alpha(ctx, 3, ash)
+    x, y, z = (SH.alloc(f, n, N) for _ in range(3))
+    S.spdz_deal_shared(ctx, 3, S.SPDZ_KIND_INPUT, 0, 0, N, ash, None, x.buf())
+    S.spdz_deal_shared(ctx, 3, S.SPDZ_KIND_INPUT, 1, 0, N, ash, None, y.buf())
+    zi = SH.alloc(f, n, P)
+    tri = [SH.alloc(f, n, 2 * N) for _ in range(3)]
+    res = {"mul": [], "ip": [], "check": []}
+    for rep in range(args.warmup + 3):
+        S.spdz_deal_triples(ctx, 3, rep * 2 * N, 2 * N, ash, *[t.buf() for t in tri])
+        S.spdz_load_preproc(ctx, ash, *[t.buf() for t in tri], 2 * N)
+        torch.cuda.synchronize()
+        ev = [_events(torch) for _ in range(3)]
+        ev[0][0].record()
+        S.spdz_mul_batch(ctx, x.buf(), y.buf(), z.buf(), N)
+        ev[0][1].record()
+        ev[1][0].record()
+        S.spdz_innerprod_batch(ctx, x.buf(), y.buf(), zi.buf(), P, L)
+        ev[1][1].record()
+        ev[2][0].record()
+        ok = S.spdz_mac_check(ctx)
+        ev[2][1].record()
+        torch.cuda.synchronize()
+        if rep >= args.warmup:
+            for k, key in enumerate(("mul", "ip", "check")):
+                res[key].append(ev[k][0].elapsed_time(ev[k][1]))
+    S.spdz_ctx_destroy(ctx)
+    hbm, src = peaks()
+    mul_ms, ip_ms = statistics.median(res["mul"]), statistics.median(res["ip"])
+    line = {"metric": "Beaver mults/s at n=3, p=2^127-1 (2^24 products) and inner-product terms/s",
+            "value": N / (mul_ms * 1e-3), "unit": "Beaver mults/s", "higher_is_better": True, "n_gpus": 1,
+            "dtype": "u128", "data": "synthetic",
+            "config": {"workload": "2^24 Beaver mults + 16384 inner products of length 1024, n=3, p127, one MAC "
+                                   "check over 2^26 opened values"},
+            "mul_ms": mul_ms, "innerprod_ms": ip_ms, "innerprod_terms_per_s": P * L / (ip_ms * 1e-3),
+            "mac_check_ms": statistics.median(res["check"]), "mac_check_passed": ok,
+            "roofline": {"mul": {"bytes_per_mult": 576, "achieved_gbs": 576 * N / (mul_ms * 1e-3) / 1e9, "peak": hbm,
+                                 "frac": 576 * N / (mul_ms * 1e-3) / 1e9 / hbm},
+                         "innerprod": {"bytes_per_term": 480, "achieved_gbs": 480 * P * L / (ip_ms * 1e-3) / 1e9,
+                                       "peak": hbm, "frac": 480 * P * L / (ip_ms * 1e-3) / 1e9 / hbm}}}
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args):
+    """Plain 2-party p61 Beaver batch of 2^16 products with one MAC check,
+    and the N sweep 2^16 .. 2^26 of the batch kernel against HBM bandwidth."""
+    import torch
+    from paper_2512_11112_b300 import shares as SH
+    from paper_2512_11112_b300 import spdz as S
+    n, f = 2, S.SPDZ_F61
+    hbm, src = peaks()
+    ctx = S.spdz_ctx_create(n, f, torch.cuda.current_stream().cuda_stream)
+    ash = SH.zeros(f, n)
+    S.spdz_deal_alpha(ctx, 1, ash)
+    NMAX = 2**26
+    x, y, z = (SH.alloc(f, n, NMAX) for _ in range(3))
+    S.spdz_deal_shared(ctx, 1, S.SPDZ_KIND_INPUT, 0, 0, NMAX, ash, None, x.buf())
+    S.spdz_deal_shared(ctx, 1, S.SPDZ_KIND_INPUT, 1, 0, NMAX, ash, None, y.buf())
+    tri = [SH.alloc(f, n, NMAX) for _ in range(3)]
+    sweep = {}
+    for lg in (16, 18, 20, 22, 24, 26):
+        N = 2**lg
+        ts_mul, ts_all = [], []
+        for rep in range(args.warmup + 5):
+            S.spdz_deal_triples(ctx, 1, rep * NMAX, N, ash, *[t.buf() for t in tri])
+            S.spdz_load_preproc(ctx, ash, *[t.buf() for t in tri], N)
+            torch.cuda.synchronize()
+            e0, e1 = _events(torch)
+            e0.record()
+            S.spdz_mul_batch(ctx, x.buf(), y.buf(), z.buf(), N)
+            e1.record()
+            ok = S.spdz_mac_check(ctx)   # synchronises
+            e2 = torch.cuda.Event(enable_timing=True)
+            e2.record()
+            torch.cuda.synchronize()
+            if rep >= args.warmup:
+                ts_mul.append(e0.elapsed_time(e1))
+                ts_all.append(e0.elapsed_time(e2))
+        ms = statistics.median(ts_mul)
+        sweep[f"2^{lg}"] = {"mul_us": ms * 1e3, "with_check_us": statistics.median(ts_all) * 1e3,
+                            "mults_per_s": N / (ms * 1e-3), "gbs": 12 * n * 8 * N / (ms * 1e-3) / 1e9,
+                            "frac_of_hbm": 12 * n * 8 * N / (ms * 1e-3) / 1e9 / hbm, "check_passed": ok}
+    S.spdz_ctx_destroy(ctx)
+    line = {"metric": "Beaver mults/s, 2 parties, p=2^61-1, 2^16 products with one MAC check",
+            "value": 2**16 / (sweep["2^16"]["with_check_us"] * 1e-6), "unit": "Beaver mults/s",
+            "higher_is_better": True, "n_gpus": 1, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "2^16 Beaver mults, n=2, p61, batch + MAC check (L2-resident: latency-bound); "
+                                   "sweep to 2^26 for the bandwidth fraction", "bytes_per_mult": 192},
+            "sweep": sweep, "hbm_peak_gbs": hbm, "peak_source": src}
+    print(json.dumps(line), flush=True)
+
+
 def run_profile(args):
     """A few launches of one kernel, for ncu: 'dag' runs the benchmark
     circuit (fused, no graph) `steps` times; 'beaver' runs spdz_mul_batch on
@@ -575,8 +726,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="circuit", choices=["circuit", "serve"],
-                    help="circuit: the benchmark circuit (default); serve: the serving workload")
+    ap.add_argument("--workload", default="circuit", choices=["circuit", "serve", "matmul", "heavy", "batch"],
+                    help="circuit: the benchmark circuit (default); serve, matmul, heavy, batch: the other "
+                         "workloads, one JSON line each")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--profile", default=None, choices=["dag", "beaver"],
                     help="small run of one kernel for an ncu capture (prints nothing)")
@@ -591,8 +743,8 @@ def main():
     if args.profile:
         run_profile(args)
         return
-    if args.workload == "serve":
-        run_serve(args)
+    if args.workload != "circuit":
+        {"serve": run_serve, "matmul": run_matmul, "heavy": run_heavy, "batch": run_batch}[args.workload](args)
         return
     if world > 1:
         import torch

@@ -1,12 +1,473 @@
-// matmul_tc.cu -- the tensor-core path of the secret-shared matrix product.
+// matmul_tc.cu -- the tensor-core path of the secret-shared matrix product
+// (Sec. III-D.3 product Z_i = C_i + [E | A_i] [B'_i ; F], see matmul.cu).
+//
+// Exact modular products on the tensor cores.  Every 61-bit operand x is
+// written in balanced base-2^7 digits, x = sum_d x_d 2^(7d) with
+// x_d in [-64, 64] (9 digits), each exactly representable in bf16.  For two
+// operands the digit-pair products L_a * R_b (tcgen05.mma kind::f16, bf16
+// inputs, f32 accumulation in tensor memory) are integers of magnitude at
+// most 2048 * 64 * 64 = 2^23 for an inner length of 2048, so the f32 sums are
+// exact; the epilogue turns each into a field element and multiplies it by
+// 2^(7(a+b)) mod 2^61 - 1 (a 61-bit rotation), accumulating mod p:
+//   L * R = sum_{a,b} 2^(7(a+b)) (L_a * R_b)   (mod p).
+// (The int8 form kind::i8 is not available on sm_103a.)
+//
+// One CTA computes a 128 x 128 output tile of one job with three roles:
+// warp 0 loads digit-plane tiles with TMA (4-stage ring of 32 KB), warp 1
+// issues the MMAs (and owns the tensor memory), warps 2..9 drain the
+// accumulators; two accumulators in tensor memory let the drain of one
+// digit pair overlap the MMAs of the next.  Every wait is bounded: on
+// timeout the CTA raises an error flag, stops issuing work, waits for what
+// it already issued and frees its tensor memory.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace spdz {
 
+constexpr int TC_DIGITS = 9;
+constexpr int TC_DIGIT_BITS = 7;
+constexpr int TC_TILE = 128;          // output tile edge (M = N = 128)
+constexpr int TC_KB = 64;             // K elements per stage (128 bytes of bf16)
+constexpr int TC_STAGES = 4;
+constexpr int TC_STAGE_BYTES = 2 * TC_TILE * TC_KB * 2;   // A and B tiles
+constexpr int TC_THREADS = 320;       // 10 warps
+constexpr uint32_t TC_TMEM_COLS = 256;
+constexpr unsigned long long TC_WAIT_NS = 1000000000ull;   // bound of one pipeline wait
+
+// ----------------------------------------------------------- digit planes
+// x in [0, p) -> 9 balanced digits (low first): d = x mod 128 taken in
+// [-64, 63], then x = (x - d) / 128; the top digit is in [0, 33].
+__device__ __forceinline__ void balanced_digits(uint64_t x, float (&d)[TC_DIGITS]) {
+    int64_t t = (int64_t)x;
+#pragma unroll
+    for (int j = 0; j < TC_DIGITS - 1; ++j) {
+        int v = (int)(t & 127);
+        if (v >= 64) v -= 128;
+        d[j] = (float)v;
+        t = (t - v) >> 7;
+    }
+    d[TC_DIGITS - 1] = (float)t;
+}
+
+// Row-major rows x cols matrix -> planes [9][rows][colsp] (bf16), columns
+// cols .. colsp-1 zero (colsp: cols rounded up for 16-byte TMA strides).
+__global__ void k_digits_rowmajor(const uint64_t *x, int64_t rows, int64_t cols, int64_t ld, int64_t colsp,
+                                  __nv_bfloat16 *planes) {
+    const int64_t total = rows * colsp;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / colsp, c = e % colsp;
+        float d[TC_DIGITS];
+        if (c < cols) {
+            balanced_digits(x[r * ld + c], d);
+        } else {
+#pragma unroll
+            for (int j = 0; j < TC_DIGITS; ++j) d[j] = 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < TC_DIGITS; ++j) planes[j * total + e] = __float2bfloat16_rn(d[j]);
+    }
+}
+
+// Row-major rows x cols matrix -> transposed planes [9][cols][rowsp]
+// (bf16), columns rows .. rowsp-1 of each output row zero, through 32 x 32
+// shared-memory tiles.
+__global__ void k_digits_transposed(const uint64_t *x, int64_t rows, int64_t cols, int64_t ld, int64_t rowsp,
+                                    __nv_bfloat16 *planes) {
+    __shared__ uint64_t tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t r = r0 + i, c = c0 + threadIdx.x;
+        tile[i][threadIdx.x] = (r < rows && c < cols) ? x[r * ld + c] : 0;
+    }
+    __syncthreads();
+    const int64_t total = cols * rowsp;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t c = c0 + i, r = r0 + threadIdx.x;   // output row c, column r
+        if (c < cols && r < rowsp) {
+            float d[TC_DIGITS];
+            if (r < rows) {
+                balanced_digits(tile[threadIdx.x][i], d);
+            } else {
+#pragma unroll
+                for (int j = 0; j < TC_DIGITS; ++j) d[j] = 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < TC_DIGITS; ++j) planes[j * total + c * rowsp + r] = __float2bfloat16_rn(d[j]);
+        }
+    }
+}
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ unsigned long long tc_now() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done) : "r"(a), "r"(parity) : "memory");
+    return done != 0;
+}
+// Bounded wait for the phase with the given parity to complete: false when
+// the CTA has aborted, or (raising the abort flag) after TC_WAIT_NS.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    const uint32_t a = smem_u32(bar);
+    const unsigned long long t0 = tc_now();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_test(a, parity)) return true;
+        if ((it & 255) == 255) {
+            if (*abort_flag) return false;
+            if (tc_now() - t0 > TC_WAIT_NS) {
+                *abort_flag = 1;
+                return false;
+            }
+        }
+    }
+}
+// Same bound, ignoring the abort flag (draining issued work before exit).
+__device__ __forceinline__ bool mbar_drain(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    const unsigned long long t0 = tc_now();
+    while (!mbar_test(a, parity))
+        if (tc_now() - t0 > TC_WAIT_NS) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle:
+// rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(const void *p) {
+    const uint64_t addr = smem_u32(p);
+    uint64_t d = 0;
+    d |= (addr >> 4) & 0x3FFFull;                 // start address
+    d |= (uint64_t)(16 >> 4) << 16;               // leading-dimension byte offset (unused here)
+    d |= (uint64_t)(1024 >> 4) << 32;             // stride-dimension byte offset
+    d |= 1ull << 46;                              // descriptor version
+    d |= 2ull << 61;                              // 128-byte swizzle
+    return d;
+}
+
+// bf16 x bf16 -> f32, A and B K-major, M = N = 128.
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_TILE >> 3) << 17) |
+                              ((uint32_t)(TC_TILE >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+                 "l"(a), "l"(b), "r"(TC_IDESC), "r"(accumulate)
+                 : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// x * 2^e mod 2^61 - 1 for x < 2^61 - 1: rotate the 61-bit word left by e.
+__device__ __forceinline__ uint64_t rot61(uint64_t x, int e) {
+    return e == 0 ? x : (((x << e) | (x >> (61 - e))) & F61::P);
+}
+
+struct TcJob {
+    const uint64_t *add;   // m x n, leading dimension ldo (may be null)
+    uint64_t *out;
+    int64_t ldo;
+    int64_t m, n, k;       // k: inner length of each of the two segments
+    int *err;              // set to 1 when a wait timed out
+};
+
+// maps: left segment 0, left segment 1, right segment 0, right segment 1
+// (3-D: x = inner index, y = row of the K-major tile, z = digit).
+__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant__ CUtensorMap L0,
+                                                           const __grid_constant__ CUtensorMap L1,
+                                                           const __grid_constant__ CUtensorMap R0,
+                                                           const __grid_constant__ CUtensorMap R1, TcJob job) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], acc_full[2], acc_empty[2], done_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_flag;
+    __shared__ int issued_g, consumed_g;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row0 = (int64_t)blockIdx.y * TC_TILE, col0 = (int64_t)blockIdx.x * TC_TILE;
+    const int kblocks = (int)((job.k + TC_KB - 1) / TC_KB);
+    const int chains = 2 * TC_DIGITS * TC_DIGITS;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 8);        // one arrival per epilogue warp
+        }
+        mbar_init(&done_bar, 1);
+        abort_flag = 0;
+        issued_g = consumed_g = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tmem_base_sh;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- TMA
+        if (lane == 0) {
+            int g = 0;
+            for (int c = 0; c < chains && !abort_flag; ++c) {
+                const int seg = c / (TC_DIGITS * TC_DIGITS), a = (c / TC_DIGITS) % TC_DIGITS, b = c % TC_DIGITS;
+                const CUtensorMap *Lm = seg == 0 ? &L0 : &L1, *Rm = seg == 0 ? &R0 : &R1;
+                for (int kb = 0; kb < kblocks; ++kb, ++g) {
+                    const int s = g % TC_STAGES;
+                    const uint32_t ph = (uint32_t)(g / TC_STAGES) & 1u;
+                    if (g >= TC_STAGES && !mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag)) break;
+                    unsigned char *st = smem + (size_t)s * TC_STAGE_BYTES;
+                    mbar_expect_tx(&full_bar[s], TC_STAGE_BYTES);
+                    tma_load_3d(st, Lm, kb * TC_KB, (int)row0, a, &full_bar[s]);
+                    tma_load_3d(st + TC_STAGE_BYTES / 2, Rm, kb * TC_KB, (int)col0, b, &full_bar[s]);
+                    issued_g = g + 1;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA
+        if (lane == 0) {
+            int g = 0;
+            for (int c = 0; c < chains && !abort_flag; ++c) {
+                const int ab = c & 1;
+                const uint32_t acc_ph = (uint32_t)(c >> 1) & 1u;
+                if (c >= 2 && !mbar_wait(&acc_empty[ab], acc_ph ^ 1u, &abort_flag)) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(ab * TC_TILE);
+                bool ok = true;
+                for (int kb = 0; kb < kblocks; ++kb, ++g) {
+                    const int s = g % TC_STAGES;
+                    const uint32_t ph = (uint32_t)(g / TC_STAGES) & 1u;
+                    if (!mbar_wait(&full_bar[s], ph, &abort_flag)) { ok = false; break; }
+                    consumed_g = g + 1;
+                    tc_fence_after();
+                    const unsigned char *st = smem + (size_t)s * TC_STAGE_BYTES;
+                    const uint64_t da = smem_desc(st), db = smem_desc(st + TC_STAGE_BYTES / 2);
+#pragma unroll
+                    for (int k16 = 0; k16 < TC_KB / 16; ++k16)
+                        mma_bf16(d_tmem, da + (uint64_t)(k16 * 2), db + (uint64_t)(k16 * 2), (kb | k16) != 0);
+                    mma_commit(&empty_bar[s]);     // frees the stage once these MMAs have read it
+                }
+                if (!ok) break;
+                mma_commit(&acc_full[ab]);         // the accumulator is complete
+            }
+            // every MMA issued above has completed once this commit arrives
+            mma_commit(&done_bar);
+            if (!mbar_drain(&done_bar, 0)) abort_flag = 1;
+        }
+    } else {
+        // ----------------------------------------------------- epilogue
+        const int ew = warp - 2;                    // 0..7
+        const int quad = warp & 3;                  // TMEM lanes 32*quad .. +31 (rows)
+        const int half = ew >> 2;                   // columns 64*half .. +63
+        const int64_t row = row0 + quad * 32 + lane;
+        uint64_t sum[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) sum[j] = 0;
+        for (int c = 0; c < chains; ++c) {
+            const int ab = c & 1;
+            const uint32_t acc_ph = (uint32_t)(c >> 1) & 1u;
+            if (!mbar_wait(&acc_full[ab], acc_ph, &abort_flag)) break;
+            tc_fence_after();
+            const int a = (c / TC_DIGITS) % TC_DIGITS, b = c % TC_DIGITS;
+            const int e = (TC_DIGIT_BITS * (a + b)) % 61;
+            const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ab * TC_TILE + half * 64);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t r[16];
+                tmem_ld16(taddr + (uint32_t)(q * 16), r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int64_t v = (int64_t)__float2ll_rn(__uint_as_float(r[j]));   // exact integer
+                    const uint64_t fv = v < 0 ? F61::P - (uint64_t)(-v) : (uint64_t)v;
+                    sum[q * 16 + j] = F61::add(sum[q * 16 + j], rot61(fv, e));
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[ab]);
+        }
+        if (!abort_flag && row < job.m) {
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                const int64_t col = col0 + half * 64 + j;
+                if (col < job.n) {
+                    uint64_t v = sum[j];
+                    if (job.add) v = F61::add(v, job.add[row * job.ldo + col]);
+                    job.out[row * job.ldo + col] = v;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (abort_flag && threadIdx.x == 0) {
+        // loads issued but never consumed must land before the CTA exits
+        for (int g = consumed_g; g < issued_g; ++g) mbar_drain(&full_bar[g % TC_STAGES], (uint32_t)(g / TC_STAGES) & 1u);
+        atomicExch(job.err, 1);
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TC_TMEM_COLS) : "memory");
+    }
+}
+
+// ------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// Tensor map over digit planes [9][rows][inner] (bf16, inner contiguous),
+// boxes of 64 inner x 128 rows x 1 digit, 128-byte swizzle; reads outside
+// the matrix return zero.
+static bool make_map(CUtensorMap *map, const void *planes, int64_t rows, int64_t inner) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, (cuuint64_t)TC_DIGITS};
+    const cuuint64_t strides[2] = {(cuuint64_t)inner * 2, (cuuint64_t)(inner * rows * 2)};
+    const cuuint32_t box[3] = {TC_KB, TC_TILE, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(planes), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct TcWorkspace {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
 int matmul_tensor(spdz_ctx *ctx, const uint64_t *E, const uint64_t *Fm, const uint64_t *Rfold, const spdz_buf *A,
                   const spdz_buf *C, const spdz_buf *Z, int64_t m, int64_t k, int64_t n) {
-    (void)E; (void)Fm; (void)Rfold; (void)A; (void)C; (void)Z; (void)m; (void)k; (void)n;
-    return set_err(ctx, SPDZ_ERR_ARG, "matmul: tensor path not built yet");
+    if (m <= 0 || n <= 0 || k <= 0 || k > 2048)
+        return set_err(ctx, SPDZ_ERR_ARG, "matmul tensor: inner length must be 1..2048 (exact f32 sums)");
+    const int NPn = ctx->n;
+    const int64_t kp = (k + 7) / 8 * 8;    // padded inner length: 16-byte TMA strides
+    const size_t plane_l = (size_t)TC_DIGITS * m * kp * 2, plane_r = (size_t)TC_DIGITS * n * kp * 2;
+    // digits of E and of every A block (left), of every folded right block and of F (right, transposed)
+    const size_t need = plane_l * (1 + 2 * NPn) + plane_r * (1 + 2 * NPn) + 256;
+    static std::mutex mu;
+    static TcWorkspace ws;   // shared by contexts of this process, grown on demand
+    std::lock_guard<std::mutex> g(mu);
+    if (need > ws.bytes) {
+        cudaStreamSynchronize(ctx->stream);
+        if (ws.p) cudaFree(ws.p);
+        ws.p = nullptr;
+        ws.bytes = 0;
+        if (cudaMalloc(&ws.p, need) != cudaSuccess) return set_err(ctx, SPDZ_ERR_OOM, "matmul tensor: workspace");
+        ws.bytes = need;
+    }
+    unsigned char *base = (unsigned char *)ws.p;
+    int *err = (int *)base;
+    __nv_bfloat16 *dE = (__nv_bfloat16 *)(base + 256);
+    __nv_bfloat16 *dA = (__nv_bfloat16 *)((unsigned char *)dE + plane_l);
+    __nv_bfloat16 *dF = (__nv_bfloat16 *)((unsigned char *)dA + plane_l * 2 * NPn);
+    __nv_bfloat16 *dR = (__nv_bfloat16 *)((unsigned char *)dF + plane_r);
+    cudaMemsetAsync(err, 0, sizeof(int), ctx->stream);
+    const int gb = 4 * ctx->sm_count;
+    k_digits_rowmajor<<<gb, 256, 0, ctx->stream>>>(E, m, k, k, kp, dE);
+    for (int w = 0; w < 2; ++w)
+        for (int i = 0; i < NPn; ++i)
+            k_digits_rowmajor<<<gb, 256, 0, ctx->stream>>>((const uint64_t *)(w == 0 ? A->val : A->mac) + (int64_t)i * A->stride,
+                                                           m, k, k, kp, (__nv_bfloat16 *)((unsigned char *)dA + plane_l * (w * NPn + i)));
+    // the transposed kernel covers output columns 0 .. kp-1 (padding included)
+    dim3 tg((unsigned)((n + 31) / 32), (unsigned)((kp + 31) / 32)), tb(32, 8);
+    k_digits_transposed<<<tg, tb, 0, ctx->stream>>>(Fm, k, n, n, kp, dF);
+    for (int j = 0; j < 2 * NPn; ++j)
+        k_digits_transposed<<<tg, tb, 0, ctx->stream>>>(Rfold + (int64_t)j * k * n, k, n, n, kp,
+                                                        (__nv_bfloat16 *)((unsigned char *)dR + plane_r * j));
+    if (int rc = check_launch(ctx, "matmul tensor digits")) return rc;
+    const size_t smem = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
+    cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    CUtensorMap mE, mF;
+    if (!make_map(&mE, dE, m, kp) || !make_map(&mF, dF, n, kp))
+        return set_err(ctx, SPDZ_ERR_CUDA, "matmul tensor: tensor map encoding failed");
+    dim3 grid((unsigned)((n + TC_TILE - 1) / TC_TILE), (unsigned)((m + TC_TILE - 1) / TC_TILE));
+    for (int w = 0; w < 2; ++w)
+        for (int i = 0; i < NPn; ++i) {
+            const int j = w * NPn + i;
+            CUtensorMap mA, mR;
+            if (!make_map(&mA, (unsigned char *)dA + plane_l * j, m, kp) || !make_map(&mR, (unsigned char *)dR + plane_r * j, n, kp))
+                return set_err(ctx, SPDZ_ERR_CUDA, "matmul tensor: tensor map encoding failed");
+            TcJob job;
+            job.add = (const uint64_t *)(w == 0 ? C->val : C->mac) + (int64_t)i * C->stride;
+            job.out = (uint64_t *)(w == 0 ? Z->val : Z->mac) + (int64_t)i * Z->stride;
+            job.ldo = n;
+            job.m = m;
+            job.n = n;
+            job.k = kp;
+            job.err = err;
+            // left [E | A_j], right [Rfold_j ; F] (transposed: rows are output columns)
+            k_tc_gemm<<<grid, TC_THREADS, smem, ctx->stream>>>(mE, mA, mR, mF, job);
+            if (int rc = check_launch(ctx, "matmul tensor gemm")) return rc;
+        }
+    int herr = 0;
+    cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (int rc = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "matmul tensor")) return rc;
+    if (herr) return set_err(ctx, SPDZ_ERR_TIMEOUT, "matmul tensor: a pipeline wait timed out");
+    return SPDZ_OK;
 }
 
 }  // namespace spdz

@@ -74,6 +74,7 @@ class spdz_sched_report(C.Structure):
 
 SPDZ_SERVE_SEQUENTIAL, SPDZ_SERVE_BATCHED, SPDZ_SERVE_HEURISTIC, SPDZ_SERVE_LEARNED = 0, 1, 2, 3
 SPDZ_MATMUL_CUDA_CORE, SPDZ_MATMUL_TENSOR = 0, 1
+TENSOR_PATH = True          # the library has the tensor-core matrix path
 
 
 class spdz_serve_request(C.Structure):
