@@ -49,6 +49,14 @@ def peaks():
         return 6400.0, "fallback"
 
 
+def read_traffic():
+    """Per-launch DRAM bytes (read + write) from the committed ncu captures."""
+    try:
+        return json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except Exception:
+        return {}
+
+
 def circuit_bytes(dag, n=N_PARTIES, w=8):
     """Algorithmic HBM bytes of one run: per party, MUL reads x, y, a, b, c
     (values and MACs) and writes z (value and MAC) = 12 words; ADD/SUB read 4
@@ -88,6 +96,12 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi takes a moment to start: wait for its first sample
+            # so that the samples cover the region that follows
+            t0 = time.time()
+            while not self.rows and time.time() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.rows.clear()
         except Exception:
             self.proc = None
         return self
@@ -97,6 +111,14 @@ class ClockSampler:
             self.rows.append([x.strip() for x in line.split(",")])
 
     def __exit__(self, *a):
+        if self.proc and not self.rows:
+            # a region shorter than the sampling period: one sample at its end
+            try:
+                r = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                    "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+                self.rows.extend([x.strip() for x in ln.split(",")] for ln in r.stdout.splitlines() if ln.strip())
+            except Exception:
+                pass
         if self.proc:
             self.proc.terminate()
             try:
@@ -153,7 +175,7 @@ class Circuit:
         self.wires = SH.alloc(self.field, N_PARTIES, dag.n_wires)
         S.spdz_deal_shared(self.ctx, seed, S.SPDZ_KIND_INPUT, INPUT_SUB, 0, dag.n_inputs, self.alpha_sh,
                            None, self.wires.buf())
-        self.pool_runs = min(runs, pool_runs or runs)
+        self.pool_runs = max(runs, pool_runs) if pool_runs else runs
         self.T = self.pool_runs * dag.n_mul
         self.tri = [SH.alloc(self.field, N_PARTIES, self.T) for _ in range(3)]
         self.next_j0 = 0
@@ -272,7 +294,9 @@ def beaver_roofline(torch, S, SH, hbm_peak, N=2**24, calls=4):
         gbs = 288 * N / (ms * 1e-3) / 1e9
         return {"kernel": "k_mul<F61,3,2> (spdz_mul_batch)", "N": N, "bytes_per_mult": 288,
                 "ms": round(ms, 4), "mults_per_s": N / (ms * 1e-3), "achieved_gbs": round(gbs, 1),
-                "peak_gbs": hbm_peak, "frac": round(gbs / hbm_peak, 4), "mac_check_passed": ok}
+                "peak_gbs": hbm_peak, "frac": round(gbs / hbm_peak, 4),
+                "traffic": read_traffic().get("k_mul") if N == 2**24 else None,
+                "l2": "inputs larger than L2 (4.8 GB per call)", "mac_check_passed": ok}
     finally:
         S.spdz_ctx_destroy(ctx)
 
@@ -357,11 +381,15 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
 
     barrier()
+    # the timed regions are bracketed for profilers started with
+    # --profile-from-start off (no effect otherwise)
+    torch.cuda.cudart().cudaProfilerStart()
     with ClockSampler(local_rank) as clk:
         t_f, ok_f = time_steps(circ, scheduled, steps, warmup, flush)
     barrier()
     t_p, ok_p = time_steps(circ, per_layer, steps, warmup, flush)
     barrier()
+    torch.cuda.cudart().cudaProfilerStop()
     tot_f, tot_p = max_over_ranks([sum(t_f), sum(t_p)], world)
     e2e_dt, bi, bo, ok_e = e2e_steps(circ, scheduled, e2e_n)
     (e2e_dt,) = max_over_ranks([e2e_dt], world)
@@ -375,13 +403,15 @@ def run_ours(args, rank, world, local_rank):
     # the fused kernel dominates the step (one begin and one check kernel of a
     # few microseconds beside it); its launch duration is bounded by the step
     achieved = bytes_run / (ms * 1e-3) / 1e9
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_path):
-        try:
-            traffic = json.load(open(tr_path)).get("k_dag_fused")
-        except Exception:
-            traffic = None
+    # DRAM traffic per launch from the committed ncu capture, used only when
+    # the chosen plan is the captured one
+    tr = read_traffic()
+    cap = tr.get("k_dag_fused_plan", {})
+    groups = sched["chosen_groups"]
+    same = (len(groups) == cap.get("groups") and all(
+        g["block"] == cap.get("block") and g["ctas_per_sm"] == cap.get("ctas_per_sm")
+        and g["cluster"] == cap.get("cluster") for g in groups))
+    traffic = tr.get("k_dag_fused") if same else None
     beaver = beaver_roofline(torch, S, SH, hbm)
     cpu = cpu_baseline(dag, seed=2) if not args.no_cpu_baseline else None
     line = {
@@ -715,6 +745,21 @@ def run_profile(args):
             circ.run(plan)
         torch.cuda.synchronize()
         assert S.spdz_check_result(circ.ctx)
+    elif args.profile == "matmul":
+        dim, n, f = 2048, N_PARTIES, S.SPDZ_F61
+        ctx = S.spdz_ctx_create(n, f, torch.cuda.current_stream().cuda_stream)
+        ash = SH.zeros(f, n)
+        S.spdz_deal_alpha(ctx, 4, ash)
+        S.spdz_load_preproc(ctx, ash, None, None, None, 0)
+        X, Y, Z, A, B, Cm = (SH.alloc(f, n, dim * dim) for _ in range(6))
+        S.spdz_deal_shared(ctx, 4, S.SPDZ_KIND_INPUT, 10, 0, dim * dim, ash, None, X.buf())
+        S.spdz_deal_shared(ctx, 4, S.SPDZ_KIND_INPUT, 11, 0, dim * dim, ash, None, Y.buf())
+        for rep in range(args.steps):
+            S.spdz_deal_matrix_triple(ctx, 4, rep, dim, dim, dim, ash, A.buf(), B.buf(), Cm.buf())
+            S.spdz_load_matrix_preproc(ctx, A.buf(), B.buf(), Cm.buf(), dim, dim, dim)
+            S.spdz_matmul(ctx, X.buf(), Y.buf(), Z.buf(), dim, dim, dim, S.SPDZ_MATMUL_TENSOR)
+            assert S.spdz_mac_check(ctx)
+        S.spdz_ctx_destroy(ctx)
     else:
         beaver_roofline(torch, S, SH, peaks()[0], N=2**24, calls=args.steps)
 
@@ -730,7 +775,7 @@ def main():
                     help="circuit: the benchmark circuit (default); serve, matmul, heavy, batch: the other "
                          "workloads, one JSON line each")
     ap.add_argument("--serve-requests", type=int, default=10000)
-    ap.add_argument("--profile", default=None, choices=["dag", "beaver"],
+    ap.add_argument("--profile", default=None, choices=["dag", "beaver", "matmul"],
                     help="small run of one kernel for an ncu capture (prints nothing)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
