@@ -231,12 +231,13 @@ def schedule(circ, reps=2, epochs=400):
     plan, rep = S.spdz_sched_choose(circ.ctx, circ.h, circ.wires.buf(), 5)
     for d, h, w in items[:-1]:
         S.spdz_dag_destroy(h)
-    names = {0: "default fused plan", 1: "autotuned uniform plan", 2: "learned plan"}
+    names = {0: "default fused plan", 1: "autotuned uniform plan", 2: "learned plan", 3: "tagged plan"}
     groups = [{"end": int(plan.group_end[g]), "cluster": int(plan.group_cluster[g]),
                "block": int(plan.group_block[g]), "ctas_per_sm": int(plan.group_ctas_per_sm[g])}
               for g in range(plan.n_groups)]
     return {"chosen": names.get(rep.chosen, "?"), "default_ms": rep.default_ms, "autotuned_ms": rep.autotuned_ms,
             "learned_ms": rep.learned_ms, "learned_predicted_ms": rep.predicted_ms,
+            "tagged_ms": rep.tagged_ms, "chosen_mode": int(plan.mode),
             "learned_groups": rep.learned_groups, "switch_us": rep.switch_us, "samples": rep.samples,
             "train_loss_ln_us": rep.train_loss, "scheduling_s": round(time.perf_counter() - t0, 2),
             "chosen_groups": groups}
@@ -400,18 +401,23 @@ def run_ours(args, rank, world, local_rank):
     per_layer_value = world * nm * steps / (tot_p * 1e-3)
     bytes_run = circuit_bytes(dag)
     ms = tot_f / steps
-    # the fused kernel dominates the step (one begin and one check kernel of a
-    # few microseconds beside it); its launch duration is bounded by the step
+    # the circuit kernel dominates the step (one begin and one check kernel of
+    # a few microseconds beside it); its launch duration is bounded by the step
     achieved = bytes_run / (ms * 1e-3) / 1e9
     # DRAM traffic per launch from the committed ncu capture, used only when
     # the chosen plan is the captured one
     tr = read_traffic()
-    cap = tr.get("k_dag_fused_plan", {})
-    groups = sched["chosen_groups"]
-    same = (len(groups) == cap.get("groups") and all(
-        g["block"] == cap.get("block") and g["ctas_per_sm"] == cap.get("ctas_per_sm")
-        and g["cluster"] == cap.get("cluster") for g in groups))
-    traffic = tr.get("k_dag_fused") if same else None
+    if sched["chosen_mode"] == S.SPDZ_SCHED_TAGGED:
+        kname = "k_dag_tagged<3> (scheduled circuit run)"
+        traffic = tr.get("k_dag_tagged")
+    else:
+        kname = "k_dag_fused<F61,3> (scheduled circuit run)"
+        cap = tr.get("k_dag_fused_plan", {})
+        groups = sched["chosen_groups"]
+        same = (len(groups) == cap.get("groups") and all(
+            g["block"] == cap.get("block") and g["ctas_per_sm"] == cap.get("ctas_per_sm")
+            and g["cluster"] == cap.get("cluster") for g in groups))
+        traffic = tr.get("k_dag_fused") if same else None
     beaver = beaver_roofline(torch, S, SH, hbm)
     cpu = cpu_baseline(dag, seed=2) if not args.no_cpu_baseline else None
     line = {
@@ -439,7 +445,7 @@ def run_ours(args, rank, world, local_rank):
         "scheduler": sched,
         "e2e": {"value": world * nm * e2e_n / e2e_dt, "unit": "Beaver mults/s",
                 "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
-        "roofline": {"bound": "hbm", "kernel": "k_dag_fused<F61,3> (scheduled circuit run)", "achieved": round(achieved, 1),
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                      "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
                      "peak_source": peak_src, "algorithmic_bytes_per_launch": bytes_run},
         "beaver_batch_roofline": beaver,
@@ -732,15 +738,16 @@ def run_batch(args):
 
 
 def run_profile(args):
-    """A few launches of one kernel, for ncu: 'dag' runs the benchmark
-    circuit (fused, no graph) `steps` times; 'beaver' runs spdz_mul_batch on
+    """A few launches of one kernel, for ncu: 'dag' ('tagged') runs the
+    benchmark circuit with the fused (tagged) plan, no graph, `steps` times; 'beaver' runs spdz_mul_batch on
     2^24 products (n=3, p61) `steps` times."""
     import torch
     from paper_2512_11112_b300 import shares as SH
     from paper_2512_11112_b300 import spdz as S
-    if args.profile == "dag":
+    if args.profile in ("dag", "tagged"):
         circ = Circuit(W.layered_dag(seed=2), seed=2, runs=args.steps)
-        plan = S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=0)
+        mode = S.SPDZ_SCHED_FUSED if args.profile == "dag" else S.SPDZ_SCHED_TAGGED
+        plan = S.plan(mode=mode, use_graph=0)
         for _ in range(args.steps):
             circ.run(plan)
         torch.cuda.synchronize()
@@ -775,7 +782,7 @@ def main():
                     help="circuit: the benchmark circuit (default); serve, matmul, heavy, batch: the other "
                          "workloads, one JSON line each")
     ap.add_argument("--serve-requests", type=int, default=10000)
-    ap.add_argument("--profile", default=None, choices=["dag", "beaver", "matmul"],
+    ap.add_argument("--profile", default=None, choices=["dag", "tagged", "beaver", "matmul"],
                     help="small run of one kernel for an ncu capture (prints nothing)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

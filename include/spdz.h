@@ -211,7 +211,24 @@ typedef struct spdz_dag spdz_dag;
 
 enum spdz_sched {
     SPDZ_SCHED_PER_LAYER = 0,  /* one kernel launch per layer and gate class (MUL, linear) */
-    SPDZ_SCHED_FUSED = 1       /* persistent kernel per layer group, device barriers between layers */
+    SPDZ_SCHED_FUSED = 1,      /* persistent kernel per layer group, device barriers between layers */
+    SPDZ_SCHED_TAGGED = 2      /* p = 2^61-1 only: one persistent kernel like FUSED (one group),
+                                  over a tagged copy of the wires.  Every share below 2^61 leaves
+                                  the top three bits of its 64-bit word free: gates also write
+                                  their outputs to a wire-major copy of the wires (owned by the
+                                  circuit, (n_inputs + n_gates) x 2n words: one wire's shares of
+                                  every party side by side) with a per-run tag in those bits,
+                                  and read their operands from it, accepting an operand once
+                                  every word carries the run's tag (an aligned 8-byte store is
+                                  seen whole or not at all).  The layer barrier therefore needs
+                                  no fence.  The copy is zeroed every 7 runs of the circuit so no
+                                  stale word carries a current tag.  Plan fields used: block,
+                                  ctas_per_sm, use_graph, spin_limit_us (bound of one barrier or
+                                  operand wait), poll_ns, record_layer_times,
+                                  barrier_extra_arrivals (testing: > 0 makes the first operand
+                                  of every gate after the first layer wait for a tag that is
+                                  never written, so the bounded wait runs out:
+                                  SPDZ_ERR_TIMEOUT); n_groups must be 0. */
 };
 
 /* Execution plan of a circuit run.  No plan changes any result bit. */
@@ -234,6 +251,9 @@ typedef struct {
                                               thread-block cluster of k CTAs with cluster
                                               barriers (for narrow layers) */
     int32_t group_block[SPDZ_MAX_GROUPS];  /* per-group threads per CTA; 0 = plan value */
+    uint32_t poll_ns;                      /* tagged: first sleep between polls of an operand
+                                              that is not ready (ns, doubling up to 16x);
+                                              0 = 128, at most 50000 */
 } spdz_plan;
 
 typedef struct {
@@ -353,10 +373,12 @@ typedef struct {
     double learned_ms;     /* measured makespan of the learned plan (-1: model not trained) */
     double predicted_ms;   /* the cost model's prediction for the learned plan (-1: none) */
     double switch_us;      /* measured cost of one extra layer group */
-    int32_t chosen;        /* plan kept for plan == NULL runs: 0 default, 1 autotuned, 2 learned */
+    int32_t chosen;        /* plan kept for plan == NULL runs: 0 default, 1 autotuned, 2 learned,
+                              3 tagged */
     int32_t learned_groups;
     int32_t samples;       /* training samples recorded so far */
     float train_loss;      /* final training loss (mean squared error of ln microseconds) */
+    double tagged_ms;      /* measured makespan of the tagged plan (-1: not applicable) */
 } spdz_sched_report;
 
 int spdz_sched_num_configs(int32_t *count, int32_t *n_features);
@@ -385,8 +407,9 @@ int spdz_sched_learned_plan(spdz_ctx *ctx, spdz_dag *dag, spdz_plan *out, double
 /* The autotuned plan: the fastest measured uniform configuration. */
 int spdz_sched_autotune(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int32_t reps, spdz_plan *out,
                         double *best_ms);
-/* Measures the default, autotuned and (if trained) learned plans, keeps the
- * fastest for this circuit's plan == NULL runs, and reports all three. */
+/* Measures the default, autotuned, (if trained) learned and (p = 2^61-1)
+ * tagged plans, keeps the fastest for this circuit's plan == NULL runs, and
+ * reports them all. */
 int spdz_sched_choose(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int32_t reps, spdz_plan *out,
                       spdz_sched_report *rep);
 

@@ -49,7 +49,8 @@ __device__ void check_epoch(DevState *ds, int final_check) {
             ds->res_sigma[i][1] = ds->sig_run[i][1];
             ds->sig_run[i][0] = ds->sig_run[i][1] = 0;
         }
-        ds->res_passed = ds->partial_fail ? 0u : 1u;
+        // a run whose device wait timed out is incomplete: it never passes
+        ds->res_passed = (ds->partial_fail || (ds->err_flags & ERR_TIMEOUT)) ? 0u : 1u;
         ds->res_epoch = (uint32_t)ds->epoch;
         ds->partial_fail = 0;
         ds->epoch += 1;

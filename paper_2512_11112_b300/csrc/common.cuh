@@ -41,7 +41,8 @@ struct DevState {
     // grid barrier of the fused circuit kernel: arrivals counted over a run
     unsigned int bar_count;
     unsigned int bar_abort;            // set when a barrier wait timed out
-    unsigned int bar_pad[62];
+    unsigned int df_tag;               // tag of the current tagged-mode run (1..7; 0: none)
+    unsigned int bar_pad[61];
     // per-layer timestamps written by the fused circuit kernel (globaltimer ns)
     unsigned long long layer_ts[1024];
 };

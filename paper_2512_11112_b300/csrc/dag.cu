@@ -8,7 +8,9 @@
 //   * fused: one persistent kernel per group of consecutive layers; CTAs
 //     meet at a device-wide barrier between layers (bounded wait, timeout
 //     status instead of a hang), the run is captured once as a CUDA graph and
-//     replayed.
+//     replayed;
+//   * tagged (p61): the fused form over a tagged wire-major copy of the wires;
+//     operands validate themselves by tag, so the layer barrier needs no fence.
 // In both, a MUL gate masks, opens (sum over the party rows in registers) and
 // combines in one pass, and the MAC-check terms of its opened values are
 // accumulated in registers and reduced once per kernel.
@@ -19,6 +21,7 @@
 // follow from its record index and a per-layer row of class boundaries;
 // constants are stored in record order.
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <vector>
 
@@ -75,9 +78,9 @@ static int occupancy(const void *kern, int block, size_t smem = 0) {
 // Returns the number of launches, or -status.
 template <class F, int NP>
 static int enqueue_run(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, const spdz_buf *w, cudaStream_t s,
-                       uint64_t tri_base, bool layer_events) {
+                       uint64_t tri_base, bool layer_events, uint32_t df_tag) {
     int launches = 0;
-    k_run_begin<<<1, 1, 0, s>>>(ctx->ds, tri_base);
+    k_run_begin<<<1, 1, 0, s>>>(ctx->ds, tri_base, df_tag);
     ++launches;
     const int block = plan.block > 0 ? plan.block : 256;
     DagArgs<F> a = base_args<F>(ctx, dag, w);
@@ -107,6 +110,40 @@ static int enqueue_run(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, cons
             }
         }
         if (layer_events) cudaEventRecord(dag->lev[dag->depth], s);
+    } else if (plan.mode == SPDZ_SCHED_TAGGED) {
+        if constexpr (F::WORDS == 1) {
+            auto kern = k_dag_tagged<NP>;
+            const size_t smem = tagged_smem<NP>(block);
+            if (smem > 48 * 1024) {
+                cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) {
+                    ctx->stream = saved;
+                    return -set_err(ctx, SPDZ_ERR_CUDA, "tagged kernel shared memory (%zu bytes): %s", smem, cudaGetErrorString(e));
+                }
+            }
+            // every CTA must be resident (gates wait on gates of other CTAs)
+            const int occ = occupancy((const void *)kern, block, smem);
+            int cpsm = plan.ctas_per_sm;
+            if (cpsm <= 0 || cpsm > occ) cpsm = occ;
+            int64_t wmax = 1;
+            for (int l = 0; l < dag->depth; ++l) wmax = std::max<int64_t>(wmax, dag->lay[l].s[5] - dag->lay[l].s[0]);
+            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)cpsm * ctx->sm_count, (wmax + 31) / 32));
+            a.mir = dag->d_mir;
+            a.n_in = dag->n_inputs;
+            a.poll_ns = plan.poll_ns ? plan.poll_ns : 128u;
+            a.record_ts = layer_events ? 1 : 0;
+            a.l0 = 0;
+            a.l1 = dag->depth;
+            kern<<<grid, block, smem, s>>>(a);
+            ++launches;
+            if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) {
+                ctx->stream = saved;
+                return -set_err(ctx, SPDZ_ERR_CUDA, "tagged circuit launch: %s", cudaGetErrorString(e));
+            }
+        } else {
+            ctx->stream = saved;
+            return -set_err(ctx, SPDZ_ERR_ARG, "tagged mode needs p = 2^61-1");
+        }
     } else {
         auto kern = F::WORDS == 1 ? k_dag_fused<F, NP> : k_dag_fused_wide<F, NP>;
         const int ng = plan.n_groups > 0 ? plan.n_groups : 1;
@@ -202,16 +239,22 @@ static int enqueue_run(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, cons
 }
 
 static int enqueue_dispatch(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, const spdz_buf *w, cudaStream_t s,
-                            uint64_t tri_base, bool layer_events) {
+                            uint64_t tri_base, bool layer_events, uint32_t df_tag) {
     int r = -SPDZ_ERR_ARG;
-    SPDZ_FIELD_SWITCH(ctx->field, SPDZ_NP_SWITCH(ctx->n, r = (enqueue_run<F, NP>(ctx, dag, plan, w, s, tri_base, layer_events))));
+    SPDZ_FIELD_SWITCH(ctx->field, SPDZ_NP_SWITCH(ctx->n, r = (enqueue_run<F, NP>(ctx, dag, plan, w, s, tri_base, layer_events, df_tag))));
     return r;
 }
 
 static bool same_plan(const spdz_plan &a, const spdz_plan &b) { return memcmp(&a, &b, sizeof a) == 0; }
 
 static int validate_plan(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &p) {
-    if (p.mode != SPDZ_SCHED_PER_LAYER && p.mode != SPDZ_SCHED_FUSED) return set_err(ctx, SPDZ_ERR_ARG, "plan: bad mode");
+    if (p.mode != SPDZ_SCHED_PER_LAYER && p.mode != SPDZ_SCHED_FUSED && p.mode != SPDZ_SCHED_TAGGED)
+        return set_err(ctx, SPDZ_ERR_ARG, "plan: bad mode");
+    if (p.mode == SPDZ_SCHED_TAGGED) {
+        if (dag->field != SPDZ_F61) return set_err(ctx, SPDZ_ERR_ARG, "plan: tagged mode needs p = 2^61-1");
+        if (p.n_groups != 0) return set_err(ctx, SPDZ_ERR_ARG, "plan: tagged mode has no layer groups");
+        if (p.poll_ns > 50000) return set_err(ctx, SPDZ_ERR_ARG, "plan: poll_ns above 50 us");
+    }
     if (p.block != 0 && (p.block < 32 || p.block > 256 || p.block % 32)) return set_err(ctx, SPDZ_ERR_ARG, "plan: block must be 32..256, a multiple of 32");
     if (p.n_groups < 0 || p.n_groups > SPDZ_MAX_GROUPS) return set_err(ctx, SPDZ_ERR_ARG, "plan: bad group count");
     if (p.barrier_extra_arrivals < 0 || p.barrier_extra_arrivals > 1024) return set_err(ctx, SPDZ_ERR_ARG, "plan: bad extra arrivals");
@@ -327,6 +370,7 @@ int spdz_dag_destroy(spdz_dag *g) {
     if (g->d_rec) cudaFree(g->d_rec);
     if (g->d_lay) cudaFree(g->d_lay);
     if (g->d_kc) cudaFree(g->d_kc);
+    if (g->d_mir) cudaFree(g->d_mir);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     for (auto &e : g->lev) cudaEventDestroy(e);
@@ -355,6 +399,24 @@ int spdz_run_dag(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan *plan_in, const s
     const uint64_t tri_base = (uint64_t)ctx->tri_cursor;
     const bool layer_events = plan.record_layer_times != 0;
     if (stats) cudaEventRecord(dag->ev0, ctx->stream);
+    // tagged: the tagged copy (allocated on first use), the run's tag, and
+    // the copy zeroed before the first run of every cycle of 7 tags
+    uint32_t df_tag = 0;
+    if (plan.mode == SPDZ_SCHED_TAGGED) {
+        const size_t need = (size_t)(dag->n_inputs + dag->n_gates) * 2 * (size_t)dag->n * sizeof(uint64_t);
+        if (!dag->d_mir) {
+            if (cudaMalloc(&dag->d_mir, std::max<size_t>(need, 16)) != cudaSuccess) {
+                dag->d_mir = nullptr;
+                return set_err(ctx, SPDZ_ERR_OOM, "run_dag: tagged wire copy (%zu bytes)", need);
+            }
+            dag->mir_bytes = need;
+            dag->df_runs = 0;
+        }
+        df_tag = (uint32_t)(dag->df_runs % 7) + 1;
+        ++dag->df_runs;
+        if (df_tag == 1 && (rc = check_cuda(ctx, cudaMemsetAsync(dag->d_mir, 0, dag->mir_bytes, ctx->stream), "zero wire copy")))
+            return rc;
+    }
     int launches = 0;
     if (plan.use_graph && !layer_events) {
         const bool reuse = dag->gexec && same_plan(dag->gplan, plan) && dag->gwires.val == wires->val &&
@@ -367,7 +429,7 @@ int spdz_run_dag(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan *plan_in, const s
             cudaGraph_t graph;
             if ((rc = check_cuda(ctx, cudaStreamBeginCapture(dag->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture")))
                 return rc;
-            int n = enqueue_dispatch(ctx, dag, plan, wires, dag->cap_stream, tri_base, false);
+            int n = enqueue_dispatch(ctx, dag, plan, wires, dag->cap_stream, tri_base, false, df_tag);
             cudaError_t ce = cudaStreamEndCapture(dag->cap_stream, &graph);
             if (n < 0) return -n;
             if ((rc = check_cuda(ctx, ce, "end capture"))) return rc;
@@ -391,7 +453,8 @@ int spdz_run_dag(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan *plan_in, const s
         }
         DevState *ds = ctx->ds;
         uint64_t tb = tri_base;
-        void *args[2] = {&ds, &tb};
+        uint32_t tg = df_tag;
+        void *args[3] = {&ds, &tb, &tg};
         cudaKernelNodeParams kp = dag->gbegin_params;
         kp.kernelParams = args;
         kp.extra = nullptr;
@@ -400,7 +463,7 @@ int spdz_run_dag(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan *plan_in, const s
             return rc;
         launches = dag->glaunches;
     } else {
-        int n = enqueue_dispatch(ctx, dag, plan, wires, ctx->stream, tri_base, layer_events);
+        int n = enqueue_dispatch(ctx, dag, plan, wires, ctx->stream, tri_base, layer_events, df_tag);
         if (n < 0) return -n;
         launches = n;
     }
@@ -427,7 +490,7 @@ int spdz_run_dag(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan *plan_in, const s
                 dag->layer_us[l] = (float)((double)(ctx->hres->layer_ts[l + 1] - ctx->hres->layer_ts[l]) * 1e-3);
         }
     }
-    if (ctx->hres->err_flags & ERR_TIMEOUT) return set_err(ctx, SPDZ_ERR_TIMEOUT, "run_dag: a device barrier wait timed out");
+    if (ctx->hres->err_flags & ERR_TIMEOUT) return set_err(ctx, SPDZ_ERR_TIMEOUT, "run_dag: a device wait timed out");
     if (!stats->passed) return set_err(ctx, SPDZ_ERR_MAC, "run_dag: MAC check failed");
     return SPDZ_OK;
 }

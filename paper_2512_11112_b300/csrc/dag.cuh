@@ -27,6 +27,10 @@ struct spdz_dag {
     uint4 *d_rec = nullptr;
     spdz::LayerRow *d_lay = nullptr;
     void *d_kc = nullptr;
+    // tagged mode: tagged wire-major copy of the wires, and the runs so far
+    uint64_t *d_mir = nullptr;
+    size_t mir_bytes = 0;
+    uint64_t df_runs = 0;
     // captured run
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;

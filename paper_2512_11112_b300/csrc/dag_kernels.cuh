@@ -57,6 +57,9 @@ template <class F> struct DagArgs {
     uint64_t spin_ns;
     int32_t record_ts;
     uint32_t extra_arrivals;                // testing: arrivals that never come
+    uint64_t *mir;                          // tagged: wire-major copy [wires][2*NP]
+    int64_t n_in;                           // tagged: input wires copied into it
+    uint32_t poll_ns;                       // tagged: first sleep between operand polls
 };
 
 // Operands of one gate that do not depend on earlier layers: its record,
@@ -199,16 +202,25 @@ __device__ __forceinline__ unsigned long long gtimer() {
 // for); thread 0 polls with acquire loads.  The wait is bounded by spin_ns,
 // after which the CTA records a timeout, raises the abort flag and returns
 // false (every later barrier of the run then returns false at once).
+// RELAXED: arrival and polls carry no ordering (no fence waits for the CTA's
+// stores); for data that validates itself (tagged operands).
+template <bool RELAXED = false>
 __device__ __forceinline__ bool grid_barrier(DevState *ds, unsigned int target, uint64_t spin_ns) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ds->bar_count) : "memory");
+        if constexpr (RELAXED)
+            asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(&ds->bar_count) : "memory");
+        else
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ds->bar_count) : "memory");
         const unsigned long long t0 = gtimer();
         while (true) {
             unsigned int v, ab;
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ds->bar_count) : "memory");
+            if constexpr (RELAXED)
+                asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ds->bar_count) : "memory");
+            else
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ds->bar_count) : "memory");
             if ((int)(v - target) >= 0) break;
             asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(ab) : "l"(&ds->bar_abort) : "memory");
             if (ab) { ok = 0; break; }
@@ -229,11 +241,12 @@ __device__ __forceinline__ bool grid_barrier(DevState *ds, unsigned int target, 
 // Start of a run: the triple cursor the run consumes from, fresh barrier
 // counters and error flags.  Its argument is updated before every replay of
 // a captured run.
-static __global__ void k_run_begin(DevState *ds, uint64_t tri_base) {
+static __global__ void k_run_begin(DevState *ds, uint64_t tri_base, uint32_t df_tag) {
     ds->tri_cursor = tri_base;
     ds->bar_count = 0;
     ds->bar_abort = 0;
     ds->err_flags = 0;
+    ds->df_tag = df_tag;
 }
 
 // Per-layer form: records [r0, r1) of layer l0 (one gate class range).
@@ -355,6 +368,221 @@ __global__ void __launch_bounds__(256, 1) k_dag_cluster(DagArgs<F> a) {
 
 template <class F, int NP> constexpr size_t fused_smem(int block) {
     return Stage<F, NP>::bytes_per_thread() * (size_t)block;
+}
+
+// ---------------------------------------------- tagged execution (p61 only)
+// A stored p61 share is below 2^61, so the top three bits of its 64-bit word
+// are free.  In tagged mode every gate also stores its output shares -- the
+// NP values, then the NP MACs -- into a wire-major copy of the wires with the
+// run's tag (1..7) in those bits.  An aligned 8-byte store is observed whole
+// or not at all, so a reader that finds the tag in all 2*NP words of an
+// operand holds that operand's value of this run, whatever order the stores
+// became visible in: no fence is needed between a gate's stores and their
+// readers.  Tag 0 never matches; the host zeroes the copy before every 7th
+// run of a circuit, so within the 7 runs that follow each word holds either
+// nothing or this cycle's tags, all different.
+constexpr int DF_TAG_SHIFT = 61;
+
+__device__ __forceinline__ void df_st2(uint64_t *p, uint64_t a, uint64_t b) {
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+__device__ __forceinline__ void df_ld2(const uint64_t *p, uint64_t &a, uint64_t &b) {
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
+__device__ __forceinline__ unsigned int ld_relaxed_u32(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Reads the operand record of wire w; true when every word carries `tag`.
+template <int NP>
+__device__ __forceinline__ bool df_fetch(const uint64_t *mir, uint32_t w, uint64_t tag, uint64_t (&v)[2 * NP]) {
+    const uint64_t *p = mir + (size_t)w * (2 * NP);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) df_ld2(p + 2 * k, v[2 * k], v[2 * k + 1]);
+    uint64_t bad = 0;
+#pragma unroll
+    for (int k = 0; k < 2 * NP; ++k) bad |= (v[k] >> DF_TAG_SHIFT) ^ tag;
+    return bad == 0;
+}
+
+// Slow path of an operand wait: one sleep (doubling from poll_ns up to 16x),
+// and every 8th call a look at the abort flag and at the bound of the wait
+// (on timeout the run is marked failed and aborted).  False when the wait
+// must give up.
+__device__ __forceinline__ bool df_backoff(DevState *ds, uint64_t spin_ns, unsigned long long t0, unsigned int it,
+                                           uint32_t poll_ns) {
+    __nanosleep(poll_ns << min(it - 1u, 4u));
+    if ((it & 7) != 0) return true;
+    if (ld_relaxed_u32(&ds->bar_abort)) return false;
+    if (gtimer() - t0 > spin_ns) {
+        atomicOr(&ds->err_flags, ERR_TIMEOUT);
+        atomicExch(&ds->bar_abort, 1u);
+        return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ uint64_t df_ld1(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// The operand record of wire w once it carries `tag` (bounded wait).  While
+// waiting, only the record's first word is polled (one sector); the whole
+// record is read again once that word carries the tag.
+template <int NP>
+__device__ __forceinline__ bool df_get(const DagArgs<F61> &a, uint32_t w, uint64_t tag, uint64_t (&v)[2 * NP]) {
+    if (df_fetch<NP>(a.mir, w, tag, v)) return true;
+    const uint64_t *p = a.mir + (size_t)w * (2 * NP);
+    const unsigned long long t0 = gtimer();
+    unsigned int it = 0;
+    while (true) {
+        if (!df_backoff(a.ds, a.spin_ns, t0, ++it, a.poll_ns)) return false;
+        if ((df_ld1(p) >> DF_TAG_SHIFT) == tag && df_fetch<NP>(a.mir, w, tag, v)) return true;
+    }
+}
+
+template <int NP>
+__device__ __forceinline__ void df_store(uint64_t *mir, uint32_t w, uint64_t tag, const uint64_t (&z)[NP],
+                                         const uint64_t (&gz)[NP]) {
+    uint64_t t[2 * NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        t[i] = z[i] | (tag << DF_TAG_SHIFT);
+        t[NP + i] = gz[i] | (tag << DF_TAG_SHIFT);
+    }
+    uint64_t *p = mir + (size_t)w * (2 * NP);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) df_st2(p + 2 * k, t[2 * k], t[2 * k + 1]);
+}
+
+// One gate in tagged mode: fetch (and if needed wait for) the operands,
+// compute, store the output shares (caller's party-major wires, and the
+// tagged copy).
+template <int NP, class TRI>
+__device__ __forceinline__ bool df_gate(const DagArgs<F61> &a, const LayerRow &L, int32_t r, int cls, uint4 rec,
+                                        uint64_t kconst, const TRI &tri, uint64_t key, uint64_t tag, uint64_t wtag,
+                                        const uint64_t (&alpha)[NP], uint64_t (&acc)[NP + 1]) {
+    using F = F61;
+    const bool binary = cls <= C_SUB;
+    uint64_t u[2 * NP], v[2 * NP];
+    if (!df_get<NP>(a, rec.x, wtag, u)) return false;
+    if (binary && !df_get<NP>(a, rec.y, tag, v)) return false;
+    uint64_t z[NP], gz[NP];
+    if (cls == C_MUL) {
+        uint64_t x[NP], gx[NP], y[NP], gy[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            x[i] = u[i] & F::P;
+            gx[i] = u[NP + i] & F::P;
+            y[i] = v[i] & F::P;
+            gy[i] = v[NP + i] & F::P;
+        }
+        const uint64_t rank = (uint64_t)(L.mulbase + (r - L.s[0]));
+        beaver_math_src<F, NP>(x, gx, y, gy, tri, alpha, key, 2 * rank, acc, z, gz);
+    } else {
+        const int op = cls == C_ADD ? SPDZ_OP_ADD : cls == C_SUB ? SPDZ_OP_SUB : cls == C_CMUL ? SPDZ_OP_CMUL : SPDZ_OP_CADD;
+        const uint64_t k = binary ? 0 : kconst;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            const uint64_t y = binary ? v[i] & F::P : 0, gy = binary ? v[NP + i] & F::P : 0;
+            const uint64_t kal = cls == C_CADD ? F::mul(alpha[i], k) : 0;
+            linear_math<F>(op, i, u[i] & F::P, u[NP + i] & F::P, y, gy, k, kal, z[i], gz[i]);
+        }
+    }
+    const uint32_t out = rec.z;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        F::st(a.wv + i * a.ws + out, z[i]);
+        F::st(a.wm + i * a.ws + out, gz[i]);
+    }
+    df_store<NP>(a.mir, out, tag, z, gz);
+    return true;
+}
+
+// The tagged form of the fused kernel (p61): gates read their operands from
+// the tagged copy (one wire's shares of every party in 2*NP consecutive
+// words, a third of the sectors of the party-major gathers) and validate
+// them by tag, so the barrier between layers needs no fence: it only keeps
+// the CTAs in step (few operands are still in flight when a layer starts,
+// and their readers re-poll one word).  The inputs are first copied into
+// the tagged copy (one wire per thread, coalesced).
+template <int NP>
+__global__ void __launch_bounds__(256, 2) k_dag_tagged(DagArgs<F61> a) {
+    using F = F61;
+    extern __shared__ __align__(16) unsigned char smem[];
+    Stage<F, NP> st;
+    st.init(smem, blockDim.x);
+    const uint64_t key = a.ds->key, tri_base = a.ds->tri_cursor;
+    const uint64_t tag = a.ds->df_tag;
+    uint64_t alpha[NP], acc[NP + 1];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
+#pragma unroll
+    for (int k = 0; k < NP + 1; ++k) acc[k] = 0;
+    const int32_t nthreads = gridDim.x * blockDim.x;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < a.n_in; w += nthreads) {
+        uint64_t z[NP], gz[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            // (canonical shares are below 2^61; the mask keeps a malformed
+            // input from reaching the tag bits)
+            z[i] = ld_cs<F>(a.wv + i * a.ws + w) & F::P;
+            gz[i] = ld_cs<F>(a.wm + i * a.ws + w) & F::P;
+        }
+        df_store<NP>(a.mir, (uint32_t)w, tag, z, gz);
+    }
+    const int32_t tid = 32 * ((int32_t)blockIdx.x + gridDim.x * (threadIdx.x >> 5)) + (threadIdx.x & 31);
+    const bool stamp = a.record_ts && blockIdx.x == 0 && threadIdx.x == 0;
+    if (stamp) a.ds->layer_ts[a.l0] = gtimer();
+    LayerRow L = load_row(a.lay, a.l0);
+    int32_t r = L.s[0] + tid;
+    bool staged = r < L.s[5];
+    if (staged) stage_issue<F, NP>(a, L, r, class_of(L, r), tri_base, st);
+    bool ok = tag != 0;
+    if (!ok && threadIdx.x == 0 && blockIdx.x == 0) atomicOr(&a.ds->err_flags, ERR_TIMEOUT);
+    unsigned int nb = 0;
+    for (int32_t l = a.l0; l < a.l1; ++l) {
+        // testing: first operands after the first layer wait for a tag nobody writes
+        const uint64_t wtag = (a.extra_arrivals && l > a.l0) ? 8u : tag;
+        if (ok) {
+            if (staged) {
+                const int cls = class_of(L, r);
+                cp_async_wait_all();
+                const uint4 rec = st.rec[threadIdx.x];
+                const uint64_t kk = cls >= C_CMUL ? st.k[threadIdx.x] : 0;
+                ok = df_gate<NP>(a, L, r, cls, rec, kk, TriSmem<F, NP>{st.tri + threadIdx.x, st.B}, key, tag, wtag,
+                                 alpha, acc);
+            }
+            for (int32_t q = r + nthreads; ok && q < L.s[5]; q += nthreads) {
+                const int cls = class_of(L, q);
+                GateIn<F, NP> g;
+                gate_load_direct<F, NP>(a, L, q, cls, tri_base, g);
+                ok = df_gate<NP>(a, L, q, cls, g.rec, g.k, TriRegs<F, NP>{g}, key, tag, wtag, alpha, acc);
+            }
+        }
+        staged = false;
+        if (l + 1 < a.l1) {
+            L = load_row(a.lay, l + 1);
+            r = L.s[0] + tid;
+            staged = ok && r < L.s[5];
+            if (staged) stage_issue<F, NP>(a, L, r, class_of(L, r), tri_base, st);
+        }
+        if (l + 1 < a.l1 || a.record_ts) {
+            ++nb;
+            ok = grid_barrier<true>(a.ds, nb * gridDim.x, a.spin_ns) && ok;
+            if (stamp) a.ds->layer_ts[l + 1] = gtimer();
+        }
+    }
+    cp_async_wait_all();
+    block_accumulate<F, NP + 1>(acc, a.ds->acc);
+}
+
+template <int NP> constexpr size_t tagged_smem(int block) {
+    return Stage<F61, NP>::bytes_per_thread() * (size_t)block;
 }
 
 }  // namespace spdz

@@ -10,9 +10,10 @@
 //     per-layer timings the pipeline records itself) and picks group
 //     boundaries and a configuration per group by dynamic programming, with a
 //     measured cost for each extra group (kernel switch).
-// spdz_sched_choose measures the default, autotuned and learned plans and
-// keeps the fastest: the autotuned plan is the learned plan's fallback and
-// the judge of its makespan error.
+// spdz_sched_choose measures the default, autotuned and learned plans (and,
+// for p = 2^61-1, the tagged plan) and keeps the fastest: the
+// autotuned plan is the learned plan's fallback and the judge of its
+// makespan error.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -205,6 +206,7 @@ int sched_predict_config(spdz_ctx *ctx, const spdz_dag *dag, int cfg, std::vecto
     return SPDZ_OK;
 }
 int sched_cluster_config() { return 4; }   // {16, 256, 0}
+int sched_cluster_width() { return kConfigs[sched_cluster_config()].cluster; }
 int sched_grid_config() { return DEFAULT_CFG; }
 double sched_switch_us(spdz_ctx *ctx) { return ctx->sched ? ((Sched *)ctx->sched)->switch_us : 3.0; }
 
@@ -383,6 +385,20 @@ int spdz_sched_choose(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int32
             best = learned;
             best_ms = r.learned_ms;
             r.chosen = 2;
+        }
+    }
+    r.tagged_ms = -1;
+    if (dag->field == SPDZ_F61) {
+        spdz_plan df;
+        memset(&df, 0, sizeof df);
+        df.mode = SPDZ_SCHED_TAGGED;
+        df.block = 256;
+        df.use_graph = 1;
+        if (int rc = measure(ctx, dag, df, wires, reps, &r.tagged_ms)) return rc;
+        if (r.tagged_ms < best_ms) {
+            best = df;
+            best_ms = r.tagged_ms;
+            r.chosen = 3;
         }
     }
     r.samples = (int32_t)s->Y.size();

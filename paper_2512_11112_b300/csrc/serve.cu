@@ -35,6 +35,7 @@ namespace spdz {
 
 int sched_predict_config(spdz_ctx *ctx, const spdz_dag *dag, int cfg, std::vector<double> &us);
 int sched_cluster_config();
+int sched_cluster_width();
 int sched_grid_config();
 double sched_switch_us(spdz_ctx *ctx);
 
@@ -222,6 +223,7 @@ struct spdz_server {
     spdz_ctx *model_ctx = nullptr;  // holds the trained cost model (learned mode)
     Arena arena;
     int sm_count = 0;
+    double hbm_bytes_per_us = 0;    // theoretical DRAM bandwidth (memory clock x bus width)
     cudaStream_t tick_stream = nullptr, deal_stream = nullptr;
     std::vector<cudaStream_t> side;
     DevState *ds_slots = nullptr;   // [max_active]
@@ -351,6 +353,13 @@ int spdz_serve_create(spdz_server **out, int n_parties, uint64_t budget_bytes, i
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    {
+        int khz = 0, bits = 0;
+        cudaDeviceGetAttribute(&khz, cudaDevAttrMemoryClockRate, dev);
+        cudaDeviceGetAttribute(&bits, cudaDevAttrGlobalMemoryBusWidth, dev);
+        // double data rate: 2 transfers per clock
+        s->hbm_bytes_per_us = khz > 0 && bits > 0 ? 2.0 * khz * 1e3 * (bits / 8.0) * 1e-6 : 8e6;
+    }
     if (!s->arena.init((size_t)budget_bytes) ||
         cudaMalloc(&s->ds_slots, sizeof(DevState) * (size_t)s->max_active) != cudaSuccess ||
         cudaMalloc(&s->d_reqs, sizeof(ReqDev) * (size_t)s->max_active) != cudaSuccess ||
@@ -539,7 +548,19 @@ int spdz_serve_run(spdz_server *s, const spdz_serve_request *reqs, int64_t count
                     std::vector<double> pc;
                     if (sched_predict_config(s->model_ctx, &tmp, sched_cluster_config(), pc) == SPDZ_OK &&
                         sched_predict_config(s->model_ctx, &tmp, sched_grid_config(), Cm.pred_grid_us) == SPDZ_OK) {
-                        for (double v : pc) Cm.pred_cluster_us += v;
+                        // a layer in one cluster of k CTAs (one per SM) cannot
+                        // move its bytes faster than k SMs' share of DRAM
+                        // bandwidth: the prediction is clamped to that floor,
+                        // which also bounds the model outside the widths it
+                        // was trained on
+                        const int k = sched_cluster_width();
+                        const double share = s->hbm_bytes_per_us * k / std::max(1, s->sm_count);
+                        const double w = field == SPDZ_F61 ? 8.0 : 16.0;
+                        for (int l = 0; l < L->depth; ++l) {
+                            const int32_t *c = &C.counts[(size_t)l * 5];
+                            const double bytes = n * w * (12.0 * c[0] + 6.0 * (c[1] + c[2]) + 4.0 * (c[3] + c[4]));
+                            Cm.pred_cluster_us += std::max(pc[(size_t)l], bytes / share);
+                        }
                         Cm.predicted = true;
                     }
                 }

@@ -72,7 +72,7 @@ def oracle_run(dag, n, seed, run_index=0, check_seed=7):
     return wv, wm, ok, sigma
 
 
-def plans(depth):
+def plans(depth, p=None):
     mid = max(1, depth // 2)
     out = {
         "per_layer": S.plan(mode=S.SPDZ_SCHED_PER_LAYER, use_graph=0),
@@ -93,6 +93,10 @@ def plans(depth):
                                           group_cluster=[8, 0], flush=[1, 0])
         out["grid_then_cluster_small_block"] = S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=0, block=64,
                                                       groups=[mid, depth], group_cluster=[0, 3])
+    if p == O.P61:
+        out["tagged"] = S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=0)
+        out["tagged_graph"] = S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=1)
+        out["tagged_1cta_small_block"] = S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=0, ctas_per_sm=1, block=32)
     return out
 
 
@@ -107,10 +111,10 @@ SMALL = [
 @pytest.mark.parametrize("p,n,widths", SMALL)
 def test_small_circuits_every_plan_matches_oracle(p, n, widths):
     dag = W.small_dag(seed=len(widths) * 7 + n, p=p, n_inputs=50, widths=widths)
-    n_plans = len(plans(dag.depth))
+    n_plans = len(plans(dag.depth, p))
     dc = DeviceCircuit(dag, n, seed=3, runs=n_plans)
     try:
-        for r, (name, plan) in enumerate(plans(dag.depth).items()):
+        for r, (name, plan) in enumerate(plans(dag.depth, p).items()):
             st, passed, sig = dc.run(plan)
             ev, em, ok, osig = oracle_run(dag, n, seed=3, run_index=r)
             gv, gm = dc.wires.host()
@@ -124,11 +128,12 @@ def test_small_circuits_every_plan_matches_oracle(p, n, widths):
 
 
 def test_benchmark_sized_circuit_matches_oracle():
-    """The 2^20-gate, 32-layer, 3-party p61 circuit: the fused graph run and
-    the per-layer run both equal the oracle on every wire."""
+    """The 2^20-gate, 32-layer, 3-party p61 circuit: the fused graph run, the
+    per-layer run and the tagged graph run all equal the oracle on every
+    wire."""
     dag = W.layered_dag(seed=2)
     n = 3
-    dc = DeviceCircuit(dag, n, seed=2, runs=2)
+    dc = DeviceCircuit(dag, n, seed=2, runs=3)
     try:
         O.set_threads(8)
         ev, em, ok, osig = oracle_run(dag, n, seed=2, run_index=0)
@@ -145,6 +150,67 @@ def test_benchmark_sized_circuit_matches_oracle():
         assert_equal(gm, em1, "per-layer MACs")
         assert passed and ok1
         assert_equal(sig, osig1, "per-layer sigma")
+        ev2, em2, ok2, osig2 = oracle_run(dag, n, seed=2, run_index=2)
+        st, passed, sig = dc.run(S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=1))
+        gv, gm = dc.wires.host()
+        assert_equal(gv, ev2, "tagged values")
+        assert_equal(gm, em2, "tagged MACs")
+        assert passed and ok2
+        assert_equal(sig, osig2, "tagged sigma")
+    finally:
+        dc.close()
+
+
+def test_tagged_runs_cycle_over_many_replays():
+    """Sixteen graph replays of the tagged plan (more than two cycles of the
+    seven run tags, so the tagged wire copy is zeroed twice in between): every
+    run equals the oracle, so no operand of an earlier run is ever taken for
+    the current one."""
+    dag = W.layered_dag(seed=13, total_gates=2**13, depth=10, wmin=32, wmax=2048, n_inputs=512)
+    n = 3
+    R = 16
+    dc = DeviceCircuit(dag, n, seed=6, runs=R)
+    try:
+        plan = S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=1)
+        for r in range(R):
+            # fresh inputs every run: a stale operand would show in the outputs
+            S.spdz_deal_shared(dc.ctx, dc.seed + r, S.SPDZ_KIND_INPUT, INPUT_SUB, 0, dag.n_inputs,
+                               dc.alpha_sh, None, dc.wires.buf())
+            st, passed, sig = dc.run(plan)
+            p = dag.p
+            alpha, ash = O.deal_alpha(p, n, dc.seed)
+            iv, im, _ = O.deal_shared(p, n, dc.seed + r, O.K_INPUT, INPUT_SUB, 0, dag.n_inputs, alpha)
+            wv, wm = O.zeros(p, n, dag.n_wires), O.zeros(p, n, dag.n_wires)
+            wv[:, :dag.n_inputs], wm[:, :dag.n_inputs] = iv, im
+            tri = O.deal_triples(p, n, dc.seed, r * dag.n_mul, dag.n_mul, alpha)
+            _, _, log = O.dag_eval(p, dag, wv, wm, tri, ash)
+            ok, osig, _, _ = O.mac_check(p, [log], ash, 7, r)
+            gv, gm = dc.wires.host()
+            assert_equal(gv, wv, f"replay {r} values")
+            assert_equal(gm, wm, f"replay {r} MACs")
+            assert passed and ok
+            assert_equal(sig, osig, f"replay {r} sigma")
+    finally:
+        dc.close()
+
+
+def test_tagged_plan_rules():
+    """The tagged mode is p61-only, has no layer groups and bounds its poll interval."""
+    dag = W.small_dag(seed=2, p=O.P127, n_inputs=20, widths=[10, 10])
+    dc = DeviceCircuit(dag, 2, seed=2, runs=1)
+    try:
+        with pytest.raises(S.SpdzError) as e:
+            S.spdz_run_dag(dc.ctx, dc.h, S.plan(mode=S.SPDZ_SCHED_TAGGED), dc.wires.buf())
+        assert e.value.code == S.SPDZ_ERR_ARG
+    finally:
+        dc.close()
+    dag = W.small_dag(seed=2, p=O.P61, n_inputs=20, widths=[10, 10])
+    dc = DeviceCircuit(dag, 2, seed=2, runs=1)
+    try:
+        for kw in ({"groups": [1, 2]}, {"poll_ns": 10**6}):
+            with pytest.raises(S.SpdzError) as e:
+                S.spdz_run_dag(dc.ctx, dc.h, S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=0, **kw), dc.wires.buf())
+            assert e.value.code == S.SPDZ_ERR_ARG
     finally:
         dc.close()
 
@@ -172,9 +238,9 @@ def test_graph_replays_consume_fresh_triples():
 
 def test_layer_times_recorded():
     dag = W.layered_dag(seed=4, total_gates=2**15, depth=16, wmin=256, wmax=8192, n_inputs=2048)
-    dc = DeviceCircuit(dag, 3, seed=4, runs=2)
+    dc = DeviceCircuit(dag, 3, seed=4, runs=3)
     try:
-        for mode in (S.SPDZ_SCHED_PER_LAYER, S.SPDZ_SCHED_FUSED):
+        for mode in (S.SPDZ_SCHED_PER_LAYER, S.SPDZ_SCHED_FUSED, S.SPDZ_SCHED_TAGGED):
             st, passed, _ = dc.run(S.plan(mode=mode, use_graph=0, record_layer_times=1))
             t = S.spdz_dag_layer_times(dc.h, dag.depth)
             assert passed and np.all(t > 0) and np.all(t < 1e5)
@@ -199,6 +265,27 @@ def test_barrier_timeout_is_a_status_not_a_hang():
         ev, em, ok, osig = oracle_run(dag, 3, seed=9, run_index=1)
         assert passed and ok
         assert_equal(dc.wires.host()[0], ev, "after timeout")
+    finally:
+        dc.close()
+
+
+def test_tagged_operand_wait_timeout_is_a_status_not_a_hang():
+    """Gates after the first layer wait for a tag that is never written; the
+    bounded operand wait runs out, the run reports SPDZ_ERR_TIMEOUT and does
+    not pass, and the next tagged run on the context is exact."""
+    dag = W.small_dag(seed=10, p=O.P61, n_inputs=64, widths=[200, 100, 50])
+    dc = DeviceCircuit(dag, 3, seed=10, runs=2)
+    try:
+        plan = S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=0, spin_limit_us=2000, barrier_extra_arrivals=1)
+        with pytest.raises(S.SpdzError) as e:
+            S.spdz_run_dag(dc.ctx, dc.h, plan, dc.wires.buf())
+        assert e.value.code == S.SPDZ_ERR_TIMEOUT
+        dc.deal_inputs()
+        st, passed, sig = dc.run(S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=0))
+        ev, em, ok, osig = oracle_run(dag, 3, seed=10, run_index=1)
+        assert passed and ok
+        assert_equal(dc.wires.host()[0], ev, "after timeout")
+        assert_equal(dc.wires.host()[1], em, "after timeout (MACs)")
     finally:
         dc.close()
 
