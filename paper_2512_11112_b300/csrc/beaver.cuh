@@ -22,6 +22,42 @@ __device__ __forceinline__ void beaver_math_src(
     // tri(k, i): triple share k of party i, k = 0..5 for a, gamma(a), b,
     // gamma(b), c, gamma(c)
     using T = typename F::T;
+    if constexpr (F::WORDS == 1) {
+        // p61: every output is one exact sum of at most three 122-bit
+        // products and one or two canonical terms (below 2^124), reduced once
+        T eps = 0, dlt = 0;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            eps = F::add(eps, F::sub(x[i], tri(0, i)));
+            dlt = F::add(dlt, F::sub(y[i], tri(2, i)));
+        }
+        const T de = F::mul(eps, dlt);
+        const T re = Draw<F>::at(key, j), rd = Draw<F>::at(key, j + 1);
+        W61 a0;
+        a0.add(acc[0]);
+        a0.mac(re, eps);
+        a0.mac(rd, dlt);
+        acc[0] = a0.reduce();
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            W61 v, m, c;
+            v.add(tri(4, i));
+            if (i == 0) v.add(de);
+            v.mac(eps, tri(2, i));
+            v.mac(dlt, tri(0, i));
+            z[i] = v.reduce();
+            m.add(tri(5, i));
+            m.mac(eps, tri(3, i));
+            m.mac(dlt, tri(1, i));
+            m.mac(alpha[i], de);
+            gz[i] = m.reduce();
+            c.add(acc[1 + i]);
+            c.mac(re, F::sub(gx[i], tri(1, i)));
+            c.mac(rd, F::sub(gy[i], tri(3, i)));
+            acc[1 + i] = c.reduce();
+        }
+        return;
+    }
     T eps = F::zero(), dlt = F::zero();
 #pragma unroll
     for (int i = 0; i < NP; ++i) {

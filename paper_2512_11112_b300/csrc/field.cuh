@@ -46,6 +46,28 @@ struct F61 {
     __device__ __forceinline__ static void st(T *p, T v) { *p = v; }
 };
 
+// Deferred reduction for p61: a sum of a few 122-bit products (and canonical
+// terms) is kept as an exact 128-bit integer and reduced once.
+struct W61 {
+    uint64_t lo = 0, hi = 0;
+    // += a * b, a and b below 2^61
+    __device__ __forceinline__ void mac(uint64_t a, uint64_t b) {
+        const uint64_t pl = a * b, ph = __umul64hi(a, b);
+        asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(pl), "l"(ph));
+    }
+    __device__ __forceinline__ void add(uint64_t a) {
+        asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(lo), "+l"(hi) : "l"(a));
+    }
+    // the sum mod 2^61 - 1, for a sum below 2^124: two folds with 2^61 == 1
+    // (the first leaves less than 2^61 + 2^63, the second at most p + 4),
+    // then one conditional subtract
+    __device__ __forceinline__ uint64_t reduce() const {
+        uint64_t s = (lo & F61::P) + ((hi << 3) | (lo >> 61));
+        s = (s & F61::P) + (s >> 61);
+        return s >= F61::P ? s - F61::P : s;
+    }
+};
+
 // ----------------------------------------------------------------- p127
 struct u128v {
     uint64_t lo, hi;
