@@ -254,6 +254,10 @@ typedef struct {
     uint32_t poll_ns;                      /* tagged: first sleep between polls of an operand
                                               that is not ready (ns, doubling up to 16x);
                                               0 = 128, at most 50000 */
+    uint32_t barrier_slack;                /* tagged: a CTA starts the next layer once all but
+                                              this many CTAs' arrivals are counted (operands
+                                              still in flight validate by tag); 0 = a full
+                                              barrier, at most the grid size */
 } spdz_plan;
 
 typedef struct {

@@ -14,6 +14,47 @@ namespace spdz {
 // The opened eps (index j) and delta (index j+1) of the check's log add
 // r_j*eps + r_{j+1}*delta to acc[0] and r_j*(gamma(x)_i - gamma(a)_i) +
 // r_{j+1}*(gamma(y)_i - gamma(b)_i) to acc[1+i].
+// p61 form with the check coefficients given (re for eps, rd for delta):
+// every output is one exact sum of at most three 122-bit products and one or
+// two canonical terms (below 2^124), reduced once.
+template <int NP, class TRI>
+__device__ __forceinline__ void beaver_math61(const uint64_t (&x)[NP], const uint64_t (&gx)[NP], const uint64_t (&y)[NP],
+                                              const uint64_t (&gy)[NP], const TRI &tri, const uint64_t (&alpha)[NP],
+                                              uint64_t re, uint64_t rd, uint64_t (&acc)[NP + 1], uint64_t (&z)[NP],
+                                              uint64_t (&gz)[NP]) {
+    using F = F61;
+    uint64_t eps = 0, dlt = 0;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        eps = F::add(eps, F::sub(x[i], tri(0, i)));
+        dlt = F::add(dlt, F::sub(y[i], tri(2, i)));
+    }
+    const uint64_t de = F::mul(eps, dlt);
+    W61 a0;
+    a0.add(acc[0]);
+    a0.mac(re, eps);
+    a0.mac(rd, dlt);
+    acc[0] = a0.reduce();
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        W61 v, m, c;
+        v.add(tri(4, i));
+        if (i == 0) v.add(de);
+        v.mac(eps, tri(2, i));
+        v.mac(dlt, tri(0, i));
+        z[i] = v.reduce();
+        m.add(tri(5, i));
+        m.mac(eps, tri(3, i));
+        m.mac(dlt, tri(1, i));
+        m.mac(alpha[i], de);
+        gz[i] = m.reduce();
+        c.add(acc[1 + i]);
+        c.mac(re, F::sub(gx[i], tri(1, i)));
+        c.mac(rd, F::sub(gy[i], tri(3, i)));
+        acc[1 + i] = c.reduce();
+    }
+}
+
 template <class F, int NP, class TRI>
 __device__ __forceinline__ void beaver_math_src(
     const typename F::T (&x)[NP], const typename F::T (&gx)[NP], const typename F::T (&y)[NP],
@@ -23,39 +64,7 @@ __device__ __forceinline__ void beaver_math_src(
     // gamma(b), c, gamma(c)
     using T = typename F::T;
     if constexpr (F::WORDS == 1) {
-        // p61: every output is one exact sum of at most three 122-bit
-        // products and one or two canonical terms (below 2^124), reduced once
-        T eps = 0, dlt = 0;
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            eps = F::add(eps, F::sub(x[i], tri(0, i)));
-            dlt = F::add(dlt, F::sub(y[i], tri(2, i)));
-        }
-        const T de = F::mul(eps, dlt);
-        const T re = Draw<F>::at(key, j), rd = Draw<F>::at(key, j + 1);
-        W61 a0;
-        a0.add(acc[0]);
-        a0.mac(re, eps);
-        a0.mac(rd, dlt);
-        acc[0] = a0.reduce();
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            W61 v, m, c;
-            v.add(tri(4, i));
-            if (i == 0) v.add(de);
-            v.mac(eps, tri(2, i));
-            v.mac(dlt, tri(0, i));
-            z[i] = v.reduce();
-            m.add(tri(5, i));
-            m.mac(eps, tri(3, i));
-            m.mac(dlt, tri(1, i));
-            m.mac(alpha[i], de);
-            gz[i] = m.reduce();
-            c.add(acc[1 + i]);
-            c.mac(re, F::sub(gx[i], tri(1, i)));
-            c.mac(rd, F::sub(gy[i], tri(3, i)));
-            acc[1 + i] = c.reduce();
-        }
+        beaver_math61<NP>(x, gx, y, gy, tri, alpha, Draw<F>::at(key, j), Draw<F>::at(key, j + 1), acc, z, gz);
         return;
     }
     T eps = F::zero(), dlt = F::zero();

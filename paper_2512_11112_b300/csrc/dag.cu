@@ -131,6 +131,7 @@ static int enqueue_run(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, cons
             a.mir = dag->d_mir;
             a.n_in = dag->n_inputs;
             a.poll_ns = plan.poll_ns ? plan.poll_ns : 128u;
+            a.slack = std::min<uint32_t>(plan.barrier_slack, (uint32_t)grid);
             a.record_ts = layer_events ? 1 : 0;
             a.l0 = 0;
             a.l1 = dag->depth;

@@ -60,6 +60,7 @@ template <class F> struct DagArgs {
     uint64_t *mir;                          // tagged: wire-major copy [wires][2*NP]
     int64_t n_in;                           // tagged: input wires copied into it
     uint32_t poll_ns;                       // tagged: first sleep between operand polls
+    uint32_t slack;                         // tagged: arrivals a layer barrier does not wait for
 };
 
 // Operands of one gate that do not depend on earlier layers: its record,
@@ -508,8 +509,10 @@ __device__ __forceinline__ bool df_gate(const DagArgs<F61> &a, const LayerRow &L
 // words, a third of the sectors of the party-major gathers) and validate
 // them by tag, so the barrier between layers needs no fence: it only keeps
 // the CTAs in step (few operands are still in flight when a layer starts,
-// and their readers re-poll one word).  The inputs are first copied into
-// the tagged copy (one wire per thread, coalesced).
+// and their readers re-poll one word); with a slack it also lets a CTA start
+// a layer before the last few CTAs have finished the one before, whose
+// operands the tags then cover.  The inputs are first copied into the tagged
+// copy (one wire per thread, coalesced).
 template <int NP>
 __global__ void __launch_bounds__(256, 2) k_dag_tagged(DagArgs<F61> a) {
     using F = F61;
@@ -524,6 +527,14 @@ __global__ void __launch_bounds__(256, 2) k_dag_tagged(DagArgs<F61> a) {
 #pragma unroll
     for (int k = 0; k < NP + 1; ++k) acc[k] = 0;
     const int32_t nthreads = gridDim.x * blockDim.x;
+    const int32_t tid = 32 * ((int32_t)blockIdx.x + gridDim.x * (threadIdx.x >> 5)) + (threadIdx.x & 31);
+    const bool stamp = a.record_ts && blockIdx.x == 0 && threadIdx.x == 0;
+    if (stamp) a.ds->layer_ts[a.l0] = gtimer();
+    LayerRow L = load_row(a.lay, a.l0);
+    int32_t r = L.s[0] + tid;
+    bool staged = r < L.s[5];
+    if (staged) stage_issue<F, NP>(a, L, r, class_of(L, r), tri_base, st);
+    // the inputs into the tagged copy (the first layer's staging is in flight)
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < a.n_in; w += nthreads) {
         uint64_t z[NP], gz[NP];
 #pragma unroll
@@ -535,13 +546,6 @@ __global__ void __launch_bounds__(256, 2) k_dag_tagged(DagArgs<F61> a) {
         }
         df_store<NP>(a.mir, (uint32_t)w, tag, z, gz);
     }
-    const int32_t tid = 32 * ((int32_t)blockIdx.x + gridDim.x * (threadIdx.x >> 5)) + (threadIdx.x & 31);
-    const bool stamp = a.record_ts && blockIdx.x == 0 && threadIdx.x == 0;
-    if (stamp) a.ds->layer_ts[a.l0] = gtimer();
-    LayerRow L = load_row(a.lay, a.l0);
-    int32_t r = L.s[0] + tid;
-    bool staged = r < L.s[5];
-    if (staged) stage_issue<F, NP>(a, L, r, class_of(L, r), tri_base, st);
     bool ok = tag != 0;
     if (!ok && threadIdx.x == 0 && blockIdx.x == 0) atomicOr(&a.ds->err_flags, ERR_TIMEOUT);
     unsigned int nb = 0;
@@ -573,7 +577,7 @@ __global__ void __launch_bounds__(256, 2) k_dag_tagged(DagArgs<F61> a) {
         }
         if (l + 1 < a.l1 || a.record_ts) {
             ++nb;
-            ok = grid_barrier<true>(a.ds, nb * gridDim.x, a.spin_ns) && ok;
+            ok = grid_barrier<true>(a.ds, nb * gridDim.x - a.slack, a.spin_ns) && ok;
             if (stamp) a.ds->layer_ts[l + 1] = gtimer();
         }
     }

@@ -394,6 +394,8 @@ int spdz_sched_choose(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int32
         df.mode = SPDZ_SCHED_TAGGED;
         df.block = 256;
         df.use_graph = 1;
+        // a layer starts when all but 1/12 of the CTAs (2 per SM) arrived
+        df.barrier_slack = (uint32_t)(2 * ctx->sm_count / 12);
         if (int rc = measure(ctx, dag, df, wires, reps, &r.tagged_ms)) return rc;
         if (r.tagged_ms < best_ms) {
             best = df;

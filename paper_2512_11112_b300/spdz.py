@@ -58,7 +58,8 @@ class spdz_plan(C.Structure):
                 ("record_layer_times", C.c_int32), ("spin_limit_us", C.c_uint32),
                 ("barrier_extra_arrivals", C.c_int32),
                 ("group_cluster", C.c_int32 * SPDZ_MAX_GROUPS),
-                ("group_block", C.c_int32 * SPDZ_MAX_GROUPS), ("poll_ns", C.c_uint32)]
+                ("group_block", C.c_int32 * SPDZ_MAX_GROUPS), ("poll_ns", C.c_uint32),
+                ("barrier_slack", C.c_uint32)]
 
 
 class spdz_stats(C.Structure):
@@ -279,7 +280,7 @@ def spdz_field_op(ctx, op: int, a, b, out, N: int) -> None:
 def plan(mode: int = SPDZ_SCHED_FUSED, block: int = 256, ctas_per_sm: int = 0, use_graph: int = 1,
          groups=None, flush=None, group_ctas=None, record_layer_times: int = 0,
          spin_limit_us: int = 0, barrier_extra_arrivals: int = 0, group_cluster=None,
-         group_block=None, poll_ns: int = 0) -> spdz_plan:
+         group_block=None, poll_ns: int = 0, barrier_slack: int = 0) -> spdz_plan:
     """Builds a spdz_plan; groups = list of exclusive end layers;
     group_cluster[g] > 0 runs group g inside one cluster of that many CTAs."""
     p = spdz_plan()
@@ -295,6 +296,7 @@ def plan(mode: int = SPDZ_SCHED_FUSED, block: int = 256, ctas_per_sm: int = 0, u
     p.record_layer_times, p.spin_limit_us = record_layer_times, spin_limit_us
     p.barrier_extra_arrivals = barrier_extra_arrivals
     p.poll_ns = poll_ns
+    p.barrier_slack = barrier_slack
     return p
 
 

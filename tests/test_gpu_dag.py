@@ -97,6 +97,9 @@ def plans(depth, p=None):
         out["tagged"] = S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=0)
         out["tagged_graph"] = S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=1)
         out["tagged_1cta_small_block"] = S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=0, ctas_per_sm=1, block=32)
+        out["tagged_slack"] = S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=1, barrier_slack=3)
+        # slack above the grid size: no CTA ever waits at a layer barrier
+        out["tagged_no_wait"] = S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=0, barrier_slack=10**6, poll_ns=32)
     return out
 
 
@@ -151,7 +154,7 @@ def test_benchmark_sized_circuit_matches_oracle():
         assert passed and ok1
         assert_equal(sig, osig1, "per-layer sigma")
         ev2, em2, ok2, osig2 = oracle_run(dag, n, seed=2, run_index=2)
-        st, passed, sig = dc.run(S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=1))
+        st, passed, sig = dc.run(S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=1, barrier_slack=24))
         gv, gm = dc.wires.host()
         assert_equal(gv, ev2, "tagged values")
         assert_equal(gm, em2, "tagged MACs")
@@ -171,7 +174,7 @@ def test_tagged_runs_cycle_over_many_replays():
     R = 16
     dc = DeviceCircuit(dag, n, seed=6, runs=R)
     try:
-        plan = S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=1)
+        plan = S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=1, barrier_slack=4)
         for r in range(R):
             # fresh inputs every run: a stale operand would show in the outputs
             S.spdz_deal_shared(dc.ctx, dc.seed + r, S.SPDZ_KIND_INPUT, INPUT_SUB, 0, dag.n_inputs,
