@@ -746,8 +746,12 @@ def run_profile(args):
     from paper_2512_11112_b300 import spdz as S
     if args.profile in ("dag", "tagged"):
         circ = Circuit(W.layered_dag(seed=2), seed=2, runs=args.steps)
-        mode = S.SPDZ_SCHED_FUSED if args.profile == "dag" else S.SPDZ_SCHED_TAGGED
-        plan = S.plan(mode=mode, use_graph=0)
+        if args.profile == "dag":
+            plan = S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=0)
+        else:
+            # the scheduler's tagged plan: slack of 1/12 of the CTAs (2 per SM)
+            sms = torch.cuda.get_device_properties(0).multi_processor_count
+            plan = S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=0, barrier_slack=2 * sms // 12)
         for _ in range(args.steps):
             circ.run(plan)
         torch.cuda.synchronize()
