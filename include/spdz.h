@@ -7,10 +7,13 @@
  * each party's value shares and MAC shares are separate device rows, so
  * opening a value is an on-device sum over the party rows.
  *
- * Fields: p = 2^61 - 1 (one uint64 per element) and p = 2^127 - 1 (two uint64
- * words per element, low word first, 16-byte aligned).  Every stored share is
- * canonical, in [0, p).  All arithmetic is exact; nothing here changes the
- * protocol's results.
+ * Fields: p = 2^61 - 1 (one uint64 per element), p = 2^127 - 1 (two uint64
+ * words per element, low word first, 16-byte aligned) and p = 2^32 - 5, the
+ * prime of the paper's evaluation (Sec. IV-A; one uint32 per element).  Host
+ * constants passed to the calls use the same element formats.  Every stored
+ * share is canonical, in [0, p).  All arithmetic is exact; nothing here
+ * changes the protocol's results.  Circuits, the tagged plan and matrix
+ * products name the fields they accept.
  *
  * Conventions for every call:
  *   - Returns an int status (SPDZ_OK or one of the SPDZ_ERR_* codes below);
@@ -45,7 +48,7 @@ enum spdz_status {
     SPDZ_ERR_STATE = 8     /* call not valid in the context's current state */
 };
 
-enum spdz_field { SPDZ_F61 = 0, SPDZ_F127 = 1 };
+enum spdz_field { SPDZ_F61 = 0, SPDZ_F127 = 1, SPDZ_F32 = 2 };
 
 /* Gate / linear-operation codes (Sec. II-A.3 addition; Sec. III-B gate set:
  * shl by k lowers to a public-constant multiply by 2^k). */
@@ -419,7 +422,8 @@ int spdz_sched_choose(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int32
 
 /* ------------------------------------------------------------- serving
  * A serving loop over circuit requests (configuration: n parties, mixed
- * fields).  Requests arrive at their arrival times (seconds after the start
+ * fields p = 2^61-1 and p = 2^127-1; other fields are SPDZ_ERR_ARG).
+ * Requests arrive at their arrival times (seconds after the start
  * of spdz_serve_run) and are admitted first come, first served while the
  * device-memory budget (one arena of budget_bytes for every admitted
  * request's wire shares and triples) and max_active slots allow; each

@@ -28,6 +28,7 @@ from . import build as _build
 
 P61 = (1 << 61) - 1
 P127 = (1 << 127) - 1
+P32 = (1 << 32) - 5        # the prime of the paper's evaluation (Sec. IV-A)
 OP_ADD, OP_SUB, OP_CMUL, OP_CADD, OP_MUL = 0, 1, 2, 3, 4
 K_ALPHA, K_TRIPLE_A, K_TRIPLE_B, K_TRIPLE_C, K_INPUT, K_CHECK = 1, 2, 3, 4, 5, 6
 K_MTRIPLE_A, K_MTRIPLE_B, K_MTRIPLE_C = 7, 8, 9

@@ -6,6 +6,8 @@
 // Layout: party-major rows (party i's shares at ptr + i*stride); for p61 a
 // thread moves two consecutive elements with one 128-bit access when every
 // row is 16-byte aligned, for p127 one element per 128-bit access.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace spdz {
@@ -15,7 +17,10 @@ int launch_check(spdz_ctx *ctx, int final_check);
 // ------------------------------------------------------- vector access
 template <class F, int V, bool STREAM>
 __device__ __forceinline__ void vld(const typename F::T *p, typename F::T (&out)[V]) {
-    if constexpr (F::WORDS == 1) {
+    if constexpr (std::is_same_v<F, F32>) {
+        static_assert(V == 1, "p32 moves one element per access");
+        out[0] = STREAM ? __ldcs(p) : *p;
+    } else if constexpr (F::WORDS == 1) {
         if constexpr (V == 2) {
             const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(p);
             ulonglong2 t = STREAM ? __ldcs(q) : *q;
@@ -35,7 +40,9 @@ __device__ __forceinline__ void vld(const typename F::T *p, typename F::T (&out)
 
 template <class F, int V>
 __device__ __forceinline__ void vst(typename F::T *p, const typename F::T (&in)[V]) {
-    if constexpr (F::WORDS == 1) {
+    if constexpr (std::is_same_v<F, F32>) {
+        *p = in[0];
+    } else if constexpr (F::WORDS == 1) {
         if constexpr (V == 2) {
             *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(in[0], in[1]);
         } else {
@@ -295,7 +302,9 @@ __global__ void k_field_op(int op, const typename F::T *x, const typename F::T *
 }
 
 template <class F> static typename F::T host_elem(const void *k) {
-    if constexpr (F::WORDS == 1) {
+    if constexpr (std::is_same_v<F, F32>) {
+        return (uint32_t)*(const uint64_t *)k;
+    } else if constexpr (F::WORDS == 1) {
         return *(const uint64_t *)k;
     } else {
         const uint64_t *w = (const uint64_t *)k;
@@ -304,7 +313,9 @@ template <class F> static typename F::T host_elem(const void *k) {
 }
 
 template <class F> static bool host_canonical(const void *k) {
-    if constexpr (F::WORDS == 1) {
+    if constexpr (std::is_same_v<F, F32>) {
+        return *(const uint64_t *)k < F32::P;
+    } else if constexpr (F::WORDS == 1) {
         return *(const uint64_t *)k < F61::P;
     } else {
         const uint64_t *w = (const uint64_t *)k;
@@ -315,7 +326,7 @@ template <class F> static bool host_canonical(const void *k) {
 
 template <class F, int NP>
 static void launch_linear(spdz_ctx *ctx, const LinArgs<F> &a, bool v2) {
-    if constexpr (F::WORDS == 1) {
+    if constexpr (std::is_same_v<F, F61>) {
         if (v2) {
             auto kern = k_linear<F, NP, 2>;
             kern<<<grid_for(ctx, (const void *)kern, 256, 0, (a.N + 1) / 2), 256, 0, ctx->stream>>>(a);
@@ -328,7 +339,7 @@ static void launch_linear(spdz_ctx *ctx, const LinArgs<F> &a, bool v2) {
 
 template <class F, int NP>
 static void launch_mul(spdz_ctx *ctx, const MulArgs<F> &a, bool v2) {
-    if constexpr (F::WORDS == 1) {
+    if constexpr (std::is_same_v<F, F61>) {
         if (v2) {
             auto kern = k_mul<F, NP, 2>;
             kern<<<grid_for(ctx, (const void *)kern, 256, 0, (a.N + 1) / 2), 256, 0, ctx->stream>>>(a);

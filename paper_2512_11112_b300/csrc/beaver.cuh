@@ -1,6 +1,7 @@
 // beaver.cuh -- the arithmetic of one Beaver product and of the linear gates,
 // on shares already in registers (Sec. II-A.3 of the paper).
 #pragma once
+#include <type_traits>
 #include "common.cuh"
 
 namespace spdz {
@@ -63,7 +64,7 @@ __device__ __forceinline__ void beaver_math_src(
     // tri(k, i): triple share k of party i, k = 0..5 for a, gamma(a), b,
     // gamma(b), c, gamma(c)
     using T = typename F::T;
-    if constexpr (F::WORDS == 1) {
+    if constexpr (std::is_same_v<F, F61>) {
         beaver_math61<NP>(x, gx, y, gy, tri, alpha, Draw<F>::at(key, j), Draw<F>::at(key, j + 1), acc, z, gz);
         return;
     }

@@ -1,6 +1,7 @@
 // common.cuh -- context state, dispatch and reduction helpers shared by the
 // kernels of the SPDZ library.
 #pragma once
+#include <cstring>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
@@ -53,6 +54,9 @@ template <class F> __device__ __forceinline__ typename F::T load_alpha(const Dev
 template <> __device__ __forceinline__ F61::T load_alpha<F61>(const DevState *ds, int i) {
     return ds->alpha[i][0];
 }
+template <> __device__ __forceinline__ F32::T load_alpha<F32>(const DevState *ds, int i) {
+    return (F32::T)ds->alpha[i][0];
+}
 template <> __device__ __forceinline__ F127::T load_alpha<F127>(const DevState *ds, int i) {
     return {ds->alpha[i][0], ds->alpha[i][1]};
 }
@@ -64,6 +68,9 @@ template <> __device__ __forceinline__ F127::T load_alpha<F127>(const DevState *
 __device__ __forceinline__ void acc_add(unsigned long long *acc, F61::T v) {
     unsigned long long old = atomicAdd(&acc[0], (unsigned long long)v);
     if (old + v < old) atomicAdd(&acc[1], 1ull);
+}
+__device__ __forceinline__ void acc_add(unsigned long long *acc, F32::T v) {
+    acc_add(acc, (F61::T)v);
 }
 __device__ __forceinline__ void acc_add(unsigned long long *acc, F127::T v) {
     unsigned long long old0 = atomicAdd(&acc[0], (unsigned long long)v.lo);
@@ -96,7 +103,15 @@ __device__ __forceinline__ F127::T acc_reduce_f127(const unsigned long long *a) 
     F127::T t = {a[2], 0};                             // a2 < 2^64 < p
     return F127::add(v, F127::add(t, t));
 }
+// 2^64 == 25 and 2^128 == 625 (mod 2^32 - 5)
+__device__ __forceinline__ F32::T acc_reduce_f32(const unsigned long long *a) {
+    return F32::add(F32::reduce64(a[0]),
+                    F32::add(F32::mul(F32::reduce64(a[1]), 25u), F32::mul(F32::reduce64(a[2]), 625u)));
+}
 template <class F> __device__ __forceinline__ typename F::T acc_reduce(const unsigned long long *a);
+template <> __device__ __forceinline__ F32::T acc_reduce<F32>(const unsigned long long *a) {
+    return acc_reduce_f32(a);
+}
 template <> __device__ __forceinline__ F61::T acc_reduce<F61>(const unsigned long long *a) {
     return acc_reduce_f61(a);
 }
@@ -108,6 +123,7 @@ template <> __device__ __forceinline__ F127::T acc_reduce<F127>(const unsigned l
 __device__ __forceinline__ F61::T shfl_xor(F61::T v, int m) {
     return __shfl_xor_sync(0xffffffffu, (unsigned long long)v, m);
 }
+__device__ __forceinline__ F32::T shfl_xor(F32::T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 __device__ __forceinline__ F127::T shfl_xor(F127::T v, int m) {
     return {__shfl_xor_sync(0xffffffffu, (unsigned long long)v.lo, m),
             __shfl_xor_sync(0xffffffffu, (unsigned long long)v.hi, m)};
@@ -165,6 +181,9 @@ __device__ __forceinline__ void block_accumulate(typename F::T (&v)[K], unsigned
     if ((f) == SPDZ_F61) {                 \
         using F = spdz::F61;               \
         __VA_ARGS__;                       \
+    } else if ((f) == SPDZ_F32) {          \
+        using F = spdz::F32;               \
+        __VA_ARGS__;                       \
     } else {                               \
         using F = spdz::F127;              \
         __VA_ARGS__;                       \
@@ -194,7 +213,19 @@ struct spdz_ctx {
 
 namespace spdz {
 
-inline size_t elem_bytes(int field) { return field == SPDZ_F61 ? 8 : 16; }
+inline size_t elem_bytes(int field) { return field == SPDZ_F61 ? 8 : field == SPDZ_F32 ? 4 : 16; }
+// Host arrays and constants hold 64-bit words: one per element (p61, p32),
+// two for p127.
+inline size_t host_elem_bytes(int field) { return field == SPDZ_F127 ? 16 : 8; }
+// Copies a host element (64-bit words) into the field's device format.
+inline void host_to_dev_elem(int field, const void *host, void *dev) {
+    if (field == SPDZ_F32) {
+        const uint32_t v = (uint32_t)*(const uint64_t *)host;
+        memcpy(dev, &v, 4);
+    } else {
+        memcpy(dev, host, elem_bytes(field));
+    }
+}
 
 int set_err(spdz_ctx *ctx, int code, const char *fmt, ...);
 int check_cuda(spdz_ctx *ctx, cudaError_t e, const char *what);

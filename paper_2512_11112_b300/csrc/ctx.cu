@@ -122,7 +122,7 @@ int spdz_ctx_create(spdz_ctx **out, int n_parties, int field, void *stream) {
     if (!out) return SPDZ_ERR_ARG;
     *out = nullptr;
     if (n_parties < 2 || n_parties > SPDZ_MAX_PARTIES) return SPDZ_ERR_ARG;
-    if (field != SPDZ_F61 && field != SPDZ_F127) return SPDZ_ERR_ARG;
+    if (field != SPDZ_F61 && field != SPDZ_F127 && field != SPDZ_F32) return SPDZ_ERR_ARG;
     spdz_ctx *ctx = new spdz_ctx();
     ctx->n = n_parties;
     ctx->field = field;
@@ -283,7 +283,7 @@ int spdz_mac_check(spdz_ctx *ctx, int *passed, void *sigma_host) {
     if (sigma_host) {
         uint64_t *s = (uint64_t *)sigma_host;
         for (int i = 0; i < ctx->n; ++i) {
-            if (ctx->field == SPDZ_F61) {
+            if (ctx->field != SPDZ_F127) {
                 s[i] = ctx->hres->res_sigma[i][0];
             } else {
                 s[2 * i] = ctx->hres->res_sigma[i][0];

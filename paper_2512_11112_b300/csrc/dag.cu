@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cstddef>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "dag_kernels.cuh"
@@ -111,7 +112,7 @@ static int enqueue_run(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, cons
         }
         if (layer_events) cudaEventRecord(dag->lev[dag->depth], s);
     } else if (plan.mode == SPDZ_SCHED_TAGGED) {
-        if constexpr (F::WORDS == 1) {
+        if constexpr (std::is_same_v<F, F61>) {
             auto kern = k_dag_tagged<NP>;
             const size_t smem = tagged_smem<NP>(block);
             if (smem > 48 * 1024) {
@@ -330,7 +331,8 @@ int spdz_dag_create(spdz_ctx *ctx, const spdz_dag_desc *d, spdz_dag **out) {
                 }
                 rec[pos] = make_uint4(d->in0[i], binary ? d->in1[i] : d->in0[i], (uint32_t)(d->n_inputs + i), 0u);
                 if (op == SPDZ_OP_CMUL || op == SPDZ_OP_CADD)
-                    memcpy(&kc[pos * eb], (const unsigned char *)d->kconst + (size_t)i * eb, eb);
+                    host_to_dev_elem(ctx->field, (const unsigned char *)d->kconst + (size_t)i * host_elem_bytes(ctx->field),
+                                     &kc[pos * eb]);
                 ++pos;
                 g->counts[(size_t)l * 5 + c]++;
             }
@@ -506,7 +508,7 @@ int spdz_check_result(spdz_ctx *ctx, int *passed, void *sigma_host) {
     if (sigma_host) {
         uint64_t *s = (uint64_t *)sigma_host;
         for (int i = 0; i < ctx->n; ++i) {
-            if (ctx->field == SPDZ_F61) {
+            if (ctx->field != SPDZ_F127) {
                 s[i] = ctx->hres->res_sigma[i][0];
             } else {
                 s[2 * i] = ctx->hres->res_sigma[i][0];

@@ -13,6 +13,7 @@ template <class F> __device__ __forceinline__ typename F::T ld_cg(const typename
 template <> __device__ __forceinline__ F61::T ld_cg<F61>(const F61::T *p) {
     return __ldcg(reinterpret_cast<const unsigned long long *>(p));
 }
+template <> __device__ __forceinline__ F32::T ld_cg<F32>(const F32::T *p) { return __ldcg(p); }
 template <> __device__ __forceinline__ F127::T ld_cg<F127>(const F127::T *p) {
     ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2 *>(p));
     return {v.x, v.y};
@@ -21,6 +22,7 @@ template <class F> __device__ __forceinline__ typename F::T ld_cs(const typename
 template <> __device__ __forceinline__ F61::T ld_cs<F61>(const F61::T *p) {
     return __ldcs(reinterpret_cast<const unsigned long long *>(p));
 }
+template <> __device__ __forceinline__ F32::T ld_cs<F32>(const F32::T *p) { return __ldcs(p); }
 template <> __device__ __forceinline__ F127::T ld_cs<F127>(const F127::T *p) {
     ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2 *>(p));
     return {v.x, v.y};
@@ -142,8 +144,10 @@ __device__ __forceinline__ void cp_async(void *smem, const void *gmem, int bytes
     const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
     if (bytes == 16)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-    else
+    else if (bytes == 8)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }

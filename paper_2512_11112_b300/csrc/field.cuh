@@ -1,10 +1,12 @@
-// field.cuh -- exact arithmetic modulo the Mersenne primes 2^61-1 and 2^127-1.
+// field.cuh -- exact arithmetic modulo the Mersenne primes 2^61-1 and 2^127-1,
+// and modulo 2^32-5 (the prime of the paper's evaluation, Sec. IV-A).
 //
 // Every function takes canonical operands in [0, p) and returns a canonical
-// result.  Products are reduced with the Mersenne identity 2^k == 1 (mod
+// result.  Mersenne products are reduced with the identity 2^k == 1 (mod
 // 2^k - 1): the double-width product is split at bit k and the halves are
-// added, followed by one conditional subtract.  Device products use 64-bit
-// mul.lo / mul.hi (lowered to 32-bit IMAD sequences by the compiler).
+// added, followed by one conditional subtract.  Products mod 2^32-5 use
+// 2^32 == 5 twice.  Device products use 64-bit mul.lo / mul.hi (lowered to
+// 32-bit IMAD sequences by the compiler).
 #pragma once
 #include <cstdint>
 
@@ -41,6 +43,41 @@ struct F61 {
     __host__ __device__ __forceinline__ static T from_draw(uint64_t d) {
         T v = d >> 3;
         return v == P ? 0 : v;
+    }
+    __device__ __forceinline__ static T ld(const T *p) { return *p; }
+    __device__ __forceinline__ static void st(T *p, T v) { *p = v; }
+};
+
+// ------------------------------------------------------------- 2^32 - 5
+// Elements are uint32 words.  (hi:lo) = hi * 2^32 + lo == 5 hi + lo.
+struct F32 {
+    using T = uint32_t;
+    static constexpr int WORDS = 1;
+    static constexpr uint32_t P = 4294967291u;   // 2^32 - 5
+
+    __host__ __device__ __forceinline__ static T zero() { return 0; }
+    __host__ __device__ __forceinline__ static bool is_zero(T a) { return a == 0; }
+    __host__ __device__ __forceinline__ static T add(T a, T b) {
+        const uint64_t s = (uint64_t)a + b;     // < 2p
+        return (T)(s >= P ? s - P : s);
+    }
+    __host__ __device__ __forceinline__ static T sub(T a, T b) {
+        return a >= b ? a - b : (T)((uint64_t)a + P - b);
+    }
+    __host__ __device__ __forceinline__ static T neg(T a) { return a == 0 ? 0 : P - a; }
+    // x < 2^64 -> x mod p: x == 5 * (x >> 32) + (x & (2^32 - 1)) < 2^35,
+    // once more (< 2^32 + 35), then one conditional subtract
+    __host__ __device__ __forceinline__ static T reduce64(uint64_t x) {
+        x = 5ull * (x >> 32) + (x & 0xffffffffull);
+        x = 5ull * (x >> 32) + (x & 0xffffffffull);
+        return (T)(x >= P ? x - P : x);
+    }
+    __host__ __device__ __forceinline__ static T mul(T a, T b) { return reduce64((uint64_t)a * b); }
+    // Field element from a 64-bit PRG word: the top 32 bits, minus p when
+    // they are p or above.
+    __host__ __device__ __forceinline__ static T from_draw(uint64_t d) {
+        const uint32_t v = (uint32_t)(d >> 32);
+        return v >= P ? v - P : v;
     }
     __device__ __forceinline__ static T ld(const T *p) { return *p; }
     __device__ __forceinline__ static void st(T *p, T v) { *p = v; }

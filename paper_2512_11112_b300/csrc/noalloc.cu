@@ -183,7 +183,7 @@ extern "C" int spdz_mul_check_noalloc(int n_parties, int field, void *stream, co
                                       const spdz_buf *y, const spdz_buf *a, const spdz_buf *b,
                                       const spdz_buf *c, const void *alpha_shares_dev, const spdz_buf *z,
                                       int64_t N, uint64_t check_seed, uint64_t epoch, void *result_dev) {
-    if (field != SPDZ_F61 && field != SPDZ_F127) return SPDZ_ERR_ARG;
+    if (field != SPDZ_F61 && field != SPDZ_F127 && field != SPDZ_F32) return SPDZ_ERR_ARG;
     // the scratch holds accumulators for at most SPDZ_MAX_PARTIES parties
     if (n_parties < 2 || n_parties > SPDZ_MAX_PARTIES) return SPDZ_ERR_ARG;
     if (N < 0 || !alpha_shares_dev || !result_dev) return SPDZ_ERR_ARG;

@@ -9,7 +9,8 @@
 // stream = kind << 56 | role << 48 | party << 40 | sub (sub < 2^40).
 // Field elements: p61 takes the top 61 bits of sm64(key, j); p127 takes
 // sm64(key, 2j) as the low word and the top 63 bits of sm64(key, 2j+1) as the
-// high word; the value p itself maps to 0.
+// high word; the value p itself maps to 0.  p = 2^32-5 takes the top 32 bits
+// of sm64(key, j), minus p when they are p or above.
 #pragma once
 #include <cstdint>
 #include "field.cuh"
@@ -44,6 +45,12 @@ template <class F> struct Draw;
 template <> struct Draw<F61> {
     __device__ __forceinline__ static F61::T at(uint64_t key, uint64_t j) {
         return F61::from_draw(sm64(key, j));
+    }
+};
+
+template <> struct Draw<F32> {
+    __device__ __forceinline__ static F32::T at(uint64_t key, uint64_t j) {
+        return F32::from_draw(sm64(key, j));
     }
 };
 

@@ -72,7 +72,7 @@ static void layer_features(const spdz_dag *dag, int l, int cfg, float *f) {
     f[1] = (float)(c[0] / w);
     f[2] = (float)((c[1] + c[2]) / w);
     f[3] = (float)((c[3] + c[4]) / w);
-    f[4] = dag->field == SPDZ_F61 ? 0.f : 1.f;
+    f[4] = dag->field == SPDZ_F127 ? 1.f : dag->field == SPDZ_F32 ? -1.f : 0.f;
     f[5] = (float)((dag->n - 2) / 6.0);
     f[6 + cfg] = 1.f;
 }

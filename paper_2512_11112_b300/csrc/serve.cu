@@ -309,6 +309,8 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // Builds and uploads a circuit once; later requests with the same
 // descriptor share it.
 int prepare_circuit(spdz_server *s, const spdz_dag_desc *d, int field, const ServeCircuit **out) {
+    // the serving loop runs requests of the two Mersenne fields
+    if (field != SPDZ_F61 && field != SPDZ_F127) return SPDZ_ERR_ARG;
     auto cit = s->circuits.find(d);
     if (cit == s->circuits.end()) {
         const size_t eb = field == SPDZ_F61 ? 8 : 16;

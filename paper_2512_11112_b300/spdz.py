@@ -2,7 +2,8 @@
 
 Every function here has the name of the C entry point it wraps and only
 marshals arguments: device buffers are torch tensors (int64 storage holding
-the uint64 words of each field element), host buffers are numpy arrays.  A
+the uint64 words of each field element; int32 storage of the uint32 elements
+of p = 2^32-5), host buffers are numpy arrays.  A
 non-OK status raises :class:`SpdzError` carrying the code and the library's
 message.  There is no fallback: if the CUDA library is missing the import
 fails.
@@ -19,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libspdz.so")
 
 SPDZ_OK, SPDZ_ERR_ARG, SPDZ_ERR_ALIGN, SPDZ_ERR_OOM, SPDZ_ERR_TRIPLES = 0, 1, 2, 3, 4
 SPDZ_ERR_MAC, SPDZ_ERR_TIMEOUT, SPDZ_ERR_CUDA, SPDZ_ERR_STATE = 5, 6, 7, 8
-SPDZ_F61, SPDZ_F127 = 0, 1
+SPDZ_F61, SPDZ_F127, SPDZ_F32 = 0, 1, 2
 SPDZ_OP_ADD, SPDZ_OP_SUB, SPDZ_OP_CMUL, SPDZ_OP_CADD, SPDZ_OP_MUL = 0, 1, 2, 3, 4
 SPDZ_KIND_ALPHA, SPDZ_KIND_TRIPLE_A, SPDZ_KIND_TRIPLE_B, SPDZ_KIND_TRIPLE_C = 1, 2, 3, 4
 SPDZ_KIND_INPUT, SPDZ_KIND_CHECK = 5, 6
@@ -27,6 +28,7 @@ SPDZ_KIND_MTRIPLE_A, SPDZ_KIND_MTRIPLE_B, SPDZ_KIND_MTRIPLE_C = 7, 8, 9
 SPDZ_MAX_PARTIES = 8
 P61 = (1 << 61) - 1
 P127 = (1 << 127) - 1
+P32 = (1 << 32) - 5
 
 
 class SpdzError(RuntimeError):
@@ -186,10 +188,12 @@ def ptr(t) -> int | None:
 
 
 def buf(val, mac, stride: int | None = None, offset: int = 0, words: int = 1) -> spdz_buf:
-    """spdz_buf over party-major tensors [n, stride(, 2)], starting at element offset."""
+    """spdz_buf over party-major tensors [n, stride(, 2)], starting at element offset
+    (the element size is taken from the tensor: int32 words, int64 words, or
+    pairs of int64 words)."""
     if stride is None:
         stride = val.shape[1]
-    eb = 8 * words
+    eb = val.element_size() * (val.shape[2] if val.dim() == 3 else 1)
     return spdz_buf(val.data_ptr() + offset * eb, mac.data_ptr() + offset * eb, stride)
 
 

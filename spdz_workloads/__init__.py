@@ -36,6 +36,7 @@ _M2 = np.uint64(0x94D049BB133111EB)
 
 P61 = (1 << 61) - 1
 P127 = (1 << 127) - 1
+P32 = (1 << 32) - 5
 
 # gate opcodes shared by the circuit format, the C ABI and the oracle
 OP_ADD, OP_SUB, OP_CMUL, OP_CADD, OP_MUL = 0, 1, 2, 3, 4
@@ -126,10 +127,10 @@ def layer_widths(seed: int, total: int, depth: int, wmin: float, wmax: float,
 
 
 def random_constants(seed: int, stream: int, count: int, p: int) -> np.ndarray:
-    """Public constants uniform in [1, p): shape [count] (p61) or [count, 2] (p127)."""
-    if p == P61:
+    """Public constants uniform in [1, p): shape [count] (p61, p32) or [count, 2] (p127)."""
+    if p in (P61, P32):
         d = draws(seed, stream, count)
-        return (np.uint64(1) + d % np.uint64(P61 - 1)).astype(np.uint64)
+        return (np.uint64(1) + d % np.uint64(p - 1)).astype(np.uint64)
     if p == P127:
         d = draws(seed, stream, 2 * count).reshape(count, 2)
         out = d.copy()

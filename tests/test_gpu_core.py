@@ -35,14 +35,15 @@ def _edges(p):
     return [v % p for v in vals]
 
 
-@pytest.mark.parametrize("p", [O.P61, O.P127])
+@pytest.mark.parametrize("p", [O.P61, O.P127, O.P32])
 def test_field_ops_match_python_ints(p):
     ctx = ctx_for(2, p)
     try:
         ev = _edges(p)
         a = [x for x in ev for _ in ev]
         b = [y for _ in ev for y in ev]
-        A, B = SH.from_host(O.to_array(p, a)), SH.from_host(O.to_array(p, b))
+        f = SH.field_of(p)
+        A, B = SH.from_host(O.to_array(p, a), field=f), SH.from_host(O.to_array(p, b), field=f)
         out = torch.zeros_like(A)
         for op, fn in ((S.SPDZ_OP_ADD, lambda x, y: (x + y) % p), (S.SPDZ_OP_SUB, lambda x, y: (x - y) % p),
                        (S.SPDZ_OP_CMUL, lambda x, y: (x * y) % p)):
@@ -54,7 +55,7 @@ def test_field_ops_match_python_ints(p):
         S.spdz_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("p,n", [(O.P61, 2), (O.P61, 3), (O.P127, 3), (O.P61, 5)])
+@pytest.mark.parametrize("p,n", [(O.P61, 2), (O.P61, 3), (O.P127, 3), (O.P61, 5), (O.P32, 3)])
 def test_device_dealer_matches_oracle_dealer(p, n):
     N, T, seed = 1000, 777, 31
     ctx = ctx_for(n, p)
@@ -83,6 +84,8 @@ MUL_CASES = [
     (O.P61, 4, 5003, 0),
     (O.P127, 3, 4099, 0),
     (O.P127, 2, 3, 0),
+    (O.P32, 3, 4097, 0),      # p = 2^32-5, the prime of the paper's evaluation
+    (O.P32, 2, 777, 1),
 ]
 
 
@@ -117,7 +120,7 @@ def test_mul_batch_and_check_match_oracle(p, n, N, off):
         S.spdz_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("p", [O.P61, O.P127])
+@pytest.mark.parametrize("p", [O.P61, O.P127, O.P32])
 def test_two_batches_one_epoch_then_next_epoch(p):
     n, N, seed, chk = 3, 3000, 77, 9
     ctx = ctx_for(n, p)
@@ -151,7 +154,7 @@ def test_two_batches_one_epoch_then_next_epoch(p):
         S.spdz_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("p,n,N,off", [(O.P61, 3, 4097, 0), (O.P61, 2, 999, 1), (O.P127, 3, 513, 0)])
+@pytest.mark.parametrize("p,n,N,off", [(O.P61, 3, 4097, 0), (O.P61, 2, 999, 1), (O.P127, 3, 513, 0), (O.P32, 3, 1025, 1)])
 def test_linear_gates_match_oracle(p, n, N, off):
     seed = 5
     ctx = ctx_for(n, p)
@@ -178,7 +181,7 @@ def test_linear_gates_match_oracle(p, n, N, off):
         S.spdz_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("p,n", [(O.P61, 3), (O.P127, 2)])
+@pytest.mark.parametrize("p,n", [(O.P61, 3), (O.P127, 2), (O.P32, 3)])
 def test_open_and_check_match_oracle(p, n):
     N, seed, chk = 2049, 12, 3
     ctx = ctx_for(n, p)
@@ -198,7 +201,7 @@ def test_open_and_check_match_oracle(p, n):
         S.spdz_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("p,P,L", [(O.P127, 37, 100), (O.P61, 64, 1024), (O.P61, 5, 7)])
+@pytest.mark.parametrize("p,P,L", [(O.P127, 37, 100), (O.P61, 64, 1024), (O.P61, 5, 7), (O.P32, 19, 300)])
 def test_innerprod_matches_oracle(p, P, L):
     n, seed, chk = 3, 8, 5
     ctx = ctx_for(n, p)
@@ -221,7 +224,7 @@ def test_innerprod_matches_oracle(p, P, L):
         S.spdz_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("p", [O.P61, O.P127])
+@pytest.mark.parametrize("p", [O.P61, O.P127, O.P32])
 def test_tampered_share_fails_check_like_oracle(p):
     """A cheating party shifts its share of a by Delta before the multiply:
     the opened eps no longer matches its MACs and the check must fail, with
@@ -234,7 +237,7 @@ def test_tampered_share_fails_check_like_oracle(p):
         av = ow.tri.av.copy()
         old = O.to_ints(p, av[party, j:j + 1])[0]
         av[party, j] = O.to_array(p, [(old + delta) % p])[0]
-        dw.tri[0].val[party, j] = SH.from_host(av[party, j:j + 1])[0]
+        dw.tri[0].val[party, j] = SH.from_host(av[party, j:j + 1], field=dw.field)[0]
         S.spdz_set_check_seed(ctx, chk)
         z = SH.alloc(dw.field, n, N)
         S.spdz_mul_batch(ctx, dw.inputs[0].buf(), dw.inputs[1].buf(), z.buf(), N)

@@ -108,6 +108,7 @@ SMALL = [
     (O.P127, 2, [64, 3, 129, 40]),
     (O.P61, 2, [1]),
     (O.P127, 3, [5, 1000, 77]),
+    (O.P32, 3, [40, 1, 300, 77]),       # p = 2^32-5
 ]
 
 

@@ -19,7 +19,7 @@ import oracle as O
 import spdz_workloads as W
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-PRIMES = [7, 11, 101, (1 << 31) - 1, O.P61, O.P127]
+PRIMES = [7, 11, 101, (1 << 31) - 1, O.P32, O.P61, O.P127]
 
 
 def rec(p, shares):
@@ -67,7 +67,7 @@ def test_splitmix64_published_outputs():
     assert [int(v) for v in got] == [int(v, 16) for _, v in rows]
 
 
-@pytest.mark.parametrize("p", [O.P61, O.P127, 7, 11])
+@pytest.mark.parametrize("p", [O.P61, O.P127, O.P32, 7, 11])
 def test_draw_elements_in_range_and_distinct_streams(p):
     a = ints(p, O.draw(p, 9, O.stream_id(2, 1, 0, 0), 0, 2000))
     b = ints(p, O.draw(p, 9, O.stream_id(2, 1, 1, 0), 0, 2000))
@@ -87,6 +87,16 @@ def test_draw_p61_is_top_61_bits():
         assert g == (0 if v == O.P61 else v)
 
 
+def test_draw_p32_is_top_32_bits_reduced_once():
+    """p = 2^32-5: the top 32 bits of the draw, minus p when they are p or above
+    (the five values 2^32-5 .. 2^32-1 map to 0 .. 4)."""
+    key = O.lib().orc_stream_key(5, O.stream_id(5, 0, 0, 3))
+    got = ints(O.P32, O.draw(O.P32, 5, O.stream_id(5, 0, 0, 3), 0, 200))
+    for j, g in enumerate(got):
+        v = O.sm64(key, j) >> 32
+        assert g == (v - O.P32 if v >= O.P32 else v)
+
+
 def test_draw_p127_two_words():
     key = O.lib().orc_stream_key(5, O.stream_id(5, 0, 0, 3))
     got = ints(O.P127, O.draw(O.P127, 5, O.stream_id(5, 0, 0, 3), 0, 50))
@@ -97,7 +107,7 @@ def test_draw_p127_two_words():
 
 # -------------------------------------------------------------------- dealer
 
-@pytest.mark.parametrize("p,n", [(O.P61, 2), (O.P61, 3), (O.P127, 3), (101, 4)])
+@pytest.mark.parametrize("p,n", [(O.P61, 2), (O.P61, 3), (O.P127, 3), (101, 4), (O.P32, 3)])
 def test_dealer_sharing_and_mac_relation(p, n):
     alpha, ash = O.deal_alpha(p, n, 17)
     al = ints(p, np.array([alpha]))[0]
@@ -114,7 +124,7 @@ def test_dealer_sharing_and_mac_relation(p, n):
     assert np.array_equal(v2, v[:, 100:150]) and np.array_equal(m2, m[:, 100:150])
 
 
-@pytest.mark.parametrize("p,n", [(O.P61, 2), (O.P127, 3), (11, 3)])
+@pytest.mark.parametrize("p,n", [(O.P61, 2), (O.P127, 3), (11, 3), (O.P32, 2)])
 def test_dealer_triples_are_products(p, n):
     alpha, ash = O.deal_alpha(p, n, 3)
     al = ints(p, np.array([alpha]))[0]
@@ -127,7 +137,7 @@ def test_dealer_triples_are_products(p, n):
 
 # ------------------------------------------------------------- linear gates
 
-@pytest.mark.parametrize("p,n", [(O.P61, 3), (O.P127, 3), (101, 2)])
+@pytest.mark.parametrize("p,n", [(O.P61, 3), (O.P127, 3), (101, 2), (O.P32, 3)])
 def test_linear_gates_closed_form(p, n):
     alpha, ash = O.deal_alpha(p, n, 8)
     al = ints(p, np.array([alpha]))[0]
@@ -199,7 +209,7 @@ def test_beaver_brute_force_tiny_field(p, n):
     assert lm == [alpha * v % p for v in lv]
 
 
-@pytest.mark.parametrize("p,n", [(O.P61, 2), (O.P61, 3), (O.P127, 3)])
+@pytest.mark.parametrize("p,n", [(O.P61, 2), (O.P61, 3), (O.P127, 3), (O.P32, 3)])
 def test_beaver_large_field_closed_form(p, n):
     alpha, ash = O.deal_alpha(p, n, 11)
     al = ints(p, np.array([alpha]))[0]
@@ -220,7 +230,7 @@ def test_beaver_large_field_closed_form(p, n):
 
 # ----------------------------------------------------------------- MAC check
 
-@pytest.mark.parametrize("p,n", [(O.P61, 2), (O.P61, 3), (O.P127, 3)])
+@pytest.mark.parametrize("p,n", [(O.P61, 2), (O.P61, 3), (O.P127, 3), (O.P32, 2)])
 def test_mac_check_accepts_honest_and_rejects_tamper(p, n):
     alpha, ash = O.deal_alpha(p, n, 21)
     al = ints(p, np.array([alpha]))[0]
@@ -266,7 +276,7 @@ def test_mac_check_chunks_add_and_epochs_differ():
 
 # ------------------------------------------------------------ inner products
 
-@pytest.mark.parametrize("p", [O.P61, O.P127])
+@pytest.mark.parametrize("p", [O.P61, O.P127, O.P32])
 def test_innerprod_closed_form(p):
     n, P, L = 3, 7, 33
     alpha, ash = O.deal_alpha(p, n, 4)
@@ -322,7 +332,7 @@ def _clear_python(p, dag, inputs):
     return w
 
 
-@pytest.mark.parametrize("p", [O.P61, O.P127])
+@pytest.mark.parametrize("p", [O.P61, O.P127, O.P32])
 def test_dag_shared_equals_cleartext(p):
     n = 3
     dag = W.small_dag(seed=12, p=p, n_inputs=40, widths=[30, 17, 1, 25, 9])

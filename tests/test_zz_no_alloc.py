@@ -13,7 +13,7 @@ import oracle as O
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("p,n,N", [(O.P61, 3, 5003), (O.P127, 2, 777)])
+@pytest.mark.parametrize("p,n,N", [(O.P61, 3, 5003), (O.P127, 2, 777), (O.P32, 3, 999)])
 def test_noalloc_matches_context_path_two_calls(p, n, N):
     if not torch.cuda.is_available():
         pytest.skip("needs a GPU")
