@@ -517,6 +517,42 @@ int spdz_load_matrix_preproc(spdz_ctx *ctx, const spdz_buf *A, const spdz_buf *B
 int spdz_matmul(spdz_ctx *ctx, const spdz_buf *X, const spdz_buf *Y, const spdz_buf *Z, int64_t m, int64_t k,
                 int64_t n, int path, void *E_out_dev, void *F_out_dev);
 
+/* ---------------------------------------------------------- linear layer
+ * The LinearLayer operator y = W x + b (Sec. III-D.3 "Data slicing" and
+ * "MPC-specific optimization"; the workload of the paper's evaluation,
+ * Sec. IV) on a secret-shared dout x din matrix W (row-major in each party
+ * row), din vector x and dout vector b.  W is cut into tiles of tile_rows
+ * consecutive rows (the last tile may be shorter; tile_rows above dout means
+ * one tile), T = ceil(dout / tile_rows).  Tile t consumes one matrix-vector
+ * triple: A_t = its rows of a dout x din matrix A, B_t (din values) and
+ * C_t = A_t B_t (its tile_rows values).  The tile opens E_t = x - B_t and
+ * D_t = W_t - A_t and every party computes
+ *   z_i = C_i + D_t B_{t,i} + A_{t,i} E_t + [i == 0] D_t E_t,
+ *   gamma(z)_i = gamma(C)_i + D_t gamma(B)_{t,i} + gamma(A)_{t,i} E_t + alpha_i D_t E_t,
+ * then y_i = z_i + b_i and gamma(y)_i = gamma(z)_i + gamma(b)_i.  The opened
+ * values join the current check epoch in this order: per tile, E_t (din
+ * values), then D_t row by row.  p = 2^61 - 1 and p = 2^32 - 5 (SPDZ_ERR_ARG
+ * otherwise).
+ * Shapes of the triple buffers: A [n][dout*din], B [n][T*din] (B_t at
+ * t*din), C [n][dout]. */
+/* Dealer for the layer's triples: A and B uniform (kinds MTRIPLE_A/B,
+ * element index = position in A, resp. t*din + k), C_t = A_t B_t (kind
+ * MTRIPLE_C, index = row), each shared with MACs under alpha_shares_dev.
+ * Uses a device workspace of (dout*din + T*din + dout) elements, kept by the
+ * context. */
+int spdz_deal_matvec_triples(spdz_ctx *ctx, uint64_t seed, uint64_t sub, int64_t dout, int64_t din, int64_t tile_rows,
+                             const void *alpha_shares_dev, const spdz_buf *A, const spdz_buf *B, const spdz_buf *C);
+/* Registers the triples (referenced, not copied) for the next
+ * spdz_linear_layer of the same shape and tiling; one layer consumes them. */
+int spdz_load_matvec_preproc(spdz_ctx *ctx, const spdz_buf *A, const spdz_buf *B, const spdz_buf *C, int64_t dout,
+                             int64_t din, int64_t tile_rows);
+/* y = W x + b as above.  D_out_dev (dout*din elements) and E_out_dev (T*din
+ * elements), device, may be NULL: they receive the opened D (row-major) and
+ * E (tile by tile).  SPDZ_ERR_TRIPLES without registered triples of this
+ * shape and tiling. */
+int spdz_linear_layer(spdz_ctx *ctx, const spdz_buf *W, const spdz_buf *x, const spdz_buf *b, const spdz_buf *y,
+                      int64_t dout, int64_t din, int64_t tile_rows, void *D_out_dev, void *E_out_dev);
+
 #ifdef __cplusplus
 }
 #endif

@@ -178,6 +178,20 @@ def deal_matrix_triple(p: int, n: int, seed: int, sub: int, M: int, K: int, N: i
     return Triples(Av, Am, Bv, Bm, Cv, Cm)
 
 
+def deal_matvec_triples(p: int, n: int, seed: int, sub: int, dout: int, din: int, R: int, alpha) -> Triples:
+    """Per-tile matrix-vector triples of a row-tiled linear layer: A [n, dout*din],
+    B [n, T*din], C [n, dout] (C_t = A_t B_t), T = ceil(dout / R)."""
+    al = np.ascontiguousarray(np.asarray(alpha, dtype=np.uint64).reshape(-1))
+    T = -(-dout // R)
+    Av, Am = zeros(p, n, dout * din), zeros(p, n, dout * din)
+    Bv, Bm = zeros(p, n, T * din), zeros(p, n, T * din)
+    Cv, Cm = zeros(p, n, dout), zeros(p, n, dout)
+    lib().orc_deal_matvec_triples(*_pp(p), C.c_int(n), C.c_uint64(seed), C.c_uint64(sub), C.c_int64(dout),
+                                  C.c_int64(din), C.c_int64(R), _ptr(al), _ptr(Av), _ptr(Am), _ptr(Bv),
+                                  _ptr(Bm), _ptr(Cv), _ptr(Cm))
+    return Triples(Av, Am, Bv, Bm, Cv, Cm)
+
+
 # ---------------------------------------------------------------- protocol
 
 def linear(p: int, op: int, xv, xm, yv, ym, k, alpha_sh):
@@ -300,6 +314,46 @@ def mat_entries(p: int, M, K, N, E, F, tri: Triples, alpha_sh, rows, cols):
                           C.c_int64(rows.size), rows.ctypes.data_as(C.POINTER(C.c_int64)),
                           cols.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(Zv), _ptr(Zm))
     return Zv, Zm
+
+
+def linear_layer(p: int, dout: int, din: int, R: int, W, x, b, tri: Triples, alpha_sh, rows=None):
+    """y = W x + b with row tiles of R rows (one matvec triple per tile): the
+    shares (yv, ym) [n, len(rows)] of the listed rows (all rows by default).
+    W, x, b are (values, MACs) pairs of [n, .] arrays."""
+    n = tri.av.shape[0]
+    rows = np.arange(dout, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    yv, ym = zeros(p, n, rows.size), zeros(p, n, rows.size)
+    lib().orc_linear_layer(*_pp(p), C.c_int(n), C.c_int64(dout), C.c_int64(din), C.c_int64(R),
+                           _ptr(W[0]), _ptr(W[1]), _ptr(x[0]), _ptr(x[1]), _ptr(b[0]), _ptr(b[1]),
+                           _ptr(tri.av), _ptr(tri.am), _ptr(tri.bv), _ptr(tri.bm), _ptr(tri.cv), _ptr(tri.cm),
+                           _ptr(alpha_sh), C.c_int64(rows.size), rows.ctypes.data_as(C.POINTER(C.c_int64)),
+                           _ptr(yv), _ptr(ym))
+    return yv, ym
+
+
+def linear_open(p: int, dout: int, din: int, R: int, W, x, tri: Triples) -> OpenLog:
+    """The layer's opened values in log order (per tile: E_t, then D_t row by
+    row) with their MAC shares."""
+    n = tri.av.shape[0]
+    T = -(-dout // R)
+    m = T * din + dout * din
+    vals, macs = zeros(p, m), zeros(p, n, m)
+    lib().orc_linear_open(*_pp(p), C.c_int(n), C.c_int64(dout), C.c_int64(din), C.c_int64(R),
+                          _ptr(W[0]), _ptr(W[1]), _ptr(x[0]), _ptr(x[1]), _ptr(tri.av), _ptr(tri.am),
+                          _ptr(tri.bv), _ptr(tri.bm), _ptr(vals), _ptr(macs))
+    return OpenLog(vals, macs)
+
+
+def linear_rlc(p: int, dout: int, din: int, R: int, W, x, tri: Triples, check_seed: int, epoch: int,
+               j0: int = 0):
+    """(A, S [n]) of the layer's whole log, streamed (the log is not stored)."""
+    n = tri.av.shape[0]
+    A, S = zeros(p, 1), zeros(p, n)
+    lib().orc_linear_rlc(*_pp(p), C.c_int(n), C.c_int64(dout), C.c_int64(din), C.c_int64(R),
+                         _ptr(W[0]), _ptr(W[1]), _ptr(x[0]), _ptr(x[1]), _ptr(tri.av), _ptr(tri.am),
+                         _ptr(tri.bv), _ptr(tri.bm), C.c_uint64(check_seed), C.c_uint64(epoch),
+                         C.c_uint64(j0), _ptr(A), _ptr(S))
+    return A[0], S
 
 
 def dag_eval(p: int, dag, wv, wm, tri: Triples, alpha_sh):

@@ -21,6 +21,8 @@
  *   - Beaver multiplication and the triple identity . Sec. II-A.3 (Multiplication)
  *   - batched MAC check (abort on failure) .......... Sec. II-A.2, II-A.4, III-D.3
  *   - matrix (tile) Beaver triples .................. Sec. III-D.3
+ *   - LinearLayer y = W x + b, row tiles, one
+ *     matrix-vector triple per tile ................ Sec. III-D.3, Sec. IV
  *   - ReduceAdd (horizontal sum, inner products) .... Sec. III-B (vectorization)
  *   - fake preprocessing (dealer) ................... Sec. IV-A
  * The paper gives no formula for the MAC-share updates, for which party adds
@@ -607,6 +609,190 @@ void orc_deal_matrix_triple(u64 plo, u64 phi, int n, u64 seed, u64 sub,
     parallel_for(M * N, matprod_range, &mc);
     orc_deal_shared(plo, phi, n, seed, K_MTRIPLE_C, sub, 0, M * N, alpha, c, Cv, Cm, NULL);
     free(a); free(b); free(c);
+}
+
+/* ------------------------------------------------------------ LinearLayer
+ * y = W x + b (Sec. III-D.3 "Data slicing" and "MPC-specific optimization";
+ * the workload of Sec. IV): W is dout x din, row-major; its rows are cut into
+ * tiles of R consecutive rows (the last tile may be shorter), T = ceil(dout/R).
+ * Tile t has its own triple: A_t = rows of a dout x din matrix A (kind
+ * MTRIPLE_A, element index row*din + col), B_t = din values (kind MTRIPLE_B,
+ * index t*din + k) and C_t = A_t B_t (kind MTRIPLE_C, index = row).  The tile
+ * opens E_t = x - B_t and D_t = W_t - A_t and every party computes
+ *   z_i = C_i + D_t B_{t,i} + A_{t,i} E_t + [i = 0] D_t E_t
+ *   gamma(z)_i = gamma(C)_i + D_t gamma(B)_{t,i} + gamma(A)_{t,i} E_t + alpha_i D_t E_t
+ * and y_i = z_i + b_i (MAC shares likewise).  Opening order of the check log:
+ * for t = 0..T-1, E_t (din values), then D_t row by row.  Shares are [n][.]:
+ * W, A [n][dout*din], x [n][din], b, C, y [n][dout], B [n][T*din]. */
+void orc_deal_matvec_triples(u64 plo, u64 phi, int n, u64 seed, u64 sub, int64_t dout, int64_t din, int64_t R,
+                             const u64 *alpha, u64 *Av, u64 *Am, u64 *Bv, u64 *Bm, u64 *Cv, u64 *Cm) {
+    u128 p = mkp(plo, phi); int w = words_of(p);
+    int64_t T = (dout + R - 1) / R;
+    u64 *a = (u64 *)malloc(sizeof(u64) * (size_t)(dout * din * w));
+    u64 *b = (u64 *)malloc(sizeof(u64) * (size_t)(T * din * w));
+    u64 *c = (u64 *)malloc(sizeof(u64) * (size_t)(dout * w));
+    orc_deal_shared(plo, phi, n, seed, K_MTRIPLE_A, sub, 0, dout * din, alpha, NULL, Av, Am, a);
+    orc_deal_shared(plo, phi, n, seed, K_MTRIPLE_B, sub, 0, T * din, alpha, NULL, Bv, Bm, b);
+    for (int64_t r = 0; r < dout; ++r) {
+        int64_t t = r / R;
+        u128 s = 0;
+        for (int64_t k = 0; k < din; ++k)
+            s = f_add(s, f_mul(ld(a, r * din + k, w), ld(b, t * din + k, w), p), p);
+        st(c, r, w, s);
+    }
+    orc_deal_shared(plo, phi, n, seed, K_MTRIPLE_C, sub, 0, dout, alpha, c, Cv, Cm, NULL);
+    free(a); free(b); free(c);
+}
+
+typedef struct {
+    u128 p; int w, n; int64_t dout, din, R;
+    const u64 *Wv, *Wm, *xv, *xm, *bv, *bm, *Av, *Am, *Bv, *Bm, *Cv, *Cm, *alpha_sh;
+    const int64_t *rows; int64_t nrows;
+    u64 *yv, *ym;                       /* [n][nrows] */
+    u64 check_key; u64 j0;              /* rlc: coefficient key and index of the first opened value */
+    u64 *rowA, *rowS;                   /* rlc partials: [dout], [n][dout] */
+} ll_ctx;
+
+/* E_t[k] (one opened value) and its MAC shares */
+static u128 ll_e(const ll_ctx *c, int64_t t, int64_t k) {
+    u128 e = 0;
+    for (int i = 0; i < c->n; ++i)
+        e = f_add(e, f_sub(ld(c->xv, (int64_t)i * c->din + k, c->w),
+                           ld(c->Bv, (int64_t)i * ((c->dout + c->R - 1) / c->R) * c->din + t * c->din + k, c->w), c->p), c->p);
+    return e;
+}
+static u128 ll_d(const ll_ctx *c, int64_t r, int64_t k) {
+    u128 d = 0;
+    const int64_t q = r * c->din + k, S = c->dout * c->din;
+    for (int i = 0; i < c->n; ++i)
+        d = f_add(d, f_sub(ld(c->Wv, (int64_t)i * S + q, c->w), ld(c->Av, (int64_t)i * S + q, c->w), c->p), c->p);
+    return d;
+}
+
+static void ll_rows_range(void *vc, int64_t lo, int64_t hi) {
+    const ll_ctx *c = (const ll_ctx *)vc;
+    u128 p = c->p; int w = c->w, n = c->n;
+    const int64_t din = c->din, S = c->dout * din, T = (c->dout + c->R - 1) / c->R;
+    for (int64_t q = lo; q < hi; ++q) {
+        const int64_t r = c->rows[q], t = r / c->R;
+        u128 de = 0;
+        for (int64_t k = 0; k < din; ++k) de = f_add(de, f_mul(ll_d(c, r, k), ll_e(c, t, k), p), p);
+        for (int i = 0; i < n; ++i) {
+            u128 z = ld(c->Cv, (int64_t)i * c->dout + r, w), gz = ld(c->Cm, (int64_t)i * c->dout + r, w);
+            for (int64_t k = 0; k < din; ++k) {
+                const u128 d = ll_d(c, r, k), e = ll_e(c, t, k);
+                const int64_t qb = (int64_t)i * T * din + t * din + k, qa = (int64_t)i * S + r * din + k;
+                z = f_add(z, f_add(f_mul(d, ld(c->Bv, qb, w), p), f_mul(ld(c->Av, qa, w), e, p), p), p);
+                gz = f_add(gz, f_add(f_mul(d, ld(c->Bm, qb, w), p), f_mul(ld(c->Am, qa, w), e, p), p), p);
+            }
+            if (i == 0) z = f_add(z, de, p);
+            gz = f_add(gz, f_mul(ld(c->alpha_sh, i, w), de, p), p);
+            z = f_add(z, ld(c->bv, (int64_t)i * c->dout + r, w), p);
+            gz = f_add(gz, ld(c->bm, (int64_t)i * c->dout + r, w), p);
+            st(c->yv, (int64_t)i * c->nrows + q, w, z);
+            st(c->ym, (int64_t)i * c->nrows + q, w, gz);
+        }
+    }
+}
+
+/* y for the listed rows only: yv, ym are [n][nrows]. */
+void orc_linear_layer(u64 plo, u64 phi, int n, int64_t dout, int64_t din, int64_t R,
+                      const u64 *Wv, const u64 *Wm, const u64 *xv, const u64 *xm, const u64 *bv, const u64 *bm,
+                      const u64 *Av, const u64 *Am, const u64 *Bv, const u64 *Bm, const u64 *Cv, const u64 *Cm,
+                      const u64 *alpha_sh, int64_t nrows, const int64_t *rows, u64 *yv, u64 *ym) {
+    ll_ctx c = {0};
+    c.p = mkp(plo, phi); c.w = words_of(c.p); c.n = n; c.dout = dout; c.din = din; c.R = R;
+    c.Wv = Wv; c.Wm = Wm; c.xv = xv; c.xm = xm; c.bv = bv; c.bm = bm;
+    c.Av = Av; c.Am = Am; c.Bv = Bv; c.Bm = Bm; c.Cv = Cv; c.Cm = Cm; c.alpha_sh = alpha_sh;
+    c.rows = rows; c.nrows = nrows; c.yv = yv; c.ym = ym;
+    parallel_for(nrows, ll_rows_range, &c);
+}
+
+/* The opened values in log order with their MAC shares: vals [m], macs
+ * [n][m], m = T*din + dout*din (small layers: the whole log is stored). */
+void orc_linear_open(u64 plo, u64 phi, int n, int64_t dout, int64_t din, int64_t R,
+                     const u64 *Wv, const u64 *Wm, const u64 *xv, const u64 *xm,
+                     const u64 *Av, const u64 *Am, const u64 *Bv, const u64 *Bm, u64 *vals, u64 *macs) {
+    ll_ctx c = {0};
+    c.p = mkp(plo, phi); c.w = words_of(c.p); c.n = n; c.dout = dout; c.din = din; c.R = R;
+    c.Wv = Wv; c.Wm = Wm; c.xv = xv; c.xm = xm; c.Av = Av; c.Am = Am; c.Bv = Bv; c.Bm = Bm;
+    const int64_t T = (dout + R - 1) / R, S = dout * din, m = T * din + S;
+    int w = c.w;
+    int64_t pos = 0;
+    for (int64_t t = 0; t < T; ++t) {
+        for (int64_t k = 0; k < din; ++k, ++pos) {
+            st(vals, pos, w, ll_e(&c, t, k));
+            for (int i = 0; i < n; ++i)
+                st(macs, (int64_t)i * m + pos, w, f_sub(ld(xm, (int64_t)i * din + k, w),
+                                                        ld(Bm, (int64_t)i * T * din + t * din + k, w), c.p));
+        }
+        const int64_t r1 = (t + 1) * R < dout ? (t + 1) * R : dout;
+        for (int64_t r = t * R; r < r1; ++r)
+            for (int64_t k = 0; k < din; ++k, ++pos) {
+                st(vals, pos, w, ll_d(&c, r, k));
+                for (int i = 0; i < n; ++i)
+                    st(macs, (int64_t)i * m + pos, w, f_sub(ld(Wm, (int64_t)i * S + r * din + k, w),
+                                                            ld(Am, (int64_t)i * S + r * din + k, w), c.p));
+            }
+    }
+}
+
+static void ll_rlc_range(void *vc, int64_t lo, int64_t hi) {
+    const ll_ctx *c = (const ll_ctx *)vc;
+    u128 p = c->p; int w = c->w, n = c->n;
+    const int64_t din = c->din, R = c->R, S = c->dout * din, T = (c->dout + R - 1) / R;
+    for (int64_t r = lo; r < hi; ++r) {
+        /* row r of the log: position of D[r][0]; the tile's E precedes its rows */
+        const int64_t t = r / R;
+        const int64_t pos0 = t * (din + R * din) + din + (r - t * R) * din;
+        u128 A = 0, Sv[64];
+        for (int i = 0; i < n; ++i) Sv[i] = 0;
+        for (int64_t k = 0; k < din; ++k) {
+            const u128 rr = draw_elem(c->check_key, c->j0 + (u64)(pos0 + k), p);
+            A = f_add(A, f_mul(rr, ll_d(c, r, k), p), p);
+            for (int i = 0; i < n; ++i)
+                Sv[i] = f_add(Sv[i], f_mul(rr, f_sub(ld(c->Wm, (int64_t)i * S + r * din + k, w),
+                                                     ld(c->Am, (int64_t)i * S + r * din + k, w), p), p), p);
+        }
+        if (r == t * R) {   /* the first row of a tile also carries the tile's E */
+            for (int64_t k = 0; k < din; ++k) {
+                const u128 rr = draw_elem(c->check_key, c->j0 + (u64)(t * (din + R * din) + k), p);
+                A = f_add(A, f_mul(rr, ll_e(c, t, k), p), p);
+                for (int i = 0; i < n; ++i)
+                    Sv[i] = f_add(Sv[i], f_mul(rr, f_sub(ld(c->xm, (int64_t)i * din + k, w),
+                                                         ld(c->Bm, (int64_t)i * T * din + t * din + k, w), p), p), p);
+            }
+        }
+        st(c->rowA, r, w, A);
+        for (int i = 0; i < n; ++i) st(c->rowS, (int64_t)i * c->dout + r, w, Sv[i]);
+    }
+}
+
+/* The check sums of the layer's log without storing it: A = sum r_j v_j and
+ * S_i = sum r_j gamma_i(v_j), with r_j the epoch's coefficient of opened
+ * value j0 + j (j in log order). */
+void orc_linear_rlc(u64 plo, u64 phi, int n, int64_t dout, int64_t din, int64_t R,
+                    const u64 *Wv, const u64 *Wm, const u64 *xv, const u64 *xm,
+                    const u64 *Av, const u64 *Am, const u64 *Bv, const u64 *Bm,
+                    u64 check_seed, u64 epoch, u64 j0, u64 *A_out, u64 *S_out) {
+    ll_ctx c = {0};
+    c.p = mkp(plo, phi); c.w = words_of(c.p); c.n = n; c.dout = dout; c.din = din; c.R = R;
+    c.Wv = Wv; c.Wm = Wm; c.xv = xv; c.xm = xm; c.Av = Av; c.Am = Am; c.Bv = Bv; c.Bm = Bm;
+    c.check_key = orc_stream_key(check_seed, orc_stream_id(K_CHECK, 0, 0, epoch));
+    c.j0 = j0;
+    int w = c.w;
+    c.rowA = (u64 *)malloc(sizeof(u64) * (size_t)(dout * w));
+    c.rowS = (u64 *)malloc(sizeof(u64) * (size_t)(n * dout * w));
+    parallel_for(dout, ll_rlc_range, &c);
+    u128 A = 0, Sv[64];
+    for (int i = 0; i < n; ++i) Sv[i] = 0;
+    for (int64_t r = 0; r < dout; ++r) {
+        A = f_add(A, ld(c.rowA, r, w), c.p);
+        for (int i = 0; i < n; ++i) Sv[i] = f_add(Sv[i], ld(c.rowS, (int64_t)i * dout + r, w), c.p);
+    }
+    st(A_out, 0, w, A);
+    for (int i = 0; i < n; ++i) st(S_out, i, w, Sv[i]);
+    free(c.rowA); free(c.rowS);
 }
 
 /* --------------------------------------------------------------------- DAG

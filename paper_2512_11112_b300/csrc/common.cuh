@@ -209,6 +209,7 @@ struct spdz_ctx {
     std::string err;
     void *sched = nullptr;               // scheduler state (sched.cu)
     void *mat = nullptr;                 // matrix-product state (matmul.cu)
+    void *ll = nullptr;                  // linear-layer state (linear_layer.cu)
 };
 
 namespace spdz {
@@ -235,6 +236,7 @@ bool buf_vec2_ok(const spdz_buf *b);    // 16-byte aligned rows (p61 vector path
 int grid_for(spdz_ctx *ctx, const void *kernel, int block, size_t smem, int64_t work_items);
 void sched_destroy(spdz_ctx *ctx);
 void mat_destroy(spdz_ctx *ctx);
+void ll_destroy(spdz_ctx *ctx);
 void sched_forget(spdz_ctx *ctx, const spdz_dag *dag);
 
 }  // namespace spdz

@@ -155,6 +155,7 @@ int spdz_ctx_destroy(spdz_ctx *ctx) {
     if (ctx->hres) cudaFreeHost(ctx->hres);
     sched_destroy(ctx);
     mat_destroy(ctx);
+    ll_destroy(ctx);
     delete ctx;
     return SPDZ_OK;
 }

@@ -1,0 +1,363 @@
+// linear_layer.cu -- the LinearLayer operator y = W x + b on a secret-shared
+// dout x din matrix W, din vector x and dout vector b (Sec. III-D.3 "Data
+// slicing" and "MPC-specific optimization"; the workload of Sec. IV).
+//
+// W is cut into tiles of R consecutive rows; tile t has its own
+// matrix-vector triple (A_t: its rows of a dout x din matrix A, B_t: din
+// values, C_t = A_t B_t).  The tile opens E_t = x - B_t and D_t = W_t - A_t,
+// and every party computes
+//   z_i = C_i + D_t B_{t,i} + A_{t,i} E_t + [i = 0] D_t E_t,
+//   gamma(z)_i = gamma(C)_i + D_t gamma(B)_{t,i} + gamma(A)_{t,i} E_t + alpha_i D_t E_t,
+// then y_i = z_i + b_i.  On one GPU every party's shares are resident, so the
+// opening of D is fused with the products that use it: one pass reads each
+// share of W and A once (the bytes that bound the operator), forms the
+// opened D element in registers, adds its check terms and feeds the four
+// matrix-vector sums of each party and D E.  E_t (din values per tile) is
+// opened first by a small pass.  Opening order of the check log, from the
+// epoch's current position: per tile, E_t, then D_t row by row.
+#include <algorithm>
+#include <type_traits>
+
+#include "dealer.cuh"
+
+namespace spdz {
+
+struct LLState {
+    spdz_buf A{}, B{}, C{};
+    int64_t dout = 0, din = 0, R = 0;
+    bool loaded = false;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+};
+
+static LLState *ll_of(spdz_ctx *ctx) {
+    if (!ctx->ll) ctx->ll = new LLState();
+    return (LLState *)ctx->ll;
+}
+
+void ll_destroy(spdz_ctx *ctx) {
+    LLState *s = (LLState *)ctx->ll;
+    if (!s) return;
+    if (s->ws) cudaFree(s->ws);
+    delete s;
+    ctx->ll = nullptr;
+}
+
+static int ll_ws(spdz_ctx *ctx, LLState *s, size_t need) {
+    if (need <= s->ws_bytes) return SPDZ_OK;
+    cudaStreamSynchronize(ctx->stream);
+    if (s->ws) cudaFree(s->ws);
+    s->ws = nullptr;
+    s->ws_bytes = 0;
+    if (cudaMalloc(&s->ws, need) != cudaSuccess) return set_err(ctx, SPDZ_ERR_OOM, "linear layer: workspace of %zu bytes", need);
+    s->ws_bytes = need;
+    return SPDZ_OK;
+}
+
+// Streaming (read once) and read-only cached loads of 4- and 8-byte words.
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t *p) { return __ldcs(reinterpret_cast<const unsigned int *>(p)); }
+__device__ __forceinline__ uint64_t ld_stream(const uint64_t *p) {
+    return __ldcs(reinterpret_cast<const unsigned long long *>(p));
+}
+__device__ __forceinline__ uint32_t ld_ro(const uint32_t *p) { return __ldg(reinterpret_cast<const unsigned int *>(p)); }
+__device__ __forceinline__ uint64_t ld_ro(const uint64_t *p) { return __ldg(reinterpret_cast<const unsigned long long *>(p)); }
+
+// ------------------------------------------------- deferred accumulation
+// Sums of products kept unreduced and reduced once.  p = 2^32-5: a 64-bit
+// product folds to 5 hi + lo < 2^35, so 2^29 terms fit a 64-bit sum.  p61:
+// an exact 128-bit sum, reduced into a residue by flush() at most every three
+// products (three 122-bit products stay below 2^124).
+template <class F> struct LAcc;
+template <> struct LAcc<F32> {
+    uint64_t s = 0;
+    __device__ __forceinline__ void mac(uint32_t a, uint32_t b) {
+        const uint64_t x = (uint64_t)a * b;
+        s += 5ull * (x >> 32) + (x & 0xffffffffull);
+    }
+    __device__ __forceinline__ void flush() {}
+    __device__ __forceinline__ uint32_t get() const { return F32::reduce64(s); }
+};
+template <> struct LAcc<F61> {
+    uint64_t res = 0;
+    W61 w;
+    __device__ __forceinline__ void mac(uint64_t a, uint64_t b) { w.mac(a, b); }
+    __device__ __forceinline__ void flush() {
+        res = F61::add(res, w.reduce());
+        w = W61{};
+    }
+    __device__ __forceinline__ uint64_t get() const { return F61::add(res, w.reduce()); }
+};
+template <class F> struct LUnroll { static constexpr int U = 3; };
+template <> struct LUnroll<F32> { static constexpr int U = 4; };
+
+// ------------------------------------------------------------- dealer
+// c[r] = A_t[r] . B_t over the secrets (t = r / R), one warp per row.
+template <class F>
+__global__ void k_tile_matvec(const typename F::T *a, const typename F::T *b, typename F::T *c, int64_t dout,
+                              int64_t din, int64_t R) {
+    using T = typename F::T;
+    constexpr int U = LUnroll<F>::U;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < dout; r += nwarps) {
+        const T *ar = a + r * din, *bt = b + (r / R) * din;
+        LAcc<F> s;
+        for (int64_t k0 = lane; k0 < din; k0 += 32 * U) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t k = k0 + 32 * u;
+                if (k < din) s.mac(ar[k], ld_ro(bt + k));
+            }
+            s.flush();
+        }
+        const T v = warp_sum<F>(s.get());
+        if (lane == 0) F::st(c + r, v);
+    }
+}
+
+// ---------------------------------------------------------- the layer
+// E_j = sum_i (x_i[k] - B_i[j]) for j = t*din + k, with its check terms.
+template <class F, int NP>
+__global__ void __launch_bounds__(256) k_ll_open_e(const typename F::T *xv, const typename F::T *xm, int64_t xs,
+                                                   const typename F::T *bv, const typename F::T *bm, int64_t bs,
+                                                   int64_t T, int64_t din, int64_t R, uint64_t base,
+                                                   typename F::T *E, DevState *ds) {
+    using Tt = typename F::T;
+    const uint64_t key = ds->key;
+    Tt acc[NP + 1];
+#pragma unroll
+    for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < T * din; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = j / din, k = j - t * din;
+        Tt e = F::zero(), g[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            e = F::add(e, F::sub(F::ld(xv + i * xs + k), F::ld(bv + i * bs + j)));
+            g[i] = F::sub(F::ld(xm + i * xs + k), F::ld(bm + i * bs + j));
+        }
+        F::st(E + j, e);
+        const Tt r = Draw<F>::at(key, base + (uint64_t)(t * (din + R * din) + k));
+        acc[0] = F::add(acc[0], F::mul(r, e));
+#pragma unroll
+        for (int i = 0; i < NP; ++i) acc[1 + i] = F::add(acc[1 + i], F::mul(r, g[i]));
+    }
+    block_accumulate<F, NP + 1>(acc, ds->acc);
+}
+
+template <class F> struct LLArgs {
+    using T = typename F::T;
+    const T *wv, *wm;  int64_t ws;        // W   [n][dout*din]
+    const T *av, *am;  int64_t as;        // A   [n][dout*din]
+    const T *bv, *bm;  int64_t bs;        // B   [n][T*din]
+    const T *cv, *cm;  int64_t cs;        // C   [n][dout]
+    const T *pv, *pm;  int64_t ps;        // b (the bias) [n][dout]
+    T *yv, *ym;        int64_t ys;        // y   [n][dout]
+    const T *E;                           // [T*din] opened
+    T *D;                                 // [dout*din] opened (optional)
+    int64_t dout, din, R;
+    uint64_t base;                        // check-log index of the layer's first opened value
+    DevState *ds;
+};
+
+// One warp per row: the row's D elements (opened in registers), their check
+// terms, and the row's sums D.B_i, D.gamma(B)_i, A_i.E, gamma(A)_i.E, D.E.
+template <class F, int NP>
+__global__ void __launch_bounds__(256) k_ll_rows(LLArgs<F> a) {
+    using T = typename F::T;
+    constexpr int U = LUnroll<F>::U;
+    const int lane = threadIdx.x & 31;
+    const uint64_t key = a.ds->key;
+    T alpha[NP], chk[NP + 1];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
+#pragma unroll
+    for (int k = 0; k < NP + 1; ++k) chk[k] = F::zero();
+    const int64_t din = a.din, nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < a.dout; r += nwarps) {
+        const int64_t t = r / a.R;
+        const uint64_t pos0 = a.base + (uint64_t)(t * (din + a.R * din) + din + (r - t * a.R) * din);
+        const int64_t row = r * din;
+        const T *Et = a.E + t * din;
+        LAcc<F> db[NP], dgb[NP], ae[NP], gae[NP], de, c0, ci[NP];
+        for (int64_t k0 = lane; k0 < din; k0 += 32 * U) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t k = k0 + 32 * u;
+                if (k < din) {
+                    T d = F::zero(), av[NP], gav[NP];
+#pragma unroll
+                    for (int i = 0; i < NP; ++i) {
+                        const T w = ld_stream(a.wv + i * a.ws + row + k);
+                        av[i] = ld_stream(a.av + i * a.as + row + k);
+                        d = F::add(d, F::sub(w, av[i]));
+                    }
+                    const T e = ld_ro(Et + k);
+                    const T rr = Draw<F>::at(key, pos0 + (uint64_t)k);
+                    c0.mac(rr, d);
+                    de.mac(d, e);
+#pragma unroll
+                    for (int i = 0; i < NP; ++i) {
+                        gav[i] = ld_stream(a.am + i * a.as + row + k);
+                        const T gw = ld_stream(a.wm + i * a.ws + row + k);
+                        ci[i].mac(rr, F::sub(gw, gav[i]));
+                        const int64_t q = i * a.bs + t * din + k;
+                        db[i].mac(d, ld_ro(a.bv + q));
+                        dgb[i].mac(d, ld_ro(a.bm + q));
+                        ae[i].mac(av[i], e);
+                        gae[i].mac(gav[i], e);
+                    }
+                    if (a.D) F::st(a.D + row + k, d);
+                }
+            }
+            c0.flush();
+            de.flush();
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                db[i].flush();
+                dgb[i].flush();
+                ae[i].flush();
+                gae[i].flush();
+                ci[i].flush();
+            }
+        }
+        chk[0] = F::add(chk[0], c0.get());
+#pragma unroll
+        for (int i = 0; i < NP; ++i) chk[1 + i] = F::add(chk[1 + i], ci[i].get());
+        const T sde = warp_sum<F>(de.get());
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            const T z = warp_sum<F>(F::add(db[i].get(), ae[i].get()));
+            const T gz = warp_sum<F>(F::add(dgb[i].get(), gae[i].get()));
+            if (lane == 0) {
+                T y = F::add(F::add(F::ld(a.cv + i * a.cs + r), z), F::ld(a.pv + i * a.ps + r));
+                if (i == 0) y = F::add(y, sde);
+                T gy = F::add(F::add(F::ld(a.cm + i * a.cs + r), gz), F::ld(a.pm + i * a.ps + r));
+                gy = F::add(gy, F::mul(alpha[i], sde));
+                F::st(a.yv + i * a.ys + r, y);
+                F::st(a.ym + i * a.ys + r, gy);
+            }
+        }
+    }
+    block_accumulate<F, NP + 1>(chk, a.ds->acc);
+}
+
+template <class F, int NP>
+static void deal_matvec(spdz_ctx *ctx, LLState *s, uint64_t seed, uint64_t sub, int64_t dout, int64_t din, int64_t R,
+                        const void *alpha_shares_dev, const spdz_buf *A, const spdz_buf *B, const spdz_buf *C) {
+    if constexpr (!std::is_same_v<F, F127>) {
+        using Tt = typename F::T;
+        const int64_t T = (dout + R - 1) / R;
+        Tt *sa = (Tt *)s->ws, *sb = sa + dout * din, *sc = sb + T * din;
+        const Tt *al = (const Tt *)alpha_shares_dev;
+        auto kern = k_deal_shared<F, NP>;
+        auto ka = make_keys<NP>(seed, SPDZ_KIND_MTRIPLE_A, sub);
+        auto kb = make_keys<NP>(seed, SPDZ_KIND_MTRIPLE_B, sub);
+        auto kc = make_keys<NP>(seed, SPDZ_KIND_MTRIPLE_C, sub);
+        kern<<<grid_for(ctx, (const void *)kern, 256, 0, dout * din), 256, 0, ctx->stream>>>(
+            ka, 0, dout * din, al, nullptr, (Tt *)A->val, (Tt *)A->mac, A->stride, sa);
+        kern<<<grid_for(ctx, (const void *)kern, 256, 0, T * din), 256, 0, ctx->stream>>>(
+            kb, 0, T * din, al, nullptr, (Tt *)B->val, (Tt *)B->mac, B->stride, sb);
+        auto km = k_tile_matvec<F>;
+        km<<<grid_for(ctx, (const void *)km, 256, 0, dout * 32), 256, 0, ctx->stream>>>(sa, sb, sc, dout, din, R);
+        kern<<<grid_for(ctx, (const void *)kern, 256, 0, dout), 256, 0, ctx->stream>>>(
+            kc, 0, dout, al, sc, (Tt *)C->val, (Tt *)C->mac, C->stride, nullptr);
+    }
+}
+
+template <class F, int NP>
+static void launch_ll(spdz_ctx *ctx, LLState *s, const spdz_buf *W, const spdz_buf *x, const spdz_buf *b,
+                      const spdz_buf *y, int64_t dout, int64_t din, int64_t R, int64_t T, uint64_t base,
+                      void *D_out_dev, void *E_out_dev) {
+    if constexpr (!std::is_same_v<F, F127>) {
+        using Tt = typename F::T;
+        Tt *E = E_out_dev ? (Tt *)E_out_dev : (Tt *)s->ws;
+        auto ke = k_ll_open_e<F, NP>;
+        ke<<<grid_for(ctx, (const void *)ke, 256, 0, T * din), 256, 0, ctx->stream>>>(
+            (const Tt *)x->val, (const Tt *)x->mac, x->stride, (const Tt *)s->B.val, (const Tt *)s->B.mac,
+            s->B.stride, T, din, R, base, E, ctx->ds);
+        LLArgs<F> a{};
+        a.wv = (const Tt *)W->val; a.wm = (const Tt *)W->mac; a.ws = W->stride;
+        a.av = (const Tt *)s->A.val; a.am = (const Tt *)s->A.mac; a.as = s->A.stride;
+        a.bv = (const Tt *)s->B.val; a.bm = (const Tt *)s->B.mac; a.bs = s->B.stride;
+        a.cv = (const Tt *)s->C.val; a.cm = (const Tt *)s->C.mac; a.cs = s->C.stride;
+        a.pv = (const Tt *)b->val; a.pm = (const Tt *)b->mac; a.ps = b->stride;
+        a.yv = (Tt *)y->val; a.ym = (Tt *)y->mac; a.ys = y->stride;
+        a.E = E;
+        a.D = (Tt *)D_out_dev;
+        a.dout = dout; a.din = din; a.R = R;
+        a.base = base;
+        a.ds = ctx->ds;
+        auto kr = k_ll_rows<F, NP>;
+        kr<<<grid_for(ctx, (const void *)kr, 256, 0, dout * 32), 256, 0, ctx->stream>>>(a);
+    }
+}
+
+}  // namespace spdz
+
+using namespace spdz;
+
+extern "C" {
+
+int spdz_deal_matvec_triples(spdz_ctx *ctx, uint64_t seed, uint64_t sub, int64_t dout, int64_t din, int64_t tile_rows,
+                             const void *alpha_shares_dev, const spdz_buf *A, const spdz_buf *B, const spdz_buf *C) {
+    if (!ctx || !alpha_shares_dev || dout <= 0 || din <= 0 || tile_rows <= 0)
+        return set_err(ctx, SPDZ_ERR_ARG, "deal_matvec_triples: bad argument");
+    if (ctx->field == SPDZ_F127) return set_err(ctx, SPDZ_ERR_ARG, "deal_matvec_triples: p = 2^61-1 or 2^32-5 only");
+    const int64_t R = std::min(tile_rows, dout), T = (dout + R - 1) / R;
+    int rc;
+    if ((rc = validate_buf(ctx, A, dout * din, "A")) || (rc = validate_buf(ctx, B, T * din, "B")) ||
+        (rc = validate_buf(ctx, C, dout, "C")))
+        return rc;
+    LLState *s = ll_of(ctx);
+    const size_t eb = elem_bytes(ctx->field);
+    if ((rc = ll_ws(ctx, s, eb * (size_t)(dout * din + T * din + dout)))) return rc;
+    SPDZ_FIELD_SWITCH(ctx->field, SPDZ_NP_SWITCH(ctx->n, (deal_matvec<F, NP>(ctx, s, seed, sub, dout, din, R, alpha_shares_dev, A, B, C))));
+    return check_launch(ctx, "deal_matvec_triples");
+}
+
+int spdz_load_matvec_preproc(spdz_ctx *ctx, const spdz_buf *A, const spdz_buf *B, const spdz_buf *C, int64_t dout,
+                             int64_t din, int64_t tile_rows) {
+    if (!ctx || dout <= 0 || din <= 0 || tile_rows <= 0) return set_err(ctx, SPDZ_ERR_ARG, "load_matvec_preproc: bad sizes");
+    const int64_t R = std::min(tile_rows, dout), T = (dout + R - 1) / R;
+    int rc;
+    if ((rc = validate_buf(ctx, A, dout * din, "A")) || (rc = validate_buf(ctx, B, T * din, "B")) ||
+        (rc = validate_buf(ctx, C, dout, "C")))
+        return rc;
+    LLState *s = ll_of(ctx);
+    s->A = *A;
+    s->B = *B;
+    s->C = *C;
+    s->dout = dout;
+    s->din = din;
+    s->R = R;
+    s->loaded = true;
+    return SPDZ_OK;
+}
+
+int spdz_linear_layer(spdz_ctx *ctx, const spdz_buf *W, const spdz_buf *x, const spdz_buf *b, const spdz_buf *y,
+                      int64_t dout, int64_t din, int64_t tile_rows, void *D_out_dev, void *E_out_dev) {
+    if (!ctx || dout <= 0 || din <= 0 || tile_rows <= 0) return set_err(ctx, SPDZ_ERR_ARG, "linear_layer: bad sizes");
+    if (ctx->field == SPDZ_F127) return set_err(ctx, SPDZ_ERR_ARG, "linear_layer: p = 2^61-1 or 2^32-5 only");
+    if (!ctx->alpha_loaded) return set_err(ctx, SPDZ_ERR_STATE, "linear_layer: preprocessing not loaded");
+    const int64_t R = std::min(tile_rows, dout), T = (dout + R - 1) / R;
+    LLState *s = ll_of(ctx);
+    if (!s->loaded || s->dout != dout || s->din != din || s->R != R)
+        return set_err(ctx, SPDZ_ERR_TRIPLES, "linear_layer: no unused %lld x %lld matrix-vector triples with %lld-row tiles",
+                       (long long)dout, (long long)din, (long long)R);
+    int rc;
+    if ((rc = validate_buf(ctx, W, dout * din, "W")) || (rc = validate_buf(ctx, x, din, "x")) ||
+        (rc = validate_buf(ctx, b, dout, "b")) || (rc = validate_buf(ctx, y, dout, "y")))
+        return rc;
+    const size_t eb = elem_bytes(ctx->field);
+    if ((D_out_dev && (uintptr_t)D_out_dev % eb) || (E_out_dev && (uintptr_t)E_out_dev % eb))
+        return set_err(ctx, SPDZ_ERR_ALIGN, "linear_layer: misaligned D or E output");
+    if (!E_out_dev && (rc = ll_ws(ctx, s, eb * (size_t)(T * din)))) return rc;
+    s->loaded = false;   // the triples are consumed
+    const uint64_t base = (uint64_t)ctx->opened;
+    SPDZ_FIELD_SWITCH(ctx->field, SPDZ_NP_SWITCH(ctx->n, (launch_ll<F, NP>(ctx, s, W, x, b, y, dout, din, R, T, base, D_out_dev, E_out_dev))));
+    if ((rc = check_launch(ctx, "linear_layer"))) return rc;
+    ctx->opened += T * din + dout * din;
+    return SPDZ_OK;
+}
+
+}  // extern "C"

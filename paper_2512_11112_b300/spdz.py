@@ -157,6 +157,9 @@ _SIGS = {
     "spdz_load_matrix_preproc": [_vp, _bufp, _bufp, _bufp, _i64, _i64, _i64],
     "spdz_matmul": [_vp, _bufp, _bufp, _bufp, _i64, _i64, _i64, _int, _vp, _vp],
     "spdz_serve_set_mode": [_vp, C.c_int32, _vp, _i64],
+    "spdz_deal_matvec_triples": [_vp, _u64, _u64, _i64, _i64, _i64, _vp, _bufp, _bufp, _bufp],
+    "spdz_load_matvec_preproc": [_vp, _bufp, _bufp, _bufp, _i64, _i64, _i64],
+    "spdz_linear_layer": [_vp, _bufp, _bufp, _bufp, _bufp, _i64, _i64, _i64, _vp, _vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
@@ -569,3 +572,21 @@ def spdz_load_matrix_preproc(ctx, A: spdz_buf, B: spdz_buf, Cb: spdz_buf, m: int
 def spdz_matmul(ctx, X: spdz_buf, Y: spdz_buf, Z: spdz_buf, m: int, k: int, n: int, path: int,
                 E_out=None, F_out=None) -> None:
     _chk(ctx, lib.spdz_matmul(ctx, C.byref(X), C.byref(Y), C.byref(Z), m, k, n, path, ptr(E_out), ptr(F_out)))
+
+
+# ------------------------------------------------------------ linear layer
+
+def spdz_deal_matvec_triples(ctx, seed: int, sub: int, dout: int, din: int, tile_rows: int, alpha_shares,
+                             A: spdz_buf, B: spdz_buf, Cb: spdz_buf) -> None:
+    _chk(ctx, lib.spdz_deal_matvec_triples(ctx, seed, sub, dout, din, tile_rows, ptr(alpha_shares), C.byref(A),
+                                           C.byref(B), C.byref(Cb)))
+
+
+def spdz_load_matvec_preproc(ctx, A: spdz_buf, B: spdz_buf, Cb: spdz_buf, dout: int, din: int, tile_rows: int) -> None:
+    _chk(ctx, lib.spdz_load_matvec_preproc(ctx, C.byref(A), C.byref(B), C.byref(Cb), dout, din, tile_rows))
+
+
+def spdz_linear_layer(ctx, W: spdz_buf, x: spdz_buf, b: spdz_buf, y: spdz_buf, dout: int, din: int, tile_rows: int,
+                      D_out=None, E_out=None) -> None:
+    _chk(ctx, lib.spdz_linear_layer(ctx, C.byref(W), C.byref(x), C.byref(b), C.byref(y), dout, din, tile_rows,
+                                    ptr(D_out), ptr(E_out)))
