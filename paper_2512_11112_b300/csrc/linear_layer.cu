@@ -65,8 +65,8 @@ __device__ __forceinline__ uint64_t ld_ro(const uint64_t *p) { return __ldg(rein
 // ------------------------------------------------- deferred accumulation
 // Sums of products kept unreduced and reduced once.  p = 2^32-5: a 64-bit
 // product folds to 5 hi + lo < 2^35, so 2^29 terms fit a 64-bit sum.  p61:
-// an exact 128-bit sum, reduced into a residue by flush() at most every three
-// products (three 122-bit products stay below 2^124).
+// an exact 128-bit sum, folded back to its residue by flush() at most every
+// three products (a residue and three 122-bit products stay below 2^124).
 template <class F> struct LAcc;
 template <> struct LAcc<F32> {
     uint64_t s = 0;
@@ -78,14 +78,13 @@ template <> struct LAcc<F32> {
     __device__ __forceinline__ uint32_t get() const { return F32::reduce64(s); }
 };
 template <> struct LAcc<F61> {
-    uint64_t res = 0;
-    W61 w;
+    W61 w;    // after flush(): the residue so far, below 2^61
     __device__ __forceinline__ void mac(uint64_t a, uint64_t b) { w.mac(a, b); }
     __device__ __forceinline__ void flush() {
-        res = F61::add(res, w.reduce());
-        w = W61{};
+        w.lo = w.reduce();
+        w.hi = 0;
     }
-    __device__ __forceinline__ uint64_t get() const { return F61::add(res, w.reduce()); }
+    __device__ __forceinline__ uint64_t get() const { return w.reduce(); }
 };
 template <class F> struct LUnroll { static constexpr int U = 3; };
 template <> struct LUnroll<F32> { static constexpr int U = 4; };
@@ -160,7 +159,8 @@ template <class F> struct LLArgs {
 };
 
 // One warp per row: the row's D elements (opened in registers), their check
-// terms, and the row's sums D.B_i, D.gamma(B)_i, A_i.E, gamma(A)_i.E, D.E.
+// terms, and the row's sums D.B_i, D.gamma(B)_i, A_i.E, gamma(A)_i.E, D.E
+// (element loads; used when the rows are not 16-byte aligned).
 template <class F, int NP>
 __global__ void __launch_bounds__(256) k_ll_rows(LLArgs<F> a) {
     using T = typename F::T;
@@ -241,6 +241,144 @@ __global__ void __launch_bounds__(256) k_ll_rows(LLArgs<F> a) {
     block_accumulate<F, NP + 1>(chk, a.ds->acc);
 }
 
+// 16-byte vector of V elements (p = 2^32-5: 4, p61: 2).
+template <class F> struct Vec16;
+template <> struct Vec16<F32> {
+    static constexpr int V = 4;
+    __device__ __forceinline__ static void ld(const uint32_t *p, uint32_t (&o)[4], bool stream) {
+        const uint4 *q = reinterpret_cast<const uint4 *>(p);
+        const uint4 t = stream ? __ldcs(q) : __ldg(q);
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    }
+};
+template <> struct Vec16<F61> {
+    static constexpr int V = 2;
+    __device__ __forceinline__ static void ld(const uint64_t *p, uint64_t (&o)[2], bool stream) {
+        const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(p);
+        const ulonglong2 t = stream ? __ldcs(q) : __ldg(q);
+        o[0] = t.x; o[1] = t.y;
+    }
+};
+
+// The row kernel with 16-byte loads (din a multiple of V, every row and
+// party row 16-byte aligned): each lane takes V consecutive columns per
+// step.  Per step, a first pass over the parties reads W_i, A_i and their
+// MACs and does everything that does not need the opened D (A_i E,
+// gamma(A)_i E, the check terms r (gamma(W)_i - gamma(A)_i), and the sum
+// forming D); a second pass reads B_i and gamma(B)_i for D B_i and
+// D gamma(B)_i.
+template <class F, int NP>
+__global__ void __launch_bounds__(256) k_ll_rows_vec(LLArgs<F> a) {
+    using T = typename F::T;
+    constexpr int V = Vec16<F>::V;
+    const int lane = threadIdx.x & 31;
+    const uint64_t key = a.ds->key;
+    T alpha[NP], chk[NP + 1];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
+#pragma unroll
+    for (int k = 0; k < NP + 1; ++k) chk[k] = F::zero();
+    const int64_t din = a.din, nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < a.dout; r += nwarps) {
+        const int64_t t = r / a.R;
+        const uint64_t pos0 = a.base + (uint64_t)(t * (din + a.R * din) + din + (r - t * a.R) * din);
+        const int64_t row = r * din;
+        const T *Et = a.E + t * din;
+        LAcc<F> db[NP], dgb[NP], ae[NP], gae[NP], de, c0, ci[NP];
+        for (int64_t k = (int64_t)lane * V; k < din; k += 32 * V) {
+            T e[V], d[V], rr[V];
+            Vec16<F>::ld(Et + k, e, false);
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                d[j] = F::zero();
+                rr[j] = Draw<F>::at(key, pos0 + (uint64_t)(k + j));
+            }
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                T w[V], av[V], gw[V], ga[V];
+                Vec16<F>::ld(a.wv + i * a.ws + row + k, w, true);
+                Vec16<F>::ld(a.av + i * a.as + row + k, av, true);
+                Vec16<F>::ld(a.wm + i * a.ws + row + k, gw, true);
+                Vec16<F>::ld(a.am + i * a.as + row + k, ga, true);
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    d[j] = F::add(d[j], F::sub(w[j], av[j]));
+                    ae[i].mac(av[j], e[j]);
+                    gae[i].mac(ga[j], e[j]);
+                    ci[i].mac(rr[j], F::sub(gw[j], ga[j]));
+                    if (j == 2) {          // at most three products between folds
+                        ae[i].flush();
+                        gae[i].flush();
+                        ci[i].flush();
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                c0.mac(rr[j], d[j]);
+                de.mac(d[j], e[j]);
+                if (j == 2) {
+                    c0.flush();
+                    de.flush();
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                T bv[V], gb[V];
+                const int64_t q = i * a.bs + t * din + k;
+                Vec16<F>::ld(a.bv + q, bv, false);
+                Vec16<F>::ld(a.bm + q, gb, false);
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    db[i].mac(d[j], bv[j]);
+                    dgb[i].mac(d[j], gb[j]);
+                    if (j == 2) {
+                        db[i].flush();
+                        dgb[i].flush();
+                    }
+                }
+                ae[i].flush();
+                gae[i].flush();
+                ci[i].flush();
+                db[i].flush();
+                dgb[i].flush();
+            }
+            c0.flush();
+            de.flush();
+            if (a.D) {
+#pragma unroll
+                for (int j = 0; j < V; ++j) F::st(a.D + row + k + j, d[j]);
+            }
+        }
+        chk[0] = F::add(chk[0], c0.get());
+#pragma unroll
+        for (int i = 0; i < NP; ++i) chk[1 + i] = F::add(chk[1 + i], ci[i].get());
+        const T sde = warp_sum<F>(de.get());
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            const T z = warp_sum<F>(F::add(db[i].get(), ae[i].get()));
+            const T gz = warp_sum<F>(F::add(dgb[i].get(), gae[i].get()));
+            if (lane == 0) {
+                T y = F::add(F::add(F::ld(a.cv + i * a.cs + r), z), F::ld(a.pv + i * a.ps + r));
+                if (i == 0) y = F::add(y, sde);
+                T gy = F::add(F::add(F::ld(a.cm + i * a.cs + r), gz), F::ld(a.pm + i * a.ps + r));
+                gy = F::add(gy, F::mul(alpha[i], sde));
+                F::st(a.yv + i * a.ys + r, y);
+                F::st(a.ym + i * a.ys + r, gy);
+            }
+        }
+    }
+    block_accumulate<F, NP + 1>(chk, a.ds->acc);
+}
+
+template <class F> static bool ll_vec_ok(const LLArgs<F> &a) {
+    constexpr int V = Vec16<F>::V;
+    auto al = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+    auto st = [](int64_t s) { return (s * (int64_t)sizeof(typename F::T)) % 16 == 0; };
+    return a.din % V == 0 && al(a.wv) && al(a.wm) && al(a.av) && al(a.am) && al(a.bv) && al(a.bm) && al(a.E) &&
+           st(a.ws) && st(a.as) && st(a.bs);
+}
+
 template <class F, int NP>
 static void deal_matvec(spdz_ctx *ctx, LLState *s, uint64_t seed, uint64_t sub, int64_t dout, int64_t din, int64_t R,
                         const void *alpha_shares_dev, const spdz_buf *A, const spdz_buf *B, const spdz_buf *C) {
@@ -287,7 +425,7 @@ static void launch_ll(spdz_ctx *ctx, LLState *s, const spdz_buf *W, const spdz_b
         a.dout = dout; a.din = din; a.R = R;
         a.base = base;
         a.ds = ctx->ds;
-        auto kr = k_ll_rows<F, NP>;
+        auto kr = ll_vec_ok(a) ? k_ll_rows_vec<F, NP> : k_ll_rows<F, NP>;
         kr<<<grid_for(ctx, (const void *)kr, 256, 0, dout * 32), 256, 0, ctx->stream>>>(a);
     }
 }
