@@ -64,7 +64,8 @@ enum spdz_op {
 enum spdz_kind {
     SPDZ_KIND_ALPHA = 1, SPDZ_KIND_TRIPLE_A = 2, SPDZ_KIND_TRIPLE_B = 3,
     SPDZ_KIND_TRIPLE_C = 4, SPDZ_KIND_INPUT = 5, SPDZ_KIND_CHECK = 6,
-    SPDZ_KIND_MTRIPLE_A = 7, SPDZ_KIND_MTRIPLE_B = 8, SPDZ_KIND_MTRIPLE_C = 9
+    SPDZ_KIND_MTRIPLE_A = 7, SPDZ_KIND_MTRIPLE_B = 8, SPDZ_KIND_MTRIPLE_C = 9,
+    SPDZ_KIND_INPUT_MASK = 10  /* masks of private inputs; stream sub = the owning party */
 };
 
 #define SPDZ_MAX_PARTIES 8
@@ -516,6 +517,30 @@ int spdz_load_matrix_preproc(spdz_ctx *ctx, const spdz_buf *A, const spdz_buf *B
  * shape. */
 int spdz_matmul(spdz_ctx *ctx, const spdz_buf *X, const spdz_buf *Y, const spdz_buf *Z, int64_t m, int64_t k,
                 int64_t n, int path, void *E_out_dev, void *F_out_dev);
+
+/* ------------------------------------------------------ inputs, outputs
+ * The steps on either side of the online core (Sec. I: parties secret-share
+ * their private inputs and combine shares of the result only to reveal the
+ * output; Sec. II-A.2: revealed values are accepted after the MAC check;
+ * Sec. IV: every input is secret-shared before the computation). */
+/* Dealer for input masks of party `owner`: r uniform (kind INPUT_MASK, stream
+ * sub = owner, element index j0 + j), shared with MACs into masks, and the
+ * clear r (which only the owner holds) into r_clear_dev ([count] elements,
+ * device). */
+int spdz_deal_input_masks(spdz_ctx *ctx, uint64_t seed, int32_t owner, uint64_t j0, int64_t count,
+                          const void *alpha_shares_dev, const spdz_buf *masks, void *r_clear_dev);
+/* Secret-shares the owner's private inputs x_dev ([N] canonical elements,
+ * device) with its masks: the owner publishes eps = x - r (written to
+ * eps_out_dev when not NULL) and out = [r] + eps, i.e. party 0's value share
+ * gets + eps and every party's MAC share + alpha_i * eps.  Each mask must be
+ * used once (the caller tracks them).  Needs the alpha shares loaded. */
+int spdz_input(spdz_ctx *ctx, const void *x_dev, const void *r_clear_dev, const spdz_buf *masks, const spdz_buf *out,
+               int64_t N, void *eps_out_dev);
+/* Reveals N shared values: opens them into out_dev (device, [N] elements;
+ * they join the check epoch), then runs the MAC check over the epoch
+ * (spdz_mac_check).  On failure *passed = 0, out_dev is zeroed and the call
+ * returns SPDZ_ERR_MAC: nothing is released.  sigma_host as spdz_mac_check. */
+int spdz_reveal(spdz_ctx *ctx, const spdz_buf *x, void *out_dev, int64_t N, int *passed, void *sigma_host);
 
 /* ---------------------------------------------------------- linear layer
  * The LinearLayer operator y = W x + b (Sec. III-D.3 "Data slicing" and

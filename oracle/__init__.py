@@ -32,6 +32,7 @@ P32 = (1 << 32) - 5        # the prime of the paper's evaluation (Sec. IV-A)
 OP_ADD, OP_SUB, OP_CMUL, OP_CADD, OP_MUL = 0, 1, 2, 3, 4
 K_ALPHA, K_TRIPLE_A, K_TRIPLE_B, K_TRIPLE_C, K_INPUT, K_CHECK = 1, 2, 3, 4, 5, 6
 K_MTRIPLE_A, K_MTRIPLE_B, K_MTRIPLE_C = 7, 8, 9
+K_INPUT_MASK = 10          # masks of private inputs (sub = the owning party)
 R_SECRET, R_VAL_SHARE, R_MAC_SHARE = 0, 1, 2
 
 _lib = None
@@ -354,6 +355,22 @@ def linear_rlc(p: int, dout: int, din: int, R: int, W, x, tri: Triples, check_se
                          _ptr(tri.bv), _ptr(tri.bm), C.c_uint64(check_seed), C.c_uint64(epoch),
                          C.c_uint64(j0), _ptr(A), _ptr(S))
     return A[0], S
+
+
+def deal_input_masks(p: int, n: int, seed: int, owner: int, j0: int, count: int, alpha):
+    """Masks for inputs owned by party `owner`: (rv, rm) shares [n, count] and
+    the clear masks r [count] the owner holds (kind INPUT_MASK, sub = owner)."""
+    return deal_shared(p, n, seed, K_INPUT_MASK, owner, j0, count, alpha)
+
+
+def input_share(p: int, x, r_clear, rv, rm, alpha_sh):
+    """The owner publishes eps = x - r; [x] = [r] + eps.  Returns (xv, xm, eps)."""
+    n, count = rv.shape[0], rv.shape[1]
+    xv, xm, eps = zeros(p, n, count), zeros(p, n, count), zeros(p, count)
+    lib().orc_input(*_pp(p), C.c_int(n), C.c_int64(count), _ptr(np.ascontiguousarray(x)),
+                    _ptr(np.ascontiguousarray(r_clear)), _ptr(rv), _ptr(rm), _ptr(alpha_sh), _ptr(xv), _ptr(xm),
+                    _ptr(eps))
+    return xv, xm, eps
 
 
 def dag_eval(p: int, dag, wv, wm, tri: Triples, alpha_sh):

@@ -23,6 +23,10 @@
  *   - matrix (tile) Beaver triples .................. Sec. III-D.3
  *   - LinearLayer y = W x + b, row tiles, one
  *     matrix-vector triple per tile ................ Sec. III-D.3, Sec. IV
+ *   - input sharing and the checked reveal of
+ *     outputs .................................... Sec. I (sharing sketch),
+ *                                                   Sec. II-A.2, Sec. IV ("all
+ *                                                   inputs are secret-shared")
  *   - ReduceAdd (horizontal sum, inner products) .... Sec. III-B (vectorization)
  *   - fake preprocessing (dealer) ................... Sec. IV-A
  * The paper gives no formula for the MAC-share updates, for which party adds
@@ -152,7 +156,7 @@ void orc_draw(u64 plo, u64 phi, u64 seed, u64 stream, u64 j0, int64_t count, u64
 }
 
 enum { K_ALPHA = 1, K_TRIPLE_A = 2, K_TRIPLE_B = 3, K_TRIPLE_C = 4, K_INPUT = 5,
-       K_CHECK = 6, K_MTRIPLE_A = 7, K_MTRIPLE_B = 8, K_MTRIPLE_C = 9 };
+       K_CHECK = 6, K_MTRIPLE_A = 7, K_MTRIPLE_B = 8, K_MTRIPLE_C = 9, K_INPUT_MASK = 10 };
 enum { R_SECRET = 0, R_VAL_SHARE = 1, R_MAC_SHARE = 2 };
 
 /* ------------------------------------------------------------- threading */
@@ -793,6 +797,27 @@ void orc_linear_rlc(u64 plo, u64 phi, int n, int64_t dout, int64_t din, int64_t 
     st(A_out, 0, w, A);
     for (int i = 0; i < n; ++i) st(S_out, i, w, Sv[i]);
     free(c.rowA); free(c.rowS);
+}
+
+/* --------------------------------------------------------- input sharing
+ * The owner of a private input x holds a dealer mask r in the clear, and the
+ * parties hold a sharing [r] with MACs (kind INPUT_MASK, sub = the owner).
+ * The owner publishes eps = x - r; every party sets [x] = [r] + eps: party 0
+ * adds eps to its value share and every party adds alpha_i * eps to its MAC
+ * share (the public-constant addition).  eps is public and is returned. */
+void orc_input(u64 plo, u64 phi, int n, int64_t count, const u64 *x, const u64 *r_clear,
+               const u64 *rv, const u64 *rm, const u64 *alpha_sh, u64 *outv, u64 *outm, u64 *eps) {
+    u128 p = mkp(plo, phi); int w = words_of(p);
+    for (int64_t j = 0; j < count; ++j) {
+        u128 e = f_sub(ld(x, j, w), ld(r_clear, j, w), p);
+        st(eps, j, w, e);
+        for (int i = 0; i < n; ++i) {
+            int64_t q = (int64_t)i * count + j;
+            u128 v = ld(rv, q, w);
+            st(outv, q, w, i == 0 ? f_add(v, e, p) : v);
+            st(outm, q, w, f_add(ld(rm, q, w), f_mul(ld(alpha_sh, i, w), e, p), p));
+        }
+    }
 }
 
 /* --------------------------------------------------------------------- DAG

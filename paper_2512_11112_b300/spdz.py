@@ -25,6 +25,7 @@ SPDZ_OP_ADD, SPDZ_OP_SUB, SPDZ_OP_CMUL, SPDZ_OP_CADD, SPDZ_OP_MUL = 0, 1, 2, 3, 
 SPDZ_KIND_ALPHA, SPDZ_KIND_TRIPLE_A, SPDZ_KIND_TRIPLE_B, SPDZ_KIND_TRIPLE_C = 1, 2, 3, 4
 SPDZ_KIND_INPUT, SPDZ_KIND_CHECK = 5, 6
 SPDZ_KIND_MTRIPLE_A, SPDZ_KIND_MTRIPLE_B, SPDZ_KIND_MTRIPLE_C = 7, 8, 9
+SPDZ_KIND_INPUT_MASK = 10
 SPDZ_MAX_PARTIES = 8
 P61 = (1 << 61) - 1
 P127 = (1 << 127) - 1
@@ -157,6 +158,9 @@ _SIGS = {
     "spdz_load_matrix_preproc": [_vp, _bufp, _bufp, _bufp, _i64, _i64, _i64],
     "spdz_matmul": [_vp, _bufp, _bufp, _bufp, _i64, _i64, _i64, _int, _vp, _vp],
     "spdz_serve_set_mode": [_vp, C.c_int32, _vp, _i64],
+    "spdz_deal_input_masks": [_vp, _u64, C.c_int32, _u64, _i64, _vp, _bufp, _vp],
+    "spdz_input": [_vp, _vp, _vp, _bufp, _bufp, _i64, _vp],
+    "spdz_reveal": [_vp, _bufp, _vp, _i64, C.POINTER(_int), _vp],
     "spdz_deal_matvec_triples": [_vp, _u64, _u64, _i64, _i64, _i64, _vp, _bufp, _bufp, _bufp],
     "spdz_load_matvec_preproc": [_vp, _bufp, _bufp, _bufp, _i64, _i64, _i64],
     "spdz_linear_layer": [_vp, _bufp, _bufp, _bufp, _bufp, _i64, _i64, _i64, _vp, _vp],
@@ -590,3 +594,25 @@ def spdz_linear_layer(ctx, W: spdz_buf, x: spdz_buf, b: spdz_buf, y: spdz_buf, d
                       D_out=None, E_out=None) -> None:
     _chk(ctx, lib.spdz_linear_layer(ctx, C.byref(W), C.byref(x), C.byref(b), C.byref(y), dout, din, tile_rows,
                                     ptr(D_out), ptr(E_out)))
+
+
+# --------------------------------------------------------- inputs, outputs
+
+def spdz_deal_input_masks(ctx, seed: int, owner: int, j0: int, count: int, alpha_shares, masks: spdz_buf,
+                          r_clear) -> None:
+    _chk(ctx, lib.spdz_deal_input_masks(ctx, seed, owner, j0, count, ptr(alpha_shares), C.byref(masks),
+                                        ptr(r_clear)))
+
+
+def spdz_input(ctx, x, r_clear, masks: spdz_buf, out: spdz_buf, N: int, eps_out=None) -> None:
+    _chk(ctx, lib.spdz_input(ctx, ptr(x), ptr(r_clear), C.byref(masks), C.byref(out), N, ptr(eps_out)))
+
+
+def spdz_reveal(ctx, x: spdz_buf, out, N: int, sigma_host=None) -> bool:
+    """Opens and checks; True when the check passed (the values are in out),
+    False when it failed (out zeroed)."""
+    ok = _int(0)
+    rc = lib.spdz_reveal(ctx, C.byref(x), ptr(out), N, C.byref(ok), ptr(sigma_host))
+    if rc not in (SPDZ_OK, SPDZ_ERR_MAC):
+        _chk(ctx, rc)
+    return bool(ok.value)
