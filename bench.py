@@ -804,12 +804,26 @@ def run_heavy(args):
 
 def run_batch(args):
     """Plain 2-party p61 Beaver batch of 2^16 products with one MAC check,
-    and the N sweep 2^16 .. 2^26 of the batch kernel against HBM bandwidth."""
+    and the N sweep 2^16 .. 2^26 of the batch kernel against HBM bandwidth
+    (and the same sweep for p = 2^32-5)."""
+    hbm, src = peaks()
+    sweep = batch_sweep(args, "p61", hbm)
+    sweep32 = batch_sweep(args, "p32", hbm)
+    line = {"metric": "Beaver mults/s, 2 parties, p=2^61-1, 2^16 products with one MAC check",
+            "value": 2**16 / (sweep["2^16"]["with_check_us"] * 1e-6), "unit": "Beaver mults/s",
+            "higher_is_better": True, "n_gpus": 1, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "2^16 Beaver mults, n=2, p61, batch + MAC check (L2-resident: latency-bound); "
+                                   "sweep to 2^26 for the bandwidth fraction", "bytes_per_mult": 192},
+            "sweep": sweep, "sweep_p32": sweep32, "hbm_peak_gbs": hbm, "peak_source": src}
+    print(json.dumps(line), flush=True)
+
+
+def batch_sweep(args, field, hbm):
     import torch
     from paper_2512_11112_b300 import shares as SH
     from paper_2512_11112_b300 import spdz as S
-    n, f = 2, S.SPDZ_F61
-    hbm, src = peaks()
+    n = 2
+    f, w = (S.SPDZ_F61, 8) if field == "p61" else (S.SPDZ_F32, 4)
     ctx = S.spdz_ctx_create(n, f, torch.cuda.current_stream().cuda_stream)
     ash = SH.zeros(f, n)
     S.spdz_deal_alpha(ctx, 1, ash)
@@ -839,16 +853,10 @@ def run_batch(args):
                 ts_all.append(e0.elapsed_time(e2))
         ms = statistics.median(ts_mul)
         sweep[f"2^{lg}"] = {"mul_us": ms * 1e3, "with_check_us": statistics.median(ts_all) * 1e3,
-                            "mults_per_s": N / (ms * 1e-3), "gbs": 12 * n * 8 * N / (ms * 1e-3) / 1e9,
-                            "frac_of_hbm": 12 * n * 8 * N / (ms * 1e-3) / 1e9 / hbm, "check_passed": ok}
+                            "mults_per_s": N / (ms * 1e-3), "gbs": 12 * n * w * N / (ms * 1e-3) / 1e9,
+                            "frac_of_hbm": 12 * n * w * N / (ms * 1e-3) / 1e9 / hbm, "check_passed": ok}
     S.spdz_ctx_destroy(ctx)
-    line = {"metric": "Beaver mults/s, 2 parties, p=2^61-1, 2^16 products with one MAC check",
-            "value": 2**16 / (sweep["2^16"]["with_check_us"] * 1e-6), "unit": "Beaver mults/s",
-            "higher_is_better": True, "n_gpus": 1, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "2^16 Beaver mults, n=2, p61, batch + MAC check (L2-resident: latency-bound); "
-                                   "sweep to 2^26 for the bandwidth fraction", "bytes_per_mult": 192},
-            "sweep": sweep, "hbm_peak_gbs": hbm, "peak_source": src}
-    print(json.dumps(line), flush=True)
+    return sweep
 
 
 def run_profile(args):

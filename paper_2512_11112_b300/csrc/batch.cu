@@ -18,8 +18,14 @@ int launch_check(spdz_ctx *ctx, int final_check);
 template <class F, int V, bool STREAM>
 __device__ __forceinline__ void vld(const typename F::T *p, typename F::T (&out)[V]) {
     if constexpr (std::is_same_v<F, F32>) {
-        static_assert(V == 1, "p32 moves one element per access");
-        out[0] = STREAM ? __ldcs(p) : *p;
+        static_assert(V == 1 || V == 4, "p32 moves one or four elements per access");
+        if constexpr (V == 4) {
+            const uint4 *q = reinterpret_cast<const uint4 *>(p);
+            const uint4 t = STREAM ? __ldcs(q) : *q;
+            out[0] = t.x; out[1] = t.y; out[2] = t.z; out[3] = t.w;
+        } else {
+            out[0] = STREAM ? __ldcs(reinterpret_cast<const unsigned int *>(p)) : *p;
+        }
     } else if constexpr (F::WORDS == 1) {
         if constexpr (V == 2) {
             const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(p);
@@ -41,7 +47,10 @@ __device__ __forceinline__ void vld(const typename F::T *p, typename F::T (&out)
 template <class F, int V>
 __device__ __forceinline__ void vst(typename F::T *p, const typename F::T (&in)[V]) {
     if constexpr (std::is_same_v<F, F32>) {
-        *p = in[0];
+        if constexpr (V == 4)
+            *reinterpret_cast<uint4 *>(p) = make_uint4(in[0], in[1], in[2], in[3]);
+        else
+            *p = in[0];
     } else if constexpr (F::WORDS == 1) {
         if constexpr (V == 2) {
             *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(in[0], in[1]);
@@ -163,7 +172,7 @@ __device__ __forceinline__ void beaver_core(const MulArgs<F> &a, int64_t e, int6
         const uint64_t j = a.base + 2 * (uint64_t)(opened_idx + v);
         re[v] = Draw<F>::at(key, j);
         rd[v] = Draw<F>::at(key, j + 1);
-        acc[0] = F::add(acc[0], F::add(F::mul(re[v], eps[v]), F::mul(rd[v], dlt[v])));
+        acc[0] = Fma<F>::f2(acc[0], re[v], eps[v], rd[v], dlt[v]);
     }
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
@@ -176,12 +185,10 @@ __device__ __forceinline__ void beaver_core(const MulArgs<F> &a, int64_t e, int6
         vld<F, V, true>(a.cm + i * a.cs + e, gc);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            T zz = F::add(c[v], F::add(F::mul(eps[v], bv[i][v]), F::mul(dlt[v], av[i][v])));
-            z[i][v] = i == 0 ? F::add(zz, de[v]) : zz;
-            T gg = F::add(gc[v], F::add(F::mul(eps[v], gb[v]), F::mul(dlt[v], ga[v])));
-            gz[i][v] = F::add(gg, F::mul(alpha[i], de[v]));
-            acc[1 + i] = F::add(acc[1 + i], F::add(F::mul(re[v], F::sub(gx[v], ga[v])),
-                                                   F::mul(rd[v], F::sub(gy[v], gb[v]))));
+            // each output one sum of products, reduced once where the field allows
+            z[i][v] = Fma<F>::f2(i == 0 ? F::add(c[v], de[v]) : c[v], eps[v], bv[i][v], dlt[v], av[i][v]);
+            gz[i][v] = Fma<F>::f3(gc[v], eps[v], gb[v], dlt[v], ga[v], alpha[i], de[v]);
+            acc[1 + i] = Fma<F>::f2(acc[1 + i], re[v], F::sub(gx[v], ga[v]), rd[v], F::sub(gy[v], gb[v]));
         }
     }
 }
@@ -332,6 +339,12 @@ static void launch_linear(spdz_ctx *ctx, const LinArgs<F> &a, bool v2) {
             kern<<<grid_for(ctx, (const void *)kern, 256, 0, (a.N + 1) / 2), 256, 0, ctx->stream>>>(a);
             return;
         }
+    } else if constexpr (std::is_same_v<F, F32>) {
+        if (v2) {
+            auto kern = k_linear<F, NP, 4>;
+            kern<<<grid_for(ctx, (const void *)kern, 256, 0, (a.N + 3) / 4), 256, 0, ctx->stream>>>(a);
+            return;
+        }
     }
     auto kern = k_linear<F, NP, 1>;
     kern<<<grid_for(ctx, (const void *)kern, 256, 0, a.N), 256, 0, ctx->stream>>>(a);
@@ -343,6 +356,12 @@ static void launch_mul(spdz_ctx *ctx, const MulArgs<F> &a, bool v2) {
         if (v2) {
             auto kern = k_mul<F, NP, 2>;
             kern<<<grid_for(ctx, (const void *)kern, 256, 0, (a.N + 1) / 2), 256, 0, ctx->stream>>>(a);
+            return;
+        }
+    } else if constexpr (std::is_same_v<F, F32>) {
+        if (v2) {
+            auto kern = k_mul<F, NP, 4>;
+            kern<<<grid_for(ctx, (const void *)kern, 256, 0, (a.N + 3) / 4), 256, 0, ctx->stream>>>(a);
             return;
         }
     }
@@ -391,7 +410,8 @@ int spdz_linear(spdz_ctx *ctx, int op, const spdz_buf *x, const spdz_buf *y, con
         return rc;
     if (!binary && !k_host) return set_err(ctx, SPDZ_ERR_ARG, "linear: constant required");
     if (op == SPDZ_OP_CADD && !ctx->alpha_loaded) return set_err(ctx, SPDZ_ERR_STATE, "linear: CADD needs alpha shares");
-    const bool v2 = ctx->field == SPDZ_F61 && buf_vec2_ok(x) && buf_vec2_ok(z) && (!binary || buf_vec2_ok(y));
+    const size_t eb = elem_bytes(ctx->field);
+    const bool v2 = ctx->field != SPDZ_F127 && buf_vec_ok(x, eb) && buf_vec_ok(z, eb) && (!binary || buf_vec_ok(y, eb));
     SPDZ_FIELD_SWITCH(ctx->field, {
         if (!binary && !host_canonical<F>(k_host)) return set_err(ctx, SPDZ_ERR_ARG, "linear: constant not in [0, p)");
         using T = typename F::T;
@@ -424,12 +444,15 @@ int spdz_mul_batch(spdz_ctx *ctx, const spdz_buf *x, const spdz_buf *y, const sp
         fill_mul_args<F>(ctx, a, x, y, z, t0);
         a.opened = (typename F::T *)opened_dev;
         a.N = N;
+        // the vector path needs every row 16-byte aligned (2 p61 or 4 p32 elements)
+        const size_t eb = sizeof(typename F::T);
         spdz_buf ta = ctx->ta, tb = ctx->tb, tc = ctx->tc;
-        ta.val = (char *)ta.val + 8 * t0; ta.mac = (char *)ta.mac + 8 * t0;
-        tb.val = (char *)tb.val + 8 * t0; tb.mac = (char *)tb.mac + 8 * t0;
-        tc.val = (char *)tc.val + 8 * t0; tc.mac = (char *)tc.mac + 8 * t0;
-        const bool v2 = F::WORDS == 1 && buf_vec2_ok(x) && buf_vec2_ok(y) && buf_vec2_ok(z) && buf_vec2_ok(&ta) &&
-                        buf_vec2_ok(&tb) && buf_vec2_ok(&tc) && ((uintptr_t)opened_dev % 16 == 0);
+        ta.val = (char *)ta.val + eb * t0; ta.mac = (char *)ta.mac + eb * t0;
+        tb.val = (char *)tb.val + eb * t0; tb.mac = (char *)tb.mac + eb * t0;
+        tc.val = (char *)tc.val + eb * t0; tc.mac = (char *)tc.mac + eb * t0;
+        const bool v2 = F::WORDS == 1 && buf_vec_ok(x, eb) && buf_vec_ok(y, eb) && buf_vec_ok(z, eb) &&
+                        buf_vec_ok(&ta, eb) && buf_vec_ok(&tb, eb) && buf_vec_ok(&tc, eb) &&
+                        ((uintptr_t)opened_dev % 16 == 0);
         SPDZ_NP_SWITCH(ctx->n, launch_mul<F, NP>(ctx, a, v2));
     });
     if ((rc = check_launch(ctx, "mul_batch"))) return rc;

@@ -233,6 +233,7 @@ int check_cuda(spdz_ctx *ctx, cudaError_t e, const char *what);
 int check_launch(spdz_ctx *ctx, const char *what);
 int validate_buf(spdz_ctx *ctx, const spdz_buf *b, int64_t N, const char *name);
 bool buf_vec2_ok(const spdz_buf *b);    // 16-byte aligned rows (p61 vector path)
+bool buf_vec_ok(const spdz_buf *b, size_t elem_bytes);   // 16-byte aligned rows, any element size
 int grid_for(spdz_ctx *ctx, const void *kernel, int block, size_t smem, int64_t work_items);
 void sched_destroy(spdz_ctx *ctx);
 void mat_destroy(spdz_ctx *ctx);

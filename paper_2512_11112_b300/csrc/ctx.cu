@@ -42,6 +42,10 @@ int validate_buf(spdz_ctx *ctx, const spdz_buf *b, int64_t N, const char *name) 
     return SPDZ_OK;
 }
 
+bool buf_vec_ok(const spdz_buf *b, size_t eb) {
+    return ((uintptr_t)b->val % 16 == 0) && ((uintptr_t)b->mac % 16 == 0) && ((b->stride * (int64_t)eb) % 16 == 0);
+}
+
 bool buf_vec2_ok(const spdz_buf *b) {
     return ((uintptr_t)b->val % 16 == 0) && ((uintptr_t)b->mac % 16 == 0) && (b->stride % 2 == 0);
 }

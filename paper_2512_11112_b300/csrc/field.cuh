@@ -105,6 +105,50 @@ struct W61 {
     }
 };
 
+// c + a1 b1 + a2 b2 (+ a3 b3) mod p with one reduction where the field allows
+// it: p61 sums the 122-bit products exactly in 128 bits (below 2^124);
+// p = 2^32-5 folds each 64-bit product to 5 hi + lo (below 2^35) and sums in
+// 64 bits; p127 reduces each product.
+template <class F> struct Fma {
+    __device__ __forceinline__ static typename F::T f2(typename F::T c, typename F::T a1, typename F::T b1,
+                                                       typename F::T a2, typename F::T b2) {
+        return F::add(c, F::add(F::mul(a1, b1), F::mul(a2, b2)));
+    }
+    __device__ __forceinline__ static typename F::T f3(typename F::T c, typename F::T a1, typename F::T b1,
+                                                       typename F::T a2, typename F::T b2, typename F::T a3,
+                                                       typename F::T b3) {
+        return F::add(f2(c, a1, b1, a2, b2), F::mul(a3, b3));
+    }
+};
+template <> struct Fma<F61> {
+    __device__ __forceinline__ static uint64_t f2(uint64_t c, uint64_t a1, uint64_t b1, uint64_t a2, uint64_t b2) {
+        W61 w;
+        w.add(c);
+        w.mac(a1, b1);
+        w.mac(a2, b2);
+        return w.reduce();
+    }
+    __device__ __forceinline__ static uint64_t f3(uint64_t c, uint64_t a1, uint64_t b1, uint64_t a2, uint64_t b2,
+                                                  uint64_t a3, uint64_t b3) {
+        W61 w;
+        w.add(c);
+        w.mac(a1, b1);
+        w.mac(a2, b2);
+        w.mac(a3, b3);
+        return w.reduce();
+    }
+};
+template <> struct Fma<F32> {
+    __device__ __forceinline__ static uint64_t fold(uint64_t x) { return 5ull * (x >> 32) + (x & 0xffffffffull); }
+    __device__ __forceinline__ static uint32_t f2(uint32_t c, uint32_t a1, uint32_t b1, uint32_t a2, uint32_t b2) {
+        return F32::reduce64((uint64_t)c + fold((uint64_t)a1 * b1) + fold((uint64_t)a2 * b2));
+    }
+    __device__ __forceinline__ static uint32_t f3(uint32_t c, uint32_t a1, uint32_t b1, uint32_t a2, uint32_t b2,
+                                                  uint32_t a3, uint32_t b3) {
+        return F32::reduce64((uint64_t)c + fold((uint64_t)a1 * b1) + fold((uint64_t)a2 * b2) + fold((uint64_t)a3 * b3));
+    }
+};
+
 // ----------------------------------------------------------------- p127
 struct u128v {
     uint64_t lo, hi;

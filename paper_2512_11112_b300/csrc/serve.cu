@@ -237,7 +237,8 @@ struct spdz_server {
     cudaEvent_t ring_start[RING] = {};    // start of its kernels
     int64_t tile_cap = 0;
     std::map<const spdz_dag_desc *, ServeCircuit> circuits;
-    double tick_us_ema = 0;                // measured duration of one tick
+    double tick_us_ema = 0;                // measured duration of one tick (moving average)
+    double tick_us_min = 0;                // shortest tick measured: the fixed cost of a tick
 };
 
 namespace {
@@ -539,7 +540,7 @@ int spdz_serve_run(spdz_server *s, const spdz_serve_request *reqs, int64_t count
             } else if (s->mode == SPDZ_SERVE_LEARNED) {
                 // cluster launch when the whole circuit in one cluster is
                 // predicted to finish before its layers would by ticks, each
-                // tick lasting at least the measured tick duration
+                // tick lasting at least the shortest measured tick
                 ServeCircuit &Cm = const_cast<ServeCircuit &>(C);
                 if (!Cm.predicted) {
                     spdz_dag tmp;
@@ -568,7 +569,10 @@ int spdz_serve_run(spdz_server *s, const spdz_serve_request *reqs, int64_t count
                 }
                 if (Cm.predicted) {
                     double tick_mode = 0;
-                    for (double g : Cm.pred_grid_us) tick_mode += std::max(g, s->tick_us_ema);
+                    // each layer costs at least one tick's fixed cost (a long
+                    // tick is long because of other requests' wide layers)
+                    const double floor_us = s->tick_us_min > 0 ? s->tick_us_min : s->tick_us_ema;
+                    for (double g : Cm.pred_grid_us) tick_mode += std::max(g, floor_us);
                     L->cluster = Cm.pred_cluster_us < tick_mode;
                 }
             }
@@ -634,6 +638,7 @@ int spdz_serve_run(spdz_server *s, const spdz_serve_request *reqs, int64_t count
                 float ms = 0;
                 if (cudaEventElapsedTime(&ms, s->ring_start[ring], s->ring_ev[ring]) == cudaSuccess && ms > 0)
                     s->tick_us_ema = s->tick_us_ema == 0 ? ms * 1e3 : 0.9 * s->tick_us_ema + 0.1 * ms * 1e3;
+                    s->tick_us_min = s->tick_us_min == 0 ? ms * 1e3 : std::min(s->tick_us_min, (double)ms * 1e3);
             }
             int64_t need = 0;
             for (Live *L : ticking) {
