@@ -76,13 +76,13 @@ __device__ __forceinline__ void beaver_math_src(
     }
     const T de = F::mul(eps, dlt);
     const T re = Draw<F>::at(key, j), rd = Draw<F>::at(key, j + 1);
-    acc[0] = F::add(acc[0], F::add(F::mul(re, eps), F::mul(rd, dlt)));
+    // each output one sum of products, reduced once where the field allows
+    acc[0] = Fma<F>::f2(acc[0], re, eps, rd, dlt);
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-        const T zz = F::add(tri(4, i), F::add(F::mul(eps, tri(2, i)), F::mul(dlt, tri(0, i))));
-        z[i] = i == 0 ? F::add(zz, de) : zz;
-        gz[i] = F::add(F::add(tri(5, i), F::add(F::mul(eps, tri(3, i)), F::mul(dlt, tri(1, i)))), F::mul(alpha[i], de));
-        acc[1 + i] = F::add(acc[1 + i], F::add(F::mul(re, F::sub(gx[i], tri(1, i))), F::mul(rd, F::sub(gy[i], tri(3, i)))));
+        z[i] = Fma<F>::f2(i == 0 ? F::add(tri(4, i), de) : tri(4, i), eps, tri(2, i), dlt, tri(0, i));
+        gz[i] = Fma<F>::f3(tri(5, i), eps, tri(3, i), dlt, tri(1, i), alpha[i], de);
+        acc[1 + i] = Fma<F>::f2(acc[1 + i], re, F::sub(gx[i], tri(1, i)), rd, F::sub(gy[i], tri(3, i)));
     }
 }
 

@@ -108,7 +108,8 @@ struct W61 {
 // c + a1 b1 + a2 b2 (+ a3 b3) mod p with one reduction where the field allows
 // it: p61 sums the 122-bit products exactly in 128 bits (below 2^124);
 // p = 2^32-5 folds each 64-bit product to 5 hi + lo (below 2^35) and sums in
-// 64 bits; p127 reduces each product.
+// 64 bits; p127 reduces each product (an exact 256-bit sum measured no
+// faster: its cost is the 128 x 128-bit products themselves).
 template <class F> struct Fma {
     __device__ __forceinline__ static typename F::T f2(typename F::T c, typename F::T a1, typename F::T b1,
                                                        typename F::T a2, typename F::T b2) {
