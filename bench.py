@@ -265,10 +265,11 @@ def time_steps(circ, plan, steps, warmup, flush):
     return [a.elapsed_time(b) for a, b in ev], ok
 
 
-def beaver_roofline(torch, S, SH, hbm_peak, N=2**24, calls=4):
-    """Standalone batched Beaver multiplication (spdz_mul_batch), n=3, p61:
-    288 algorithmic bytes per product (12 words per party)."""
-    field = S.SPDZ_F61
+def beaver_roofline(torch, S, SH, hbm_peak, N=2**24, calls=4, field=None):
+    """Standalone batched Beaver multiplication (spdz_mul_batch), n=3, p61
+    (or the given field): 12 words per party and product (288 algorithmic
+    bytes for p61)."""
+    field = S.SPDZ_F61 if field is None else field
     ctx = S.spdz_ctx_create(N_PARTIES, field, torch.cuda.current_stream().cuda_stream)
     try:
         a_sh = SH.zeros(field, N_PARTIES)
@@ -292,8 +293,10 @@ def beaver_roofline(torch, S, SH, hbm_peak, N=2**24, calls=4):
             ts.append(e0.elapsed_time(e1))
         ok = S.spdz_mac_check(ctx)
         ms = statistics.median(ts)
-        gbs = 288 * N / (ms * 1e-3) / 1e9
-        return {"kernel": "k_mul<F61,3,2> (spdz_mul_batch)", "N": N, "bytes_per_mult": 288,
+        bpm = 12 * N_PARTIES * {S.SPDZ_F61: 8, S.SPDZ_F127: 16, S.SPDZ_F32: 4}[field]
+        gbs = bpm * N / (ms * 1e-3) / 1e9
+        kname = {S.SPDZ_F61: "k_mul<F61,3,2>", S.SPDZ_F127: "k_mul<F127,3,1>", S.SPDZ_F32: "k_mul<F32,3,4>"}[field]
+        return {"kernel": f"{kname} (spdz_mul_batch)", "N": N, "bytes_per_mult": bpm,
                 "ms": round(ms, 4), "mults_per_s": N / (ms * 1e-3), "achieved_gbs": round(gbs, 1),
                 "peak_gbs": hbm_peak, "frac": round(gbs / hbm_peak, 4),
                 "traffic": read_traffic().get("k_mul") if N == 2**24 else None,
@@ -896,6 +899,8 @@ def run_profile(args):
             S.spdz_matmul(ctx, X.buf(), Y.buf(), Z.buf(), dim, dim, dim, S.SPDZ_MATMUL_TENSOR)
             assert S.spdz_mac_check(ctx)
         S.spdz_ctx_destroy(ctx)
+    elif args.profile == "beaver127":
+        beaver_roofline(torch, S, SH, peaks()[0], N=2**24, calls=args.steps, field=S.SPDZ_F127)
     else:
         beaver_roofline(torch, S, SH, peaks()[0], N=2**24, calls=args.steps)
 
@@ -911,7 +916,7 @@ def main():
                     help="circuit: the benchmark circuit (default); serve, matmul, heavy, batch: the other "
                          "workloads, one JSON line each")
     ap.add_argument("--serve-requests", type=int, default=10000)
-    ap.add_argument("--profile", default=None, choices=["dag", "tagged", "beaver", "matmul", "linear"],
+    ap.add_argument("--profile", default=None, choices=["dag", "tagged", "beaver", "beaver127", "matmul", "linear"],
                     help="small run of one kernel for an ncu capture (prints nothing)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
