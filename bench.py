@@ -440,7 +440,7 @@ def run_ours(args, rank, world, local_rank):
                                "60% mul / 15% add / 15% sub / 10% const-mul, n=3, p=2^61-1",
                    "gates": dag.n_gates, "beaver_mults": nm, "parties": N_PARTIES, "field": "p61",
                    "scheduler": "fused persistent kernels + CUDA graph, plan chosen by the learned scheduler "
-                                "(judged against the autotuned plan)", "l2": "flushed between steps (256 MB write)",
+                                "(checked against the autotuned plan)", "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}", "widths": dag.meta["widths"]},
         "mac_check_passed": bool(ok_f and ok_p and ok_e),
         "per_layer": {"value": per_layer_value, "ms_per_step": tot_p / steps,
