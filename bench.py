@@ -452,8 +452,10 @@ def run_ours(args, rank, world, local_rank):
                      "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
                      "peak_source": peak_src, "algorithmic_bytes_per_launch": bytes_run},
         "beaver_batch_roofline": beaver,
-        # per step: the run's begin kernel, one kernel per layer group, the check kernel
-        "gpu_launches": steps * (2 + max(1, len(sched["chosen_groups"]))),
+        # per step: the run's begin kernel, one kernel per layer group, the check
+        # kernel (the tagged kernel runs the check itself: begin + one kernel)
+        "gpu_launches": steps * (2 if sched["chosen_mode"] == S.SPDZ_SCHED_TAGGED
+                                 else 2 + max(1, len(sched["chosen_groups"]))),
         "clocks": clk.summary(),
     }
     if cpu:

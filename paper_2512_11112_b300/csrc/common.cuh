@@ -43,7 +43,8 @@ struct DevState {
     unsigned int bar_count;
     unsigned int bar_abort;            // set when a barrier wait timed out
     unsigned int df_tag;               // tag of the current tagged-mode run (1..7; 0: none)
-    unsigned int bar_pad[61];
+    unsigned int run_done;             // CTAs of a tagged run that have finished
+    unsigned int bar_pad[60];
     // per-layer timestamps written by the fused circuit kernel (globaltimer ns)
     unsigned long long layer_ts[1024];
 };
@@ -79,8 +80,15 @@ __device__ __forceinline__ void acc_add(unsigned long long *acc, F127::T v) {
     if (old1 + add1 < old1) atomicAdd(&acc[2], 1ull);
 }
 
-// 192-bit accumulator -> field element.
-__device__ __forceinline__ F61::T acc_reduce_f61(const unsigned long long *a) {
+// 192-bit accumulator -> field element.  The words are read from L2 (they
+// are written by other CTAs' atomics, and may share a cache line with
+// state this SM read earlier).
+__device__ __forceinline__ void acc_words(const unsigned long long *a, unsigned long long (&w)[3]) {
+    w[0] = __ldcg(a);
+    w[1] = __ldcg(a + 1);
+    w[2] = __ldcg(a + 2);
+}
+__device__ __forceinline__ F61::T acc_reduce_f61(const unsigned long long (&a)[3]) {
     auto red = [](uint64_t w) -> uint64_t {          // one word mod p
         uint64_t s = (w & F61::P) + (w >> 61);
         return s >= F61::P ? s - F61::P : s;
@@ -88,7 +96,7 @@ __device__ __forceinline__ F61::T acc_reduce_f61(const unsigned long long *a) {
     // 2^64 == 2^3 and 2^128 == 2^6 (mod 2^61 - 1)
     return F61::add(red(a[0]), F61::add(F61::mul(red(a[1]), 8), F61::mul(red(a[2]), 64)));
 }
-__device__ __forceinline__ F127::T acc_reduce_f127(const unsigned long long *a) {
+__device__ __forceinline__ F127::T acc_reduce_f127(const unsigned long long (&a)[3]) {
     // (a1:a0) < 2^128 reduced by a fold, then + 2*a2 since 2^128 == 2
     uint64_t lo = a[0], hi = a[1];
     uint64_t top = hi >> 63;
@@ -104,19 +112,26 @@ __device__ __forceinline__ F127::T acc_reduce_f127(const unsigned long long *a) 
     return F127::add(v, F127::add(t, t));
 }
 // 2^64 == 25 and 2^128 == 625 (mod 2^32 - 5)
-__device__ __forceinline__ F32::T acc_reduce_f32(const unsigned long long *a) {
+__device__ __forceinline__ F32::T acc_reduce_f32(const unsigned long long (&a)[3]) {
     return F32::add(F32::reduce64(a[0]),
                     F32::add(F32::mul(F32::reduce64(a[1]), 25u), F32::mul(F32::reduce64(a[2]), 625u)));
 }
-template <class F> __device__ __forceinline__ typename F::T acc_reduce(const unsigned long long *a);
-template <> __device__ __forceinline__ F32::T acc_reduce<F32>(const unsigned long long *a) {
-    return acc_reduce_f32(a);
+// from words already loaded
+template <class F> __device__ __forceinline__ typename F::T acc_reduce_w(const unsigned long long (&w)[3]);
+template <> __device__ __forceinline__ F32::T acc_reduce_w<F32>(const unsigned long long (&w)[3]) {
+    return acc_reduce_f32(w);
 }
-template <> __device__ __forceinline__ F61::T acc_reduce<F61>(const unsigned long long *a) {
-    return acc_reduce_f61(a);
+template <> __device__ __forceinline__ F61::T acc_reduce_w<F61>(const unsigned long long (&w)[3]) {
+    return acc_reduce_f61(w);
 }
-template <> __device__ __forceinline__ F127::T acc_reduce<F127>(const unsigned long long *a) {
-    return acc_reduce_f127(a);
+template <> __device__ __forceinline__ F127::T acc_reduce_w<F127>(const unsigned long long (&w)[3]) {
+    return acc_reduce_f127(w);
+}
+// from the accumulator in memory
+template <class F> __device__ __forceinline__ typename F::T acc_reduce(const unsigned long long *a) {
+    unsigned long long w[3];
+    acc_words(a, w);
+    return acc_reduce_w<F>(w);
 }
 
 // ------------------------------------------------------------- reductions

@@ -233,10 +233,16 @@ static int enqueue_run(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, cons
             l0 = l1;
         }
     }
-    int rc = launch_check(ctx, 1);
-    ++launches;
+    // the tagged kernel finishes with the run's check itself
+    if (plan.mode != SPDZ_SCHED_TAGGED) {
+        int rc = launch_check(ctx, 1);
+        ++launches;
+        if (rc) {
+            ctx->stream = saved;
+            return -rc;
+        }
+    }
     ctx->stream = saved;
-    if (rc) return -rc;
     return launches;
 }
 

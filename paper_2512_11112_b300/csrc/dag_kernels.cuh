@@ -5,6 +5,7 @@
 // the per-layer, fused and cluster kernels.
 #pragma once
 #include "beaver.cuh"
+#include "check.cuh"
 #include "dag.cuh"
 
 namespace spdz {
@@ -252,6 +253,7 @@ static __global__ void k_run_begin(DevState *ds, uint64_t tri_base, uint32_t df_
     ds->bar_abort = 0;
     ds->err_flags = 0;
     ds->df_tag = df_tag;
+    ds->run_done = 0;
 }
 
 // Per-layer form: records [r0, r1) of layer l0 (one gate class range).
@@ -587,6 +589,17 @@ __global__ void __launch_bounds__(256, 2) k_dag_tagged(DagArgs<F61> a) {
     }
     cp_async_wait_all();
     block_accumulate<F, NP + 1>(acc, a.ds->acc);
+    // the last CTA to finish runs the run's MAC check (its accumulator
+    // atomics, like every CTA's, are ordered before its count by the fence)
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&a.ds->run_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        check_epoch<F, NP>(a.ds, 1);
+    }
 }
 
 template <int NP> constexpr size_t tagged_smem(int block) {
