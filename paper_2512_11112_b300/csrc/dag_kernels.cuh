@@ -244,6 +244,43 @@ __device__ __forceinline__ bool grid_barrier(DevState *ds, unsigned int target, 
     return s_ok != 0;
 }
 
+__device__ __forceinline__ unsigned int ld_relaxed_u32(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+// The relaxed barrier in two halves, so that a CTA can work between its
+// arrival and its wait.  Arrival: every thread of the CTA has finished the
+// layer; thread 0 counts the CTA (no ordering, as grid_barrier<true>).
+__device__ __forceinline__ void grid_arrive_relaxed(DevState *ds) {
+    __syncthreads();
+    if (threadIdx.x == 0) asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(&ds->bar_count) : "memory");
+}
+// Wait: thread 0 polls until `target` arrivals (bounded by spin_ns, as in
+// grid_barrier), then the CTA goes on together.
+__device__ __forceinline__ bool grid_wait_relaxed(DevState *ds, unsigned int target, uint64_t spin_ns) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned long long t0 = gtimer();
+        while (true) {
+            const unsigned int v = ld_relaxed_u32(&ds->bar_count);
+            if ((int)(v - target) >= 0) break;
+            if (ld_relaxed_u32(&ds->bar_abort)) { ok = 0; break; }
+            if (gtimer() - t0 > spin_ns) {
+                atomicOr(&ds->err_flags, ERR_TIMEOUT);
+                atomicExch(&ds->bar_abort, 1u);
+                ok = 0;
+                break;
+            }
+            __nanosleep(20);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 // Start of a run: the triple cursor the run consumes from, fresh barrier
 // counters and error flags.  Its argument is updated before every replay of
 // a captured run.
@@ -396,22 +433,27 @@ __device__ __forceinline__ void df_st2(uint64_t *p, uint64_t a, uint64_t b) {
 __device__ __forceinline__ void df_ld2(const uint64_t *p, uint64_t &a, uint64_t &b) {
     asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
 }
-__device__ __forceinline__ unsigned int ld_relaxed_u32(const unsigned int *p) {
-    unsigned int v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 
-// Reads the operand record of wire w; true when every word carries `tag`.
+// Issues the loads of the operand record of wire w (its first use waits).
 template <int NP>
-__device__ __forceinline__ bool df_fetch(const uint64_t *mir, uint32_t w, uint64_t tag, uint64_t (&v)[2 * NP]) {
+__device__ __forceinline__ void df_issue(const uint64_t *mir, uint32_t w, uint64_t (&v)[2 * NP]) {
     const uint64_t *p = mir + (size_t)w * (2 * NP);
 #pragma unroll
     for (int k = 0; k < NP; ++k) df_ld2(p + 2 * k, v[2 * k], v[2 * k + 1]);
+}
+// True when every word of a loaded record carries `tag`.
+template <int NP>
+__device__ __forceinline__ bool df_tagged(const uint64_t (&v)[2 * NP], uint64_t tag) {
     uint64_t bad = 0;
 #pragma unroll
     for (int k = 0; k < 2 * NP; ++k) bad |= (v[k] >> DF_TAG_SHIFT) ^ tag;
     return bad == 0;
+}
+// Reads the operand record of wire w; true when every word carries `tag`.
+template <int NP>
+__device__ __forceinline__ bool df_fetch(const uint64_t *mir, uint32_t w, uint64_t tag, uint64_t (&v)[2 * NP]) {
+    df_issue<NP>(mir, w, v);
+    return df_tagged<NP>(v, tag);
 }
 
 // Slow path of an operand wait: one sleep (doubling from poll_ns up to 16x),
@@ -437,12 +479,12 @@ __device__ __forceinline__ uint64_t df_ld1(const uint64_t *p) {
     return v;
 }
 
-// The operand record of wire w once it carries `tag` (bounded wait).  While
-// waiting, only the record's first word is polled (one sector); the whole
-// record is read again once that word carries the tag.
+// The operand record of wire w once it carries `tag`, after a first read
+// that did not (bounded wait).  While waiting, only the record's first word
+// is polled (one sector); the whole record is read again once that word
+// carries the tag.
 template <int NP>
-__device__ __forceinline__ bool df_get(const DagArgs<F61> &a, uint32_t w, uint64_t tag, uint64_t (&v)[2 * NP]) {
-    if (df_fetch<NP>(a.mir, w, tag, v)) return true;
+__device__ __forceinline__ bool df_wait(const DagArgs<F61> &a, uint32_t w, uint64_t tag, uint64_t (&v)[2 * NP]) {
     const uint64_t *p = a.mir + (size_t)w * (2 * NP);
     const unsigned long long t0 = gtimer();
     unsigned int it = 0;
@@ -476,8 +518,12 @@ __device__ __forceinline__ bool df_gate(const DagArgs<F61> &a, const LayerRow &L
     using F = F61;
     const bool binary = cls <= C_SUB;
     uint64_t u[2 * NP], v[2 * NP];
-    if (!df_get<NP>(a, rec.x, wtag, u)) return false;
-    if (binary && !df_get<NP>(a, rec.y, tag, v)) return false;
+    // both operands' loads in flight at once; a wait only for a record whose
+    // first read missed its tag
+    df_issue<NP>(a.mir, rec.x, u);
+    if (binary) df_issue<NP>(a.mir, rec.y, v);
+    if (!df_tagged<NP>(u, wtag) && !df_wait<NP>(a, rec.x, wtag, u)) return false;
+    if (binary && !df_tagged<NP>(v, tag) && !df_wait<NP>(a, rec.y, tag, v)) return false;
     uint64_t z[NP], gz[NP];
     if (cls == C_MUL) {
         uint64_t x[NP], gx[NP], y[NP], gy[NP];
@@ -517,8 +563,10 @@ __device__ __forceinline__ bool df_gate(const DagArgs<F61> &a, const LayerRow &L
 // the CTAs in step (few operands are still in flight when a layer starts,
 // and their readers re-poll one word); with a slack it also lets a CTA start
 // a layer before the last few CTAs have finished the one before, whose
-// operands the tags then cover.  The inputs are first copied into the tagged
-// copy (one wire per thread, coalesced).
+// operands the tags then cover.  A thread's first gate of the next layer is
+// staged between the CTA's arrival at the barrier and its wait, off the
+// layer's critical path.  The inputs are first copied into the tagged copy
+// (one wire per thread, coalesced).
 template <int NP>
 __global__ void __launch_bounds__(256, 2) k_dag_tagged(DagArgs<F61> a) {
     using F = F61;
@@ -575,15 +623,17 @@ __global__ void __launch_bounds__(256, 2) k_dag_tagged(DagArgs<F61> a) {
             }
         }
         staged = false;
-        if (l + 1 < a.l1) {
-            L = load_row(a.lay, l + 1);
-            r = L.s[0] + tid;
-            staged = ok && r < L.s[5];
-            if (staged) stage_issue<F, NP>(a, L, r, class_of(L, r), tri_base, st);
-        }
-        if (l + 1 < a.l1 || a.record_ts) {
+        const bool more = l + 1 < a.l1;
+        if (more || a.record_ts) {
             ++nb;
-            ok = grid_barrier<true>(a.ds, nb * gridDim.x - a.slack, a.spin_ns) && ok;
+            grid_arrive_relaxed(a.ds);
+            if (more) {
+                L = load_row(a.lay, l + 1);
+                r = L.s[0] + tid;
+                staged = ok && r < L.s[5];
+                if (staged) stage_issue<F, NP>(a, L, r, class_of(L, r), tri_base, st);
+            }
+            ok = grid_wait_relaxed(a.ds, nb * gridDim.x - a.slack, a.spin_ns) && ok;
             if (stamp) a.ds->layer_ts[l + 1] = gtimer();
         }
     }
