@@ -13,7 +13,10 @@
 // (The int8 form kind::i8 is not available on sm_103a.)
 //
 // One CTA computes a 128 x 128 output tile of one job with three roles:
-// warp 0 loads digit-plane tiles with TMA (4-stage ring of 32 KB), warp 1
+// warp 0 loads digit-plane tiles with TMA (3-stage ring of 64 KB: 128 of
+// the inner dimension per stage, so the MMA thread waits once per 8 MMAs --
+// a barrier wait in that thread stalls it behind the MMAs it has issued,
+// and 4 MMAs per wait left the tensor pipe idle 40 % of the time), warp 1
 // issues the MMAs (and owns the tensor memory), warps 2..9 drain the
 // accumulators; two accumulators in tensor memory let the drain of one
 // digit pair overlap the MMAs of the next.  Every wait is bounded: on
@@ -34,9 +37,11 @@ namespace spdz {
 constexpr int TC_DIGITS = 9;
 constexpr int TC_DIGIT_BITS = 7;
 constexpr int TC_TILE = 128;          // output tile edge (M = N = 128)
-constexpr int TC_KB = 64;             // K elements per stage (128 bytes of bf16)
-constexpr int TC_STAGES = 4;
-constexpr int TC_STAGE_BYTES = 2 * TC_TILE * TC_KB * 2;   // A and B tiles
+constexpr int TC_KB = 64;             // K elements per TMA box (128 bytes of bf16, the swizzle span)
+constexpr int TC_KSTAGE = 128;        // K elements per stage: two boxes of each operand
+constexpr int TC_STAGES = 3;
+constexpr int TC_BOX_BYTES = TC_TILE * TC_KB * 2;            // one 128 x 64 bf16 box
+constexpr int TC_STAGE_BYTES = 4 * TC_BOX_BYTES;             // A and B, two boxes each
 constexpr int TC_THREADS = 320;       // 10 warps
 constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr unsigned long long TC_WAIT_NS = 1000000000ull;   // bound of one pipeline wait
@@ -224,7 +229,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
     __shared__ int issued_g, consumed_g;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row0 = (int64_t)blockIdx.y * TC_TILE, col0 = (int64_t)blockIdx.x * TC_TILE;
-    const int kblocks = (int)((job.k + TC_KB - 1) / TC_KB);
+    const int kblocks = (int)((job.k + TC_KSTAGE - 1) / TC_KSTAGE);
     const int chains = 2 * TC_DIGITS * TC_DIGITS;
 
     if (threadIdx.x == 0) {
@@ -263,10 +268,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
                     const int s = g % TC_STAGES;
                     const uint32_t ph = (uint32_t)(g / TC_STAGES) & 1u;
                     if (g >= TC_STAGES && !mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag)) break;
+                    // A boxes at 0 and 16 KB, B boxes at 32 and 48 KB (inner offsets 0, 64)
                     unsigned char *st = smem + (size_t)s * TC_STAGE_BYTES;
                     mbar_expect_tx(&full_bar[s], TC_STAGE_BYTES);
-                    tma_load_3d(st, Lm, kb * TC_KB, (int)row0, a, &full_bar[s]);
-                    tma_load_3d(st + TC_STAGE_BYTES / 2, Rm, kb * TC_KB, (int)col0, b, &full_bar[s]);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        tma_load_3d(st + h * TC_BOX_BYTES, Lm, kb * TC_KSTAGE + h * TC_KB, (int)row0, a, &full_bar[s]);
+                        tma_load_3d(st + (2 + h) * TC_BOX_BYTES, Rm, kb * TC_KSTAGE + h * TC_KB, (int)col0, b, &full_bar[s]);
+                    }
                     issued_g = g + 1;
                 }
             }
@@ -289,10 +298,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
                     consumed_g = g + 1;
                     tc_fence_after();
                     const unsigned char *st = smem + (size_t)s * TC_STAGE_BYTES;
-                    const uint64_t da = smem_desc(st), db = smem_desc(st + TC_STAGE_BYTES / 2);
 #pragma unroll
-                    for (int k16 = 0; k16 < TC_KB / 16; ++k16)
-                        mma_bf16(d_tmem, da + (uint64_t)(k16 * 2), db + (uint64_t)(k16 * 2), (kb | k16) != 0);
+                    for (int k16 = 0; k16 < TC_KSTAGE / 16; ++k16) {
+                        const int h = k16 / (TC_KB / 16), kk = k16 % (TC_KB / 16);
+                        const uint64_t da = smem_desc(st + h * TC_BOX_BYTES), db = smem_desc(st + (2 + h) * TC_BOX_BYTES);
+                        mma_bf16(d_tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), (kb | k16) != 0);
+                    }
                     mma_commit(&empty_bar[s]);     // frees the stage once these MMAs have read it
                 }
                 if (!ok) break;
