@@ -213,6 +213,8 @@ struct TcJob {
     int64_t ldo;
     int64_t m, n, k;       // k: inner length of each of the two segments
     int *err;              // set to 1 when a wait timed out
+    uint64_t *part;        // nsplit > 1: [nsplit][m][n] partial sums, combined by k_tc_combine
+    int nsplit;            // CTAs per output tile (blockIdx.z: which share of the digit-pair chains)
 };
 
 // maps: left segment 0, left segment 1, right segment 0, right segment 1
@@ -230,7 +232,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row0 = (int64_t)blockIdx.y * TC_TILE, col0 = (int64_t)blockIdx.x * TC_TILE;
     const int kblocks = (int)((job.k + TC_KSTAGE - 1) / TC_KSTAGE);
-    const int chains = 2 * TC_DIGITS * TC_DIGITS;
+    // this CTA's share [c0, c1) of the tile's 2 x 81 digit-pair chains
+    const int nchains = 2 * TC_DIGITS * TC_DIGITS;
+    const int c0 = (int)((int64_t)nchains * blockIdx.z / job.nsplit), c1 = (int)((int64_t)nchains * (blockIdx.z + 1) / job.nsplit);
+    const int chains = c1 - c0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
@@ -261,7 +266,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
         // ---------------------------------------------------------- TMA
         if (lane == 0) {
             int g = 0;
-            for (int c = 0; c < chains && !abort_flag; ++c) {
+            for (int ci = 0; ci < chains && !abort_flag; ++ci) {
+                const int c = c0 + ci;
                 const int seg = c / (TC_DIGITS * TC_DIGITS), a = (c / TC_DIGITS) % TC_DIGITS, b = c % TC_DIGITS;
                 const CUtensorMap *Lm = seg == 0 ? &L0 : &L1, *Rm = seg == 0 ? &R0 : &R1;
                 for (int kb = 0; kb < kblocks; ++kb, ++g) {
@@ -284,10 +290,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
         // ---------------------------------------------------------- MMA
         if (lane == 0) {
             int g = 0;
-            for (int c = 0; c < chains && !abort_flag; ++c) {
-                const int ab = c & 1;
-                const uint32_t acc_ph = (uint32_t)(c >> 1) & 1u;
-                if (c >= 2 && !mbar_wait(&acc_empty[ab], acc_ph ^ 1u, &abort_flag)) break;
+            for (int ci = 0; ci < chains && !abort_flag; ++ci) {
+                const int ab = ci & 1;
+                const uint32_t acc_ph = (uint32_t)(ci >> 1) & 1u;
+                if (ci >= 2 && !mbar_wait(&acc_empty[ab], acc_ph ^ 1u, &abort_flag)) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(ab * TC_TILE);
                 bool ok = true;
@@ -322,9 +328,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
         uint64_t sum[64];
 #pragma unroll
         for (int j = 0; j < 64; ++j) sum[j] = 0;
-        for (int c = 0; c < chains; ++c) {
-            const int ab = c & 1;
-            const uint32_t acc_ph = (uint32_t)(c >> 1) & 1u;
+        for (int ci = 0; ci < chains; ++ci) {
+            const int c = c0 + ci;
+            const int ab = ci & 1;
+            const uint32_t acc_ph = (uint32_t)(ci >> 1) & 1u;
             if (!mbar_wait(&acc_full[ab], acc_ph, &abort_flag)) break;
             tc_fence_after();
             const int a = (c / TC_DIGITS) % TC_DIGITS, b = c % TC_DIGITS;
@@ -347,13 +354,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
             if (lane == 0) mbar_arrive(&acc_empty[ab]);
         }
         if (!abort_flag && row < job.m) {
+            if (job.nsplit == 1) {
 #pragma unroll
-            for (int j = 0; j < 64; ++j) {
-                const int64_t col = col0 + half * 64 + j;
-                if (col < job.n) {
-                    uint64_t v = sum[j];
-                    if (job.add) v = F61::add(v, job.add[row * job.ldo + col]);
-                    job.out[row * job.ldo + col] = v;
+                for (int j = 0; j < 64; ++j) {
+                    const int64_t col = col0 + half * 64 + j;
+                    if (col < job.n) {
+                        uint64_t v = sum[j];
+                        if (job.add) v = F61::add(v, job.add[row * job.ldo + col]);
+                        job.out[row * job.ldo + col] = v;
+                    }
+                }
+            } else {
+                uint64_t *prow = job.part + ((int64_t)blockIdx.z * job.m + row) * job.n;
+#pragma unroll
+                for (int j = 0; j < 64; ++j) {
+                    const int64_t col = col0 + half * 64 + j;
+                    if (col < job.n) prow[col] = sum[j];
                 }
             }
         }
@@ -369,6 +385,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TC_TMEM_COLS) : "memory");
+    }
+}
+
+// out = add + sum of the nsplit partial tiles, mod p (elementwise).
+__global__ void k_tc_combine(const uint64_t *part, int nsplit, int64_t m, int64_t n, const uint64_t *add, uint64_t *out,
+                             int64_t ldo) {
+    const int64_t total = m * n, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        const int64_t r = i / n, c = i - r * n;
+        uint64_t v = add ? add[r * ldo + c] : 0;
+        for (int q = 0; q < nsplit; ++q) v = F61::add(v, __ldcs(reinterpret_cast<const unsigned long long *>(part) + q * total + i));
+        out[r * ldo + c] = v;
     }
 }
 
@@ -418,7 +446,21 @@ int matmul_tensor(spdz_ctx *ctx, const uint64_t *E, const uint64_t *Fm, const ui
     const int64_t kp = (k + 7) / 8 * 8;    // padded inner length: 16-byte TMA strides
     const size_t plane_l = (size_t)TC_DIGITS * m * kp * 2, plane_r = (size_t)TC_DIGITS * n * kp * 2;
     // digits of E and of every A block (left), of every folded right block and of F (right, transposed)
-    const size_t need = plane_l * (1 + 2 * NPn) + plane_r * (1 + 2 * NPn) + 256;
+    // CTAs per output tile: the smallest split (at most 8) whose last wave of
+    // one-CTA-per-SM launches is at least 95 % full
+    const int64_t tiles = ((n + TC_TILE - 1) / TC_TILE) * ((m + TC_TILE - 1) / TC_TILE);
+    int nsplit = 1;
+    {
+        double best = 0.0;
+        for (int ns = 1; ns <= 8; ++ns) {
+            const int64_t ctas = tiles * ns, waves = (ctas + ctx->sm_count - 1) / ctx->sm_count;
+            const double fill = (double)ctas / (double)(waves * ctx->sm_count);
+            if (fill > best + 1e-9) { best = fill; nsplit = ns; }
+            if (fill >= 0.95) break;
+        }
+    }
+    const size_t part_bytes = nsplit > 1 ? (size_t)nsplit * m * n * sizeof(uint64_t) : 0;
+    const size_t need = plane_l * (1 + 2 * NPn) + plane_r * (1 + 2 * NPn) + part_bytes + 512;
     static std::mutex mu;
     static TcWorkspace ws;   // shared by contexts of this process, grown on demand
     std::lock_guard<std::mutex> g(mu);
@@ -436,6 +478,7 @@ int matmul_tensor(spdz_ctx *ctx, const uint64_t *E, const uint64_t *Fm, const ui
     __nv_bfloat16 *dA = (__nv_bfloat16 *)((unsigned char *)dE + plane_l);
     __nv_bfloat16 *dF = (__nv_bfloat16 *)((unsigned char *)dA + plane_l * 2 * NPn);
     __nv_bfloat16 *dR = (__nv_bfloat16 *)((unsigned char *)dF + plane_r);
+    uint64_t *dP = (uint64_t *)((((uintptr_t)((unsigned char *)dR + plane_r * 2 * NPn)) + 255) & ~(uintptr_t)255);
     cudaMemsetAsync(err, 0, sizeof(int), ctx->stream);
     const int gb = 4 * ctx->sm_count;
     k_digits_rowmajor<<<gb, 256, 0, ctx->stream>>>(E, m, k, k, kp, dE);
@@ -455,7 +498,7 @@ int matmul_tensor(spdz_ctx *ctx, const uint64_t *E, const uint64_t *Fm, const ui
     CUtensorMap mE, mF;
     if (!make_map(&mE, dE, m, kp) || !make_map(&mF, dF, n, kp))
         return set_err(ctx, SPDZ_ERR_CUDA, "matmul tensor: tensor map encoding failed");
-    dim3 grid((unsigned)((n + TC_TILE - 1) / TC_TILE), (unsigned)((m + TC_TILE - 1) / TC_TILE));
+    dim3 grid((unsigned)((n + TC_TILE - 1) / TC_TILE), (unsigned)((m + TC_TILE - 1) / TC_TILE), (unsigned)nsplit);
     for (int w = 0; w < 2; ++w)
         for (int i = 0; i < NPn; ++i) {
             const int j = w * NPn + i;
@@ -470,9 +513,15 @@ int matmul_tensor(spdz_ctx *ctx, const uint64_t *E, const uint64_t *Fm, const ui
             job.n = n;
             job.k = kp;
             job.err = err;
+            job.part = dP;
+            job.nsplit = nsplit;
             // left [E | A_j], right [Rfold_j ; F] (transposed: rows are output columns)
             k_tc_gemm<<<grid, TC_THREADS, smem, ctx->stream>>>(mE, mA, mR, mF, job);
             if (int rc = check_launch(ctx, "matmul tensor gemm")) return rc;
+            if (nsplit > 1) {
+                k_tc_combine<<<gb, 256, 0, ctx->stream>>>(dP, nsplit, m, n, job.add, job.out, job.ldo);
+                if (int rc = check_launch(ctx, "matmul tensor combine")) return rc;
+            }
         }
     int herr = 0;
     cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
