@@ -120,6 +120,44 @@ def test_mul_batch_and_check_match_oracle(p, n, N, off):
         S.spdz_ctx_destroy(ctx)
 
 
+@pytest.mark.parametrize("p", [O.P61, O.P127])
+def test_mul_batch_full_size_sampled(p):
+    """The batch the benchmark times: 2^24 products, 3 parties, in one call on
+    the full buffers.  Sampled products (the ends, the middle, 16-byte vector
+    edges and random indices) against the oracle, which deals each sampled
+    index's inputs and triple from the same counters; the check over all
+    2^25 opened values passes and its sigma sums to zero."""
+    n, N, seed, chk = 3, 2**24, 91, 17
+    ctx = ctx_for(n, p)
+    try:
+        dw = DeviceWorld(ctx, p, n, seed, N, N)
+        S.spdz_set_check_seed(ctx, chk)
+        z = SH.alloc(dw.field, n, N)
+        opened = SH.zeros(dw.field, 2 * N)
+        x, y = dw.inputs
+        S.spdz_mul_batch(ctx, x.buf(), y.buf(), z.buf(), N, opened)
+        sigma = O.zeros(p, n)
+        assert S.spdz_mac_check(ctx, sigma)
+        assert sum(O.to_ints(p, sigma)) % p == 0
+        rng = np.random.default_rng(3)
+        idx = np.unique(np.concatenate([[0, 1, 2, 3, N // 2 - 1, N // 2, N - 2, N - 1],
+                                        rng.integers(0, N, 24)])).astype(np.int64)
+        ti = torch.from_numpy(idx).to(z.val.device)
+        gv, gm = SH.to_host(z.val[:, ti]), SH.to_host(z.mac[:, ti])
+        go = SH.to_host(opened[torch.from_numpy(np.stack([2 * idx, 2 * idx + 1], 1).reshape(-1)).to(opened.device)])
+        alpha, ash = O.deal_alpha(p, n, seed)
+        for s_, j in enumerate(idx.tolist()):
+            xv, xm, _ = O.deal_shared(p, n, seed, O.K_INPUT, 0, j, 1, alpha)
+            yv, ym, _ = O.deal_shared(p, n, seed, O.K_INPUT, 1, j, 1, alpha)
+            tri = O.deal_triples(p, n, seed, j, 1, alpha)
+            zv, zm, _, _, log = O.mul(p, xv, xm, yv, ym, tri, ash)
+            assert_equal(gv[:, s_], zv[:, 0], f"z val at {j}")
+            assert_equal(gm[:, s_], zm[:, 0], f"z mac at {j}")
+            assert_equal(go[2 * s_:2 * s_ + 2], log.vals, f"eps/delta at {j}")
+    finally:
+        S.spdz_ctx_destroy(ctx)
+
+
 @pytest.mark.parametrize("p", [O.P61, O.P127, O.P32])
 def test_two_batches_one_epoch_then_next_epoch(p):
     n, N, seed, chk = 3, 3000, 77, 9
@@ -220,6 +258,37 @@ def test_innerprod_matches_oracle(p, P, L):
         assert_equal(gv, zv, "ip val")
         assert_equal(gm, zm, "ip mac")
         assert_equal(sig, osig, "sigma")
+    finally:
+        S.spdz_ctx_destroy(ctx)
+
+
+def test_innerprod_full_size_sampled():
+    """The inner-product workload at its full size (16,384 products of
+    length 1024, 3 parties, p = 2^127-1) in one call: sampled products (the
+    first, the last and random ones) against the oracle over each product's
+    own 1024 dealt terms; the check over all 2^25 opened values passes and
+    its sigma sums to zero."""
+    p, n, P, L, seed, chk = O.P127, 3, 16384, 1024, 23, 6
+    ctx = ctx_for(n, p)
+    try:
+        dw = DeviceWorld(ctx, p, n, seed, P * L, P * L)
+        S.spdz_set_check_seed(ctx, chk)
+        z = SH.alloc(dw.field, n, P)
+        S.spdz_innerprod_batch(ctx, dw.inputs[0].buf(), dw.inputs[1].buf(), z.buf(), P, L)
+        sig = O.zeros(p, n)
+        assert S.spdz_mac_check(ctx, sig)
+        assert sum(O.to_ints(p, sig)) % p == 0
+        gv, gm = z.host()
+        alpha, ash = O.deal_alpha(p, n, seed)
+        rng = np.random.default_rng(5)
+        for q in sorted({0, 1, P // 2, P - 1, *rng.integers(0, P, 8).tolist()}):
+            j0 = q * L
+            xv, xm, _ = O.deal_shared(p, n, seed, O.K_INPUT, 0, j0, L, alpha)
+            yv, ym, _ = O.deal_shared(p, n, seed, O.K_INPUT, 1, j0, L, alpha)
+            tri = O.deal_triples(p, n, seed, j0, L, alpha)
+            zv, zm, _, _, _ = O.innerprod(p, 1, L, xv, xm, yv, ym, tri, ash)
+            assert_equal(gv[:, q], zv[:, 0], f"ip val {q}")
+            assert_equal(gm[:, q], zm[:, 0], f"ip mac {q}")
     finally:
         S.spdz_ctx_destroy(ctx)
 
