@@ -2,26 +2,29 @@
 // (Sec. III-D.3 product Z_i = C_i + [E | A_i] [B'_i ; F], see matmul.cu).
 //
 // Exact modular products on the tensor cores.  Every 61-bit operand x is
-// written in balanced base-2^7 digits, x = sum_d x_d 2^(7d) with
-// x_d in [-64, 64] (9 digits), each exactly representable in bf16.  For two
-// operands the digit-pair products L_a * R_b (tcgen05.mma kind::f16, bf16
-// inputs, f32 accumulation in tensor memory) are integers of magnitude at
-// most 2048 * 64 * 64 = 2^23 for an inner length of 2048, so the f32 sums are
-// exact; the epilogue turns each into a field element and multiplies it by
-// 2^(7(a+b)) mod 2^61 - 1 (a 61-bit rotation), accumulating mod p:
-//   L * R = sum_{a,b} 2^(7(a+b)) (L_a * R_b)   (mod p).
+// written in balanced base-2^8 digits, x = sum_d x_d 2^(8d) with
+// x_d in [-128, 127] (8 digits, the top one in [0, 33]), each exactly
+// representable in bf16.  For two operands the digit-pair products
+// L_a * R_b (tcgen05.mma kind::f16, bf16 inputs, f32 accumulation in tensor
+// memory) are summed over chunks of at most 1024 of the inner dimension:
+// integers of magnitude at most 1024 * 128 * 128 = 2^24, so every partial
+// f32 sum is exact; the epilogue turns each into a field element and
+// multiplies it by 2^(8(a+b)) mod 2^61 - 1 (a 61-bit rotation), accumulating
+// mod p:
+//   L * R = sum_{chunks} sum_{a,b} 2^(8(a+b)) (L_a * R_b)   (mod p).
 // (The int8 form kind::i8 is not available on sm_103a.)
 //
-// One CTA computes a 128 x 128 output tile of one job with three roles:
-// warp 0 loads digit-plane tiles with TMA (3-stage ring of 64 KB: 128 of
-// the inner dimension per stage, so the MMA thread waits once per 8 MMAs --
-// a barrier wait in that thread stalls it behind the MMAs it has issued,
-// and 4 MMAs per wait left the tensor pipe idle 40 % of the time), warp 1
-// issues the MMAs (and owns the tensor memory), warps 2..9 drain the
-// accumulators; two accumulators in tensor memory let the drain of one
-// digit pair overlap the MMAs of the next.  Every wait is bounded: on
-// timeout the CTA raises an error flag, stops issuing work, waits for what
-// it already issued and frees its tensor memory.
+// One CTA computes a 128 x 128 output tile of one job (or its share of the
+// tile's digit-pair chains) with three roles: warp 0 loads digit-plane
+// tiles with TMA (3-stage ring of 64 KB: 128 of the inner dimension per
+// stage, so the MMA thread waits once per 8 MMAs -- a barrier wait in that
+// thread stalls it behind the MMAs it has issued, and 4 MMAs per wait left
+// the tensor pipe idle 40 % of the time), warp 1 issues the MMAs (and owns
+// the tensor memory), warps 2..9 drain the accumulators; two accumulators in
+// tensor memory let the drain of one chain overlap the MMAs of the next.
+// Every wait is bounded: on timeout the CTA raises an error flag, stops
+// issuing work, waits for what it already issued and frees its tensor
+// memory.
 #include <cuda.h>
 
 #include <algorithm>
@@ -34,8 +37,9 @@
 
 namespace spdz {
 
-constexpr int TC_DIGITS = 9;
-constexpr int TC_DIGIT_BITS = 7;
+constexpr int TC_DIGITS = 8;
+constexpr int TC_DIGIT_BITS = 8;
+constexpr int TC_KCHUNK = 1024;       // inner length of one exact digit-pair sum
 constexpr int TC_TILE = 128;          // output tile edge (M = N = 128)
 constexpr int TC_KB = 64;             // K elements per TMA box (128 bytes of bf16, the swizzle span)
 constexpr int TC_KSTAGE = 128;        // K elements per stage: two boxes of each operand
@@ -47,16 +51,16 @@ constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr unsigned long long TC_WAIT_NS = 1000000000ull;   // bound of one pipeline wait
 
 // ----------------------------------------------------------- digit planes
-// x in [0, p) -> 9 balanced digits (low first): d = x mod 128 taken in
-// [-64, 63], then x = (x - d) / 128; the top digit is in [0, 33].
+// x in [0, p) -> 8 balanced digits (low first): d = x mod 256 taken in
+// [-128, 127], then x = (x - d) / 256; the top digit is in [0, 33].
 __device__ __forceinline__ void balanced_digits(uint64_t x, float (&d)[TC_DIGITS]) {
     int64_t t = (int64_t)x;
 #pragma unroll
     for (int j = 0; j < TC_DIGITS - 1; ++j) {
-        int v = (int)(t & 127);
-        if (v >= 64) v -= 128;
+        int v = (int)(t & 255);
+        if (v >= 128) v -= 256;
         d[j] = (float)v;
-        t = (t - v) >> 7;
+        t = (t - v) >> 8;
     }
     d[TC_DIGITS - 1] = (float)t;
 }
@@ -198,6 +202,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
                    "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
                  : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                 "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -231,9 +244,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
     __shared__ int issued_g, consumed_g;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row0 = (int64_t)blockIdx.y * TC_TILE, col0 = (int64_t)blockIdx.x * TC_TILE;
-    const int kblocks = (int)((job.k + TC_KSTAGE - 1) / TC_KSTAGE);
-    // this CTA's share [c0, c1) of the tile's 2 x 81 digit-pair chains
-    const int nchains = 2 * TC_DIGITS * TC_DIGITS;
+    // chains: (segment, inner chunk of TC_KCHUNK, digit a, digit b); this
+    // CTA's share [c0, c1) of the tile's chains
+    const int nchunks = (int)((job.k + TC_KCHUNK - 1) / TC_KCHUNK);
+    const int pairs = TC_DIGITS * TC_DIGITS;
+    const int nchains = 2 * nchunks * pairs;
+    auto chain_kblocks = [&](int kc) {
+        const int64_t len = min((int64_t)TC_KCHUNK, job.k - (int64_t)kc * TC_KCHUNK);
+        return (int)((len + TC_KSTAGE - 1) / TC_KSTAGE);
+    };
     const int c0 = (int)((int64_t)nchains * blockIdx.z / job.nsplit), c1 = (int)((int64_t)nchains * (blockIdx.z + 1) / job.nsplit);
     const int chains = c1 - c0;
 
@@ -268,8 +287,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
             int g = 0;
             for (int ci = 0; ci < chains && !abort_flag; ++ci) {
                 const int c = c0 + ci;
-                const int seg = c / (TC_DIGITS * TC_DIGITS), a = (c / TC_DIGITS) % TC_DIGITS, b = c % TC_DIGITS;
+                const int seg = c / (nchunks * pairs), kc = (c / pairs) % nchunks;
+                const int a = (c / TC_DIGITS) % TC_DIGITS, b = c % TC_DIGITS;
                 const CUtensorMap *Lm = seg == 0 ? &L0 : &L1, *Rm = seg == 0 ? &R0 : &R1;
+                const int kblocks = chain_kblocks(kc), kbase = kc * TC_KCHUNK;
                 for (int kb = 0; kb < kblocks; ++kb, ++g) {
                     const int s = g % TC_STAGES;
                     const uint32_t ph = (uint32_t)(g / TC_STAGES) & 1u;
@@ -279,8 +300,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
                     mbar_expect_tx(&full_bar[s], TC_STAGE_BYTES);
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        tma_load_3d(st + h * TC_BOX_BYTES, Lm, kb * TC_KSTAGE + h * TC_KB, (int)row0, a, &full_bar[s]);
-                        tma_load_3d(st + (2 + h) * TC_BOX_BYTES, Rm, kb * TC_KSTAGE + h * TC_KB, (int)col0, b, &full_bar[s]);
+                        const int kx = kbase + kb * TC_KSTAGE + h * TC_KB;
+                        tma_load_3d(st + h * TC_BOX_BYTES, Lm, kx, (int)row0, a, &full_bar[s]);
+                        tma_load_3d(st + (2 + h) * TC_BOX_BYTES, Rm, kx, (int)col0, b, &full_bar[s]);
                     }
                     issued_g = g + 1;
                 }
@@ -296,6 +318,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
                 if (ci >= 2 && !mbar_wait(&acc_empty[ab], acc_ph ^ 1u, &abort_flag)) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(ab * TC_TILE);
+                const int kblocks = chain_kblocks(((c0 + ci) / pairs) % nchunks);
                 bool ok = true;
                 for (int kb = 0; kb < kblocks; ++kb, ++g) {
                     const int s = g % TC_STAGES;
@@ -325,7 +348,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
         const int quad = warp & 3;                  // TMEM lanes 32*quad .. +31 (rows)
         const int half = ew >> 2;                   // columns 64*half .. +63
         const int64_t row = row0 + quad * 32 + lane;
-        uint64_t sum[64];
+        // Each accumulator entry v is an integer with |v| <= 2^24: it is
+        // taken as v + 2^24 >= 0 and the offsets, sum_c 2^24 2^(e_c) mod p,
+        // come off once at the end.  Sums are kept below 2^61 + 2 by one
+        // fold per addition (2^61 == 1) and reduced at the end.
+        uint64_t sum[64], off = 0;
 #pragma unroll
         for (int j = 0; j < 64; ++j) sum[j] = 0;
         for (int ci = 0; ci < chains; ++ci) {
@@ -336,22 +363,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
             tc_fence_after();
             const int a = (c / TC_DIGITS) % TC_DIGITS, b = c % TC_DIGITS;
             const int e = (TC_DIGIT_BITS * (a + b)) % 61;
+            off = F61::add(off, rot61(1ull << 24, e));
             const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ab * TC_TILE + half * 64);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                uint32_t r[16];
-                tmem_ld16(taddr + (uint32_t)(q * 16), r);
+            for (int q = 0; q < 2; ++q) {
+                uint32_t r[32];
+                tmem_ld32(taddr + (uint32_t)(q * 32), r);
                 tmem_wait_ld();
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int64_t v = (int64_t)__float2ll_rn(__uint_as_float(r[j]));   // exact integer
-                    const uint64_t fv = v < 0 ? F61::P - (uint64_t)(-v) : (uint64_t)v;
-                    sum[q * 16 + j] = F61::add(sum[q * 16 + j], rot61(fv, e));
+                for (int j = 0; j < 32; ++j) {
+                    const int32_t v = __float2int_rn(__uint_as_float(r[j]));        // exact, |v| <= 2^24
+                    const uint64_t u = (uint64_t)(uint32_t)(v + (1 << 24));           // [0, 2^25]
+                    const uint64_t t = sum[q * 32 + j] + rot61(u, e);                 // < 2^62 + 2
+                    sum[q * 32 + j] = (t & F61::P) + (t >> 61);                       // < 2^61 + 2
                 }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[ab]);
+        }
+#pragma unroll
+        for (int j = 0; j < 64; ++j) {
+            uint64_t v = sum[j];
+            v = v >= F61::P ? v - F61::P : v;                 // canonical (v <= p + 1 before)
+            sum[j] = F61::sub(v, off);
         }
         if (!abort_flag && row < job.m) {
             if (job.nsplit == 1) {

@@ -134,3 +134,77 @@ def test_benchmark_size_sampled_entries(path, dim):
     assert_equal(d["Z"][0][:, idx], Zv, "sampled Z values")
     assert_equal(d["Z"][1][:, idx], Zm, "sampled Z MACs")
     assert_equal(d["C"][0][:, idx], Cv[:, idx], "sampled C values")
+
+
+def _worst_digit_value():
+    """A value of [0, p) whose balanced base-2^8 digits are -128 in the seven
+    low places (and 1 on top): every digit-pair product of two such values
+    is 128 * 128 = 2^14, the largest a digit pair can give."""
+    v = sum(-128 * 256**i for i in range(7)) + 256**7
+    assert 0 < v < P
+    t, digits = v, []
+    for _ in range(7):
+        d = t % 256
+        d = d - 256 if d >= 128 else d
+        digits.append(d)
+        t = (t - d) // 256
+    assert digits == [-128] * 7 and t == 1
+    return v
+
+
+@pytest.mark.parametrize("path", [0, 1])
+def test_largest_digit_sums_stay_exact(path):
+    """Shares built so that the opened E, and the right operand E is
+    multiplied by in the value product of party 0 (B_0 + F), hold in every
+    entry a value whose low digits are all -128: each digit-pair sum over an
+    inner chunk of 1024 is then exactly 2^24, the largest the tensor path
+    allows.  Every entry of Z and gamma(Z) equals the oracle, and the check
+    over E and F passes."""
+    if path == 1 and not _tensor_path_available():
+        pytest.skip("tensor path not built")
+    n, m, k, nn = 2, 64, 2048, 64
+    f = S.SPDZ_F61
+    ctx = ctx_for(n, P)
+    try:
+        ash_d = SH.zeros(f, n)
+        S.spdz_deal_alpha(ctx, SEED, ash_d)
+        A, B, Cm = SH.alloc(f, n, m * k), SH.alloc(f, n, k * nn), SH.alloc(f, n, m * nn)
+        S.spdz_deal_matrix_triple(ctx, SEED, SUB, m, k, nn, ash_d, A.buf(), B.buf(), Cm.buf())
+        alpha, ash = O.deal_alpha(P, n, SEED)
+        al = O.to_ints(P, ash)
+        (Av, Am), (Bv, Bm) = A.host(), B.host()
+        w = _worst_digit_value()
+        Ei = [w] * (m * k)
+        B0 = O.to_ints(P, Bv[0])
+        Fi = [(w - b) % P for b in B0]                    # B_0 + F = w everywhere
+        Xv, Xm, Yv, Ym = (O.zeros(P, n, m * k), O.zeros(P, n, m * k), O.zeros(P, n, k * nn), O.zeros(P, n, k * nn))
+        for i in range(n):
+            ai, gai = O.to_ints(P, Av[i]), O.to_ints(P, Am[i])
+            bi, gbi = O.to_ints(P, Bv[i]), O.to_ints(P, Bm[i])
+            Xv[i] = O.to_array(P, [(a + (e if i == 0 else 0)) % P for a, e in zip(ai, Ei)])
+            Xm[i] = O.to_array(P, [(g + al[i] * e) % P for g, e in zip(gai, Ei)])
+            Yv[i] = O.to_array(P, [(b + (x if i == 0 else 0)) % P for b, x in zip(bi, Fi)])
+            Ym[i] = O.to_array(P, [(g + al[i] * x) % P for g, x in zip(gbi, Fi)])
+        X, Y = SH.alloc(f, n, m * k), SH.alloc(f, n, k * nn)
+        X.val[:, :m * k] = SH.from_host(Xv)
+        X.mac[:, :m * k] = SH.from_host(Xm)
+        Y.val[:, :k * nn] = SH.from_host(Yv)
+        Y.mac[:, :k * nn] = SH.from_host(Ym)
+        S.spdz_load_preproc(ctx, ash_d, None, None, None, 0)
+        S.spdz_set_check_seed(ctx, CHK)
+        S.spdz_load_matrix_preproc(ctx, A.buf(), B.buf(), Cm.buf(), m, k, nn)
+        Z = SH.alloc(f, n, m * nn)
+        E, F = SH.zeros(f, m * k), SH.zeros(f, k * nn)
+        S.spdz_matmul(ctx, X.buf(), Y.buf(), Z.buf(), m, k, nn, path, E, F)
+        assert S.spdz_mac_check(ctx)
+        assert O.to_ints(P, SH.to_host(E)) == Ei
+        assert O.to_ints(P, SH.to_host(F)) == Fi
+        Cv, Cmm = Cm.host()
+        tri = O.Triples(Av, Am, Bv, Bm, Cv, Cmm)
+        rows, cols = np.divmod(np.arange(m * nn), nn)
+        Zv, Zm = O.mat_entries(P, m, k, nn, O.to_array(P, Ei), O.to_array(P, Fi), tri, ash, rows, cols)
+        gv, gm = Z.host()
+        assert_equal(gv, Zv, "Z values")
+        assert_equal(gm, Zm, "Z MACs")
+    finally:
+        S.spdz_ctx_destroy(ctx)
