@@ -213,8 +213,12 @@ __device__ __forceinline__ void mul_elems(const MulArgs<F> &a, int64_t e, uint64
     }
 }
 
+// Two CTAs of 256 threads per SM (at most 128 registers) while a thread's
+// NP x V products fit them; larger instances keep one.
+template <int NP, int V> constexpr int mul_min_blocks() { return NP * V <= 12 ? 2 : 1; }
+
 template <class F, int NP, int V>
-__global__ void __launch_bounds__(256) k_mul(MulArgs<F> a) {
+__global__ void __launch_bounds__(256, mul_min_blocks<NP, V>()) k_mul(MulArgs<F> a) {
     using T = typename F::T;
     const uint64_t key = a.ds->key;
     T alpha[NP], acc[NP + 1];
