@@ -268,7 +268,7 @@ template <> struct Vec16<F61> {
 // forming D); a second pass reads B_i and gamma(B)_i for D B_i and
 // D gamma(B)_i.
 template <class F, int NP>
-__global__ void __launch_bounds__(256) k_ll_rows_vec(LLArgs<F> a) {
+__device__ __forceinline__ void ll_rows_vec_body(const LLArgs<F> &a) {
     using T = typename F::T;
     constexpr int V = Vec16<F>::V;
     const int lane = threadIdx.x & 31;
@@ -371,6 +371,19 @@ __global__ void __launch_bounds__(256) k_ll_rows_vec(LLArgs<F> a) {
     block_accumulate<F, NP + 1>(chk, a.ds->acc);
 }
 
+// The row kernel; the 2-party p61 layer runs three CTAs per SM (80
+// registers, a little spilling: measured 10 % faster), every other instance
+// the compiler's own register budget (three per SM made p = 2^32-5 no
+// faster and 3 parties slower).
+template <class F, int NP>
+__global__ void __launch_bounds__(256) k_ll_rows_vec(LLArgs<F> a) {
+    ll_rows_vec_body<F, NP>(a);
+}
+template <class F, int NP>
+__global__ void __launch_bounds__(256, 3) k_ll_rows_vec3(LLArgs<F> a) {
+    ll_rows_vec_body<F, NP>(a);
+}
+
 template <class F> static bool ll_vec_ok(const LLArgs<F> &a) {
     constexpr int V = Vec16<F>::V;
     auto al = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
@@ -425,7 +438,11 @@ static void launch_ll(spdz_ctx *ctx, LLState *s, const spdz_buf *W, const spdz_b
         a.dout = dout; a.din = din; a.R = R;
         a.base = base;
         a.ds = ctx->ds;
-        auto kr = ll_vec_ok(a) ? k_ll_rows_vec<F, NP> : k_ll_rows<F, NP>;
+        void (*kr)(LLArgs<F>) = k_ll_rows<F, NP>;
+        if (ll_vec_ok(a)) {
+            if constexpr (std::is_same_v<F, F61> && NP == 2) kr = k_ll_rows_vec3<F, NP>;
+            else kr = k_ll_rows_vec<F, NP>;
+        }
         kr<<<grid_for(ctx, (const void *)kr, 256, 0, dout * 32), 256, 0, ctx->stream>>>(a);
     }
 }
