@@ -508,22 +508,39 @@ __device__ __forceinline__ void df_store(uint64_t *mir, uint32_t w, uint64_t tag
     for (int k = 0; k < NP; ++k) df_st2(p + 2 * k, t[2 * k], t[2 * k + 1]);
 }
 
+// An input wire's shares from the caller's party-major wires (written
+// before the run, read-only during it), as a tagged-copy record.
+template <int NP>
+__device__ __forceinline__ void df_input(const DagArgs<F61> &a, uint32_t w, uint64_t (&v)[2 * NP]) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        v[i] = __ldg(reinterpret_cast<const unsigned long long *>(a.wv + i * a.ws + w));
+        v[NP + i] = __ldg(reinterpret_cast<const unsigned long long *>(a.wm + i * a.ws + w));
+    }
+}
+
 // One gate in tagged mode: fetch (and if needed wait for) the operands,
 // compute, store the output shares (caller's party-major wires, and the
-// tagged copy).
+// tagged copy).  inputs: every operand is an input wire (the first layer),
+// read from the caller's wires with no tag to wait for.
 template <int NP, class TRI>
 __device__ __forceinline__ bool df_gate(const DagArgs<F61> &a, const LayerRow &L, int32_t r, int cls, uint4 rec,
                                         uint64_t kconst, const TRI &tri, uint64_t key, uint64_t tag, uint64_t wtag,
-                                        const uint64_t (&alpha)[NP], uint64_t (&acc)[NP + 1]) {
+                                        const uint64_t (&alpha)[NP], uint64_t (&acc)[NP + 1], bool inputs) {
     using F = F61;
     const bool binary = cls <= C_SUB;
     uint64_t u[2 * NP], v[2 * NP];
-    // both operands' loads in flight at once; a wait only for a record whose
-    // first read missed its tag
-    df_issue<NP>(a.mir, rec.x, u);
-    if (binary) df_issue<NP>(a.mir, rec.y, v);
-    if (!df_tagged<NP>(u, wtag) && !df_wait<NP>(a, rec.x, wtag, u)) return false;
-    if (binary && !df_tagged<NP>(v, tag) && !df_wait<NP>(a, rec.y, tag, v)) return false;
+    if (inputs) {
+        df_input<NP>(a, rec.x, u);
+        if (binary) df_input<NP>(a, rec.y, v);
+    } else {
+        // both operands' loads in flight at once; a wait only for a record
+        // whose first read missed its tag
+        df_issue<NP>(a.mir, rec.x, u);
+        if (binary) df_issue<NP>(a.mir, rec.y, v);
+        if (!df_tagged<NP>(u, wtag) && !df_wait<NP>(a, rec.x, wtag, u)) return false;
+        if (binary && !df_tagged<NP>(v, tag) && !df_wait<NP>(a, rec.y, tag, v)) return false;
+    }
     uint64_t z[NP], gz[NP];
     if (cls == C_MUL) {
         uint64_t x[NP], gx[NP], y[NP], gy[NP];
@@ -556,6 +573,32 @@ __device__ __forceinline__ bool df_gate(const DagArgs<F61> &a, const LayerRow &L
     return true;
 }
 
+// A thread's gates of one layer: its staged first gate, then the rest with
+// direct loads.  False when an operand wait gave up.
+template <int NP>
+__device__ __forceinline__ bool df_layer(const DagArgs<F61> &a, const LayerRow &L, int32_t r, bool staged,
+                                         int32_t nthreads, const Stage<F61, NP> &st, uint64_t tri_base, uint64_t key,
+                                         uint64_t tag, uint64_t wtag, const uint64_t (&alpha)[NP],
+                                         uint64_t (&acc)[NP + 1], bool inputs) {
+    using F = F61;
+    bool ok = true;
+    if (staged) {
+        const int cls = class_of(L, r);
+        cp_async_wait_all();
+        const uint4 rec = st.rec[threadIdx.x];
+        const uint64_t kk = cls >= C_CMUL ? st.k[threadIdx.x] : 0;
+        ok = df_gate<NP>(a, L, r, cls, rec, kk, TriSmem<F, NP>{st.tri + threadIdx.x, st.B}, key, tag, wtag, alpha,
+                         acc, inputs);
+    }
+    for (int32_t q = r + nthreads; ok && q < L.s[5]; q += nthreads) {
+        const int cls = class_of(L, q);
+        GateIn<F, NP> g;
+        gate_load_direct<F, NP>(a, L, q, cls, tri_base, g);
+        ok = df_gate<NP>(a, L, q, cls, g.rec, g.k, TriRegs<F, NP>{g}, key, tag, wtag, alpha, acc, inputs);
+    }
+    return ok;
+}
+
 // The tagged form of the fused kernel (p61): gates read their operands from
 // the tagged copy (one wire's shares of every party in 2*NP consecutive
 // words, a third of the sectors of the party-major gathers) and validate
@@ -565,8 +608,7 @@ __device__ __forceinline__ bool df_gate(const DagArgs<F61> &a, const LayerRow &L
 // a layer before the last few CTAs have finished the one before, whose
 // operands the tags then cover.  A thread's first gate of the next layer is
 // staged between the CTA's arrival at the barrier and its wait, off the
-// layer's critical path.  The inputs are first copied into the tagged copy
-// (one wire per thread, coalesced).
+// layer's critical path.
 template <int NP>
 __global__ void __launch_bounds__(256, 2) k_dag_tagged(DagArgs<F61> a) {
     using F = F61;
@@ -588,40 +630,35 @@ __global__ void __launch_bounds__(256, 2) k_dag_tagged(DagArgs<F61> a) {
     int32_t r = L.s[0] + tid;
     bool staged = r < L.s[5];
     if (staged) stage_issue<F, NP>(a, L, r, class_of(L, r), tri_base, st);
-    // the inputs into the tagged copy (the first layer's staging is in flight)
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < a.n_in; w += nthreads) {
-        uint64_t z[NP], gz[NP];
+    // The inputs into the tagged copy, for the layers after the first (whose
+    // gates read them from the caller's wires): the threads with no gate in
+    // the first layer copy them at once; if every thread has one, all copy
+    // after their first-layer gates.  Either way before the first barrier.
+    const int64_t w0 = (int64_t)L.s[5] - L.s[0];
+    const bool copy_first = tid >= w0;
+    const int64_t cstart = w0 < nthreads ? tid - w0 : tid, cstride = w0 < nthreads ? nthreads - w0 : nthreads;
+    auto copy_inputs = [&]() {
+        for (int64_t w = cstart; w < a.n_in; w += cstride) {
+            uint64_t z[NP], gz[NP];
 #pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            // (canonical shares are below 2^61; the mask keeps a malformed
-            // input from reaching the tag bits)
-            z[i] = ld_cs<F>(a.wv + i * a.ws + w) & F::P;
-            gz[i] = ld_cs<F>(a.wm + i * a.ws + w) & F::P;
+            for (int i = 0; i < NP; ++i) {
+                // (canonical shares are below 2^61; the mask keeps a malformed
+                // input from reaching the tag bits)
+                z[i] = ld_cs<F>(a.wv + i * a.ws + w) & F::P;
+                gz[i] = ld_cs<F>(a.wm + i * a.ws + w) & F::P;
+            }
+            df_store<NP>(a.mir, (uint32_t)w, tag, z, gz);
         }
-        df_store<NP>(a.mir, (uint32_t)w, tag, z, gz);
-    }
+    };
+    if (copy_first) copy_inputs();
     bool ok = tag != 0;
     if (!ok && threadIdx.x == 0 && blockIdx.x == 0) atomicOr(&a.ds->err_flags, ERR_TIMEOUT);
     unsigned int nb = 0;
     for (int32_t l = a.l0; l < a.l1; ++l) {
         // testing: first operands after the first layer wait for a tag nobody writes
         const uint64_t wtag = (a.extra_arrivals && l > a.l0) ? 8u : tag;
-        if (ok) {
-            if (staged) {
-                const int cls = class_of(L, r);
-                cp_async_wait_all();
-                const uint4 rec = st.rec[threadIdx.x];
-                const uint64_t kk = cls >= C_CMUL ? st.k[threadIdx.x] : 0;
-                ok = df_gate<NP>(a, L, r, cls, rec, kk, TriSmem<F, NP>{st.tri + threadIdx.x, st.B}, key, tag, wtag,
-                                 alpha, acc);
-            }
-            for (int32_t q = r + nthreads; ok && q < L.s[5]; q += nthreads) {
-                const int cls = class_of(L, q);
-                GateIn<F, NP> g;
-                gate_load_direct<F, NP>(a, L, q, cls, tri_base, g);
-                ok = df_gate<NP>(a, L, q, cls, g.rec, g.k, TriRegs<F, NP>{g}, key, tag, wtag, alpha, acc);
-            }
-        }
+        if (ok) ok = df_layer<NP>(a, L, r, staged, nthreads, st, tri_base, key, tag, wtag, alpha, acc, l == a.l0);
+        if (l == a.l0 && w0 >= nthreads) copy_inputs();
         staged = false;
         const bool more = l + 1 < a.l1;
         if (more || a.record_ts) {
