@@ -365,19 +365,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
             const int e = (TC_DIGIT_BITS * (a + b)) % 61;
             off = F61::add(off, rot61(1ull << 24, e));
             const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ab * TC_TILE + half * 64);
+            // for e <= 36, u * 2^e <= 2^61 needs no wrap: a plain shift
+            auto drain = [&](auto nowrap) {
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                uint32_t r[32];
-                tmem_ld32(taddr + (uint32_t)(q * 32), r);
-                tmem_wait_ld();
+                for (int q = 0; q < 2; ++q) {
+                    uint32_t r[32];
+                    tmem_ld32(taddr + (uint32_t)(q * 32), r);
+                    tmem_wait_ld();
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int32_t v = __float2int_rn(__uint_as_float(r[j]));        // exact, |v| <= 2^24
-                    const uint64_t u = (uint64_t)(uint32_t)(v + (1 << 24));           // [0, 2^25]
-                    const uint64_t t = sum[q * 32 + j] + rot61(u, e);                 // < 2^62 + 2
-                    sum[q * 32 + j] = (t & F61::P) + (t >> 61);                       // < 2^61 + 2
+                    for (int j = 0; j < 32; ++j) {
+                        const int32_t v = __float2int_rn(__uint_as_float(r[j]));    // exact, |v| <= 2^24
+                        const uint64_t u = (uint64_t)(uint32_t)(v + (1 << 24));       // [0, 2^25]
+                        const uint64_t t = sum[q * 32 + j] + (decltype(nowrap)::value ? u << e : rot61(u, e));
+                        sum[q * 32 + j] = (t & F61::P) + (t >> 61);                   // < 2^61 + 2
+                    }
                 }
-            }
+            };
+            if (e <= 36) drain(std::true_type{});
+            else drain(std::false_type{});
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[ab]);
