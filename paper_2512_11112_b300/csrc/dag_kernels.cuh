@@ -631,12 +631,14 @@ __global__ void __launch_bounds__(256, 2) k_dag_tagged(DagArgs<F61> a) {
     bool staged = r < L.s[5];
     if (staged) stage_issue<F, NP>(a, L, r, class_of(L, r), tri_base, st);
     // The inputs into the tagged copy, for the layers after the first (whose
-    // gates read them from the caller's wires): the threads with no gate in
-    // the first layer copy them at once; if every thread has one, all copy
-    // after their first-layer gates.  Either way before the first barrier.
+    // gates read them from the caller's wires): when at least a quarter of
+    // the threads have no gate in the first layer, those copy them at once;
+    // otherwise every thread copies after its first-layer gates.  Either way
+    // before the first barrier.
     const int64_t w0 = (int64_t)L.s[5] - L.s[0];
-    const bool copy_first = tid >= w0;
-    const int64_t cstart = w0 < nthreads ? tid - w0 : tid, cstride = w0 < nthreads ? nthreads - w0 : nthreads;
+    const bool idle_copy = nthreads - w0 >= nthreads / 4;
+    const bool copy_first = idle_copy && tid >= w0;
+    const int64_t cstart = idle_copy ? tid - w0 : tid, cstride = idle_copy ? nthreads - w0 : nthreads;
     auto copy_inputs = [&]() {
         for (int64_t w = cstart; w < a.n_in; w += cstride) {
             uint64_t z[NP], gz[NP];
@@ -658,7 +660,7 @@ __global__ void __launch_bounds__(256, 2) k_dag_tagged(DagArgs<F61> a) {
         // testing: first operands after the first layer wait for a tag nobody writes
         const uint64_t wtag = (a.extra_arrivals && l > a.l0) ? 8u : tag;
         if (ok) ok = df_layer<NP>(a, L, r, staged, nthreads, st, tri_base, key, tag, wtag, alpha, acc, l == a.l0);
-        if (l == a.l0 && w0 >= nthreads) copy_inputs();
+        if (l == a.l0 && !idle_copy) copy_inputs();
         staged = false;
         const bool more = l + 1 < a.l1;
         if (more || a.record_ts) {

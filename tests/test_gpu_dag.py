@@ -165,6 +165,29 @@ def test_benchmark_sized_circuit_matches_oracle():
         dc.close()
 
 
+@pytest.mark.parametrize("widths", [[80000, 2000, 300], [70000, 500, 40], [4000, 3000, 7]])
+def test_tagged_first_layer_input_paths(widths):
+    """The tagged kernel's first layer reads its input operands from the
+    caller's wires while the inputs are copied into the tagged copy for the
+    later layers: by the threads without a first-layer gate (4000 gates), or
+    by every thread after its gate when the first layer is wider than the
+    grid (80000) or leaves fewer than a quarter of the threads idle (70000).
+    70,000 inputs, 2 parties, p61; every wire and sigma against the oracle."""
+    p, n = O.P61, 2
+    dag = W.small_dag(seed=sum(widths) % 97, p=p, n_inputs=70000, widths=widths)
+    dc = DeviceCircuit(dag, n, seed=4, runs=1)
+    try:
+        st, passed, sig = dc.run(S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=0, barrier_slack=24))
+        ev, em, ok, osig = oracle_run(dag, n, seed=4, run_index=0)
+        gv, gm = dc.wires.host()
+        assert_equal(gv, ev, "wire values")
+        assert_equal(gm, em, "wire MACs")
+        assert passed and ok and st.passed == 1
+        assert_equal(sig, osig, "sigma")
+    finally:
+        dc.close()
+
+
 def test_tagged_runs_cycle_over_many_replays():
     """Sixteen graph replays of the tagged plan (more than two cycles of the
     seven run tags, so the tagged wire copy is zeroed twice in between): every
