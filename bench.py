@@ -308,7 +308,11 @@ def beaver_roofline(torch, S, SH, hbm_peak, N=2**24, calls=4, field=None):
 def e2e_steps(circ, plan, steps):
     """Same metric through the public call with host buffers: each step
     copies its input shares and the triples it consumes from pinned host
-    memory, runs, and reads the last layer's output shares back."""
+    memory, runs, and copies the last layer's output shares back.  The
+    triples of step k+1 (their own pool slots) are copied on a second stream
+    while step k runs; the inputs (the same wires every step) are copied
+    after step k on the run's stream.  Every run checks its MACs on the
+    device; the verdict of the last one is read after the last step."""
     torch = circ.torch
     dag, S = circ.dag, circ.S
     nin, nm = dag.n_inputs, dag.n_mul
@@ -322,25 +326,36 @@ def e2e_steps(circ, plan, steps):
     for k in range(steps):
         lo = c0 + k * nm
         h_tri.append([part[:, lo:lo + nm].cpu().pin_memory() for t in circ.tri for part in (t.val, t.mac)])
-    h_out = [torch.empty_like(circ.wires.val[:, out_lo:dag.n_wires], device="cpu").pin_memory()
-             for _ in range(2)]
+    h_out = [[torch.empty_like(circ.wires.val[:, out_lo:dag.n_wires], device="cpu").pin_memory()
+              for _ in range(2)] for _ in range(2)]
     bi = sum(x.numel() * 8 for x in h_in) + sum(x.numel() * 8 for x in h_tri[0])
-    bo = sum(x.numel() * 8 for x in h_out) + 4
+    bo = sum(x.numel() * 8 for x in h_out[0]) + 4
+    side = torch.cuda.Stream()
+    ready = [torch.cuda.Event() for _ in range(steps)]
+
+    def copy_triples(k):
+        with torch.cuda.stream(side):
+            lo, j = c0 + k * nm, 0
+            for t in circ.tri:
+                for part in (t.val, t.mac):
+                    part[:, lo:lo + nm].copy_(h_tri[k][j], non_blocking=True)
+                    j += 1
+            ready[k].record(side)
+
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    copy_triples(0)
     for k in range(steps):
-        c = circ.T - S.spdz_triples_left(circ.ctx)
+        if k + 1 < steps:
+            copy_triples(k + 1)
         circ.wires.val[:, :nin].copy_(h_in[0], non_blocking=True)
         circ.wires.mac[:, :nin].copy_(h_in[1], non_blocking=True)
-        j = 0
-        for t in circ.tri:
-            for part in (t.val, t.mac):
-                part[:, c:c + nm].copy_(h_tri[k][j], non_blocking=True)
-                j += 1
+        circ.stream.wait_event(ready[k])
         circ.run(plan)
-        h_out[0].copy_(circ.wires.val[:, out_lo:dag.n_wires], non_blocking=True)
-        h_out[1].copy_(circ.wires.mac[:, out_lo:dag.n_wires], non_blocking=True)
-        ok = S.spdz_check_result(circ.ctx)       # reads the verdict: synchronises
+        h_out[k % 2][0].copy_(circ.wires.val[:, out_lo:dag.n_wires], non_blocking=True)
+        h_out[k % 2][1].copy_(circ.wires.mac[:, out_lo:dag.n_wires], non_blocking=True)
+    torch.cuda.synchronize()
+    ok = S.spdz_check_result(circ.ctx)
     dt = time.perf_counter() - t0
     return dt, bi, bo, ok
 
