@@ -371,6 +371,144 @@ __device__ __forceinline__ void ll_rows_vec_body(const LLArgs<F> &a) {
     block_accumulate<F, NP + 1>(chk, a.ds->acc);
 }
 
+// The same row kernel with each row split between two warps (half of the
+// columns each), a CTA taking blockDim/64 rows per round: with 8192 rows the
+// rounds divide evenly over the CTAs, where one warp per row left the last
+// of four rounds half empty.  Used for 2 parties at p = 2^32-5 (14 % faster
+// at 8192 x 8192); with more parties or p61 the extra live sums cost more
+// registers than the even rounds gain.
+template <class F, int NP>
+__device__ __forceinline__ void ll_rows_split_body(const LLArgs<F> &a) {
+    using T = typename F::T;
+    constexpr int V = Vec16<F>::V;
+    const int lane = threadIdx.x & 31;
+    const uint64_t key = a.ds->key;
+    T alpha[NP], chk[NP + 1];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
+#pragma unroll
+    for (int k = 0; k < NP + 1; ++k) chk[k] = F::zero();
+    // Two warps share a row (each one half of the columns); a CTA takes
+    // blockDim/64 rows per round, so the rounds divide the rows evenly over
+    // the CTAs; the halves' row sums meet in shared memory (two buffers by
+    // round parity, one CTA barrier per round).
+    constexpr int RMAX = 16;
+    __shared__ T part[2][RMAX][2 * NP + 1];
+    const int warp = threadIdx.x >> 5, rpc = (int)(blockDim.x >> 6), h = warp & 1;
+    const int64_t din = a.din, half = (din + 64 * V - 1) / (64 * V) * (32 * V);
+    const int64_t klo = h * half, khi = min(din, (int64_t)(h + 1) * half);
+    int par = 0;
+    for (int64_t base = (int64_t)blockIdx.x * rpc; base < a.dout; base += (int64_t)gridDim.x * rpc, par ^= 1) {
+        const int64_t r = base + (warp >> 1);
+        const bool live = r < a.dout;
+        const int64_t rr_ = live ? r : 0;
+        const int64_t t = rr_ / a.R;
+        const uint64_t pos0 = a.base + (uint64_t)(t * (din + a.R * din) + din + (rr_ - t * a.R) * din);
+        const int64_t row = rr_ * din;
+        const T *Et = a.E + t * din;
+        LAcc<F> db[NP], dgb[NP], ae[NP], gae[NP], de, c0, ci[NP];
+        for (int64_t k = klo + (int64_t)lane * V; live && k < khi; k += 32 * V) {
+            T e[V], d[V], rr[V];
+            Vec16<F>::ld(Et + k, e, false);
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                d[j] = F::zero();
+                rr[j] = Draw<F>::at(key, pos0 + (uint64_t)(k + j));
+            }
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                T w[V], av[V], gw[V], ga[V];
+                Vec16<F>::ld(a.wv + i * a.ws + row + k, w, true);
+                Vec16<F>::ld(a.av + i * a.as + row + k, av, true);
+                Vec16<F>::ld(a.wm + i * a.ws + row + k, gw, true);
+                Vec16<F>::ld(a.am + i * a.as + row + k, ga, true);
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    d[j] = F::add(d[j], F::sub(w[j], av[j]));
+                    ae[i].mac(av[j], e[j]);
+                    gae[i].mac(ga[j], e[j]);
+                    ci[i].mac(rr[j], F::sub(gw[j], ga[j]));
+                    if (j == 2) {          // at most three products between folds
+                        ae[i].flush();
+                        gae[i].flush();
+                        ci[i].flush();
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                c0.mac(rr[j], d[j]);
+                de.mac(d[j], e[j]);
+                if (j == 2) {
+                    c0.flush();
+                    de.flush();
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                T bv[V], gb[V];
+                const int64_t q = i * a.bs + t * din + k;
+                Vec16<F>::ld(a.bv + q, bv, false);
+                Vec16<F>::ld(a.bm + q, gb, false);
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    db[i].mac(d[j], bv[j]);
+                    dgb[i].mac(d[j], gb[j]);
+                    if (j == 2) {
+                        db[i].flush();
+                        dgb[i].flush();
+                    }
+                }
+                ae[i].flush();
+                gae[i].flush();
+                ci[i].flush();
+                db[i].flush();
+                dgb[i].flush();
+            }
+            c0.flush();
+            de.flush();
+            if (a.D) {
+#pragma unroll
+                for (int j = 0; j < V; ++j) F::st(a.D + row + k + j, d[j]);
+            }
+        }
+        chk[0] = F::add(chk[0], c0.get());
+#pragma unroll
+        for (int i = 0; i < NP; ++i) chk[1 + i] = F::add(chk[1 + i], ci[i].get());
+        // this half's row sums: z_i, gamma(z)_i (D B_i + A_i E and MACs), D.E
+        T zs[NP], gs[NP];
+        const T sde = warp_sum<F>(de.get());
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            zs[i] = warp_sum<F>(F::add(db[i].get(), ae[i].get()));
+            gs[i] = warp_sum<F>(F::add(dgb[i].get(), gae[i].get()));
+        }
+        if (h == 1 && lane == 0) {
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                part[par][warp >> 1][i] = zs[i];
+                part[par][warp >> 1][NP + i] = gs[i];
+            }
+            part[par][warp >> 1][2 * NP] = sde;
+        }
+        __syncthreads();
+        if (h == 0 && lane == 0 && live) {
+            const T sd = F::add(sde, part[par][warp >> 1][2 * NP]);
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                const T z = F::add(zs[i], part[par][warp >> 1][i]), gz = F::add(gs[i], part[par][warp >> 1][NP + i]);
+                T y = F::add(F::add(F::ld(a.cv + i * a.cs + r), z), F::ld(a.pv + i * a.ps + r));
+                if (i == 0) y = F::add(y, sd);
+                T gy = F::add(F::add(F::ld(a.cm + i * a.cs + r), gz), F::ld(a.pm + i * a.ps + r));
+                gy = F::add(gy, F::mul(alpha[i], sd));
+                F::st(a.yv + i * a.ys + r, y);
+                F::st(a.ym + i * a.ys + r, gy);
+            }
+        }
+    }
+    block_accumulate<F, NP + 1>(chk, a.ds->acc);
+}
+
 // The row kernel; the 2-party p61 layer runs three CTAs per SM (80
 // registers, a little spilling: measured 10 % faster), every other instance
 // the compiler's own register budget (three per SM made p = 2^32-5 no
@@ -382,6 +520,10 @@ __global__ void __launch_bounds__(256) k_ll_rows_vec(LLArgs<F> a) {
 template <class F, int NP>
 __global__ void __launch_bounds__(256, 3) k_ll_rows_vec3(LLArgs<F> a) {
     ll_rows_vec_body<F, NP>(a);
+}
+template <class F, int NP>
+__global__ void __launch_bounds__(256) k_ll_rows_split(LLArgs<F> a) {
+    ll_rows_split_body<F, NP>(a);
 }
 
 template <class F> static bool ll_vec_ok(const LLArgs<F> &a) {
@@ -441,6 +583,7 @@ static void launch_ll(spdz_ctx *ctx, LLState *s, const spdz_buf *W, const spdz_b
         void (*kr)(LLArgs<F>) = k_ll_rows<F, NP>;
         if (ll_vec_ok(a)) {
             if constexpr (std::is_same_v<F, F61> && NP == 2) kr = k_ll_rows_vec3<F, NP>;
+            else if constexpr (std::is_same_v<F, F32> && NP == 2) kr = k_ll_rows_split<F, NP>;
             else kr = k_ll_rows_vec<F, NP>;
         }
         kr<<<grid_for(ctx, (const void *)kr, 256, 0, dout * 32), 256, 0, ctx->stream>>>(a);
