@@ -740,8 +740,9 @@ def run_linear(args):
             "paper_note": "the paper's runtimes are on an RTX A6000 box with 64 CPU cores, wall-clock, setup "
                           "inclusion not stated; vs_baseline divides this layer's online time by the paper's best "
                           "(CPU back end, 64 threads)",
-            "roofline": {"bound": "hbm", "kernel": "k_ll_rows<F32,2> (+ k_ll_open_e)", "achieved": head["achieved_gbs"],
-                         "peak": hbm, "unit": "GB/s", "frac": head["frac"], "traffic": None, "peak_source": src,
+            "roofline": {"bound": "hbm", "kernel": "k_ll_rows_split<F32,2> (+ k_ll_open_e)",
+                         "achieved": head["achieved_gbs"], "peak": hbm, "unit": "GB/s", "frac": head["frac"],
+                         "traffic": read_traffic().get("k_ll_rows_split"), "peak_source": src,
                          "algorithmic_bytes_per_launch": head["algorithmic_bytes"]},
             "mac_check_ms": head["check_ms"], "mac_check_passed": head["mac_check_passed"],
             "cases": rows, "clocks": clk.summary()}
