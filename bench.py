@@ -830,13 +830,56 @@ def run_batch(args):
     hbm, src = peaks()
     sweep = batch_sweep(args, "p61", hbm)
     sweep32 = batch_sweep(args, "p32", hbm)
+    linear = linear_gates_roofline(args, hbm)
     line = {"metric": "Beaver mults/s, 2 parties, p=2^61-1, 2^16 products with one MAC check",
             "value": 2**16 / (sweep["2^16"]["with_check_us"] * 1e-6), "unit": "Beaver mults/s",
             "higher_is_better": True, "n_gpus": 1, "dtype": "u64", "data": "synthetic",
             "config": {"workload": "2^16 Beaver mults, n=2, p61, batch + MAC check (L2-resident: latency-bound); "
                                    "sweep to 2^26 for the bandwidth fraction", "bytes_per_mult": 192},
-            "sweep": sweep, "sweep_p32": sweep32, "hbm_peak_gbs": hbm, "peak_source": src}
+            "sweep": sweep, "sweep_p32": sweep32, "linear_gates": linear, "hbm_peak_gbs": hbm,
+            "peak_source": src}
     print(json.dumps(line), flush=True)
+
+
+def linear_gates_roofline(args, hbm):
+    """Stand-alone linear gates (spdz_linear), 2^24 elements, n=3, p61: ADD
+    and SUB read x and y and write z (6 n w = 144 B per element, values and
+    MACs), CMUL and CADD read x and write z (4 n w = 96 B)."""
+    import torch
+    from paper_2512_11112_b300 import shares as SH
+    from paper_2512_11112_b300 import spdz as S
+    n, N, f = 3, 2**24, S.SPDZ_F61
+    ctx = S.spdz_ctx_create(n, f, torch.cuda.current_stream().cuda_stream)
+    try:
+        ash = SH.zeros(f, n)
+        S.spdz_deal_alpha(ctx, 1, ash)
+        S.spdz_load_preproc(ctx, ash, None, None, None, 0)
+        x, y, z = (SH.alloc(f, n, N) for _ in range(3))
+        S.spdz_deal_shared(ctx, 1, S.SPDZ_KIND_INPUT, 0, 0, N, ash, None, x.buf())
+        S.spdz_deal_shared(ctx, 1, S.SPDZ_KIND_INPUT, 1, 0, N, ash, None, y.buf())
+        k = SH.to_host(SH.zeros(f, 1))
+        k[0] = 123456789
+        out = {}
+        for name, op, binary in (("add", S.SPDZ_OP_ADD, True), ("sub", S.SPDZ_OP_SUB, True),
+                                 ("cmul", S.SPDZ_OP_CMUL, False), ("cadd", S.SPDZ_OP_CADD, False)):
+            ts = []
+            for rep in range(max(args.warmup, 3) + 5):
+                e0, e1 = _events(torch)
+                e0.record()
+                S.spdz_linear(ctx, op, x.buf(), y.buf() if binary else None, None if binary else k, z.buf(), N)
+                e1.record()
+                torch.cuda.synchronize()
+                if rep >= max(args.warmup, 3):
+                    ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            bpe = (6 if binary else 4) * n * 8
+            gbs = bpe * N / (ms * 1e-3) / 1e9
+            out[name] = {"ms": round(ms, 4), "bytes_per_elem": bpe, "achieved_gbs": round(gbs, 1),
+                         "frac": round(gbs / hbm, 4)}
+        return {"kernel": "k_linear<F61,3> (spdz_linear)", "N": N, "ops": out,
+                "l2": "inputs larger than L2 (2.4 GB per ADD)"}
+    finally:
+        S.spdz_ctx_destroy(ctx)
 
 
 def batch_sweep(args, field, hbm):
