@@ -876,6 +876,23 @@ def linear_gates_roofline(args, hbm):
             gbs = bpe * N / (ms * 1e-3) / 1e9
             out[name] = {"ms": round(ms, 4), "bytes_per_elem": bpe, "achieved_gbs": round(gbs, 1),
                          "frac": round(gbs / hbm, 4)}
+        # the stand-alone open (spdz_open): reads every party's value and MAC
+        # share, writes the public value (2 n w + w = 56 B per element)
+        pub = SH.zeros(f, N)
+        ts = []
+        for rep in range(max(args.warmup, 3) + 5):
+            e0, e1 = _events(torch)
+            e0.record()
+            S.spdz_open(ctx, x.buf(), pub, N)
+            e1.record()
+            torch.cuda.synchronize()
+            if rep >= max(args.warmup, 3):
+                ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        bpe = (2 * n + 1) * 8
+        gbs = bpe * N / (ms * 1e-3) / 1e9
+        out["open"] = {"ms": round(ms, 4), "bytes_per_elem": bpe, "achieved_gbs": round(gbs, 1),
+                       "frac": round(gbs / hbm, 4), "kernel": "k_open<F61,3,2> (spdz_open)"}
         return {"kernel": "k_linear<F61,3> (spdz_linear)", "N": N, "ops": out,
                 "l2": "inputs larger than L2 (2.4 GB per ADD)"}
     finally:

@@ -279,7 +279,46 @@ __global__ void __launch_bounds__(256) k_innerprod(MulArgs<F> a) {
 }
 
 // ----------------------------------------------------------------- open
-template <class F, int NP>
+// Open V consecutive elements: sum the value shares, store the public value,
+// and add the check terms r v and r gamma_i (one reduction per two products
+// where the field allows it).
+template <class F, int NP, int V>
+__device__ __forceinline__ void open_elems(const MulArgs<F> &a, int64_t j, uint64_t key, typename F::T (&acc)[NP + 1]) {
+    using T = typename F::T;
+    T v[V], g[NP][V], r[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) v[q] = F::zero();
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        T x[V];
+        vld<F, V, false>(a.xv + i * a.xs + j, x);
+        vld<F, V, false>(a.xm + i * a.xs + j, g[i]);
+#pragma unroll
+        for (int q = 0; q < V; ++q) v[q] = F::add(v[q], x[q]);
+    }
+    vst<F, V>(a.opened + j, v);
+#pragma unroll
+    for (int q = 0; q < V; ++q) r[q] = Draw<F>::at(key, a.base + (uint64_t)(j + q));
+    if constexpr (V % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < V; q += 2) {
+            acc[0] = Fma<F>::f2(acc[0], r[q], v[q], r[q + 1], v[q + 1]);
+#pragma unroll
+            for (int i = 0; i < NP; ++i) acc[1 + i] = Fma<F>::f2(acc[1 + i], r[q], g[i][q], r[q + 1], g[i][q + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            acc[0] = F::add(acc[0], F::mul(r[q], v[q]));
+#pragma unroll
+            for (int i = 0; i < NP; ++i) acc[1 + i] = F::add(acc[1 + i], F::mul(r[q], g[i][q]));
+        }
+    }
+}
+
+// Stand-alone open: V elements per thread (16-byte loads when every row is
+// 16-byte aligned), the N % V tail one element per thread.
+template <class F, int NP, int V>
 __global__ void __launch_bounds__(256) k_open(MulArgs<F> a) {
     using T = typename F::T;
     const uint64_t key = a.ds->key;
@@ -287,19 +326,10 @@ __global__ void __launch_bounds__(256) k_open(MulArgs<F> a) {
 #pragma unroll
     for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < a.N; j += stride) {
-        T v = F::zero(), g[NP];
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            v = F::add(v, F::ld(a.xv + i * a.xs + j));
-            g[i] = F::ld(a.xm + i * a.xs + j);
-        }
-        F::st(a.opened + j, v);
-        T r = Draw<F>::at(key, a.base + (uint64_t)j);
-        acc[0] = F::add(acc[0], F::mul(r, v));
-#pragma unroll
-        for (int i = 0; i < NP; ++i) acc[1 + i] = F::add(acc[1 + i], F::mul(r, g[i]));
-    }
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t ng = a.N / V;
+    for (int64_t g = tid; g < ng; g += stride) open_elems<F, NP, V>(a, g * V, key, acc);
+    for (int64_t j = ng * V + tid; j < a.N; j += stride) open_elems<F, NP, 1>(a, j, key, acc);
     block_accumulate<F, NP + 1>(acc, a.ds->acc);
 }
 
@@ -504,9 +534,18 @@ int spdz_open(spdz_ctx *ctx, const spdz_buf *x, void *out_dev, int64_t N) {
         MulArgs<F> a{};
         a.xv = (const T *)x->val; a.xm = (const T *)x->mac; a.xs = x->stride;
         a.opened = (T *)out_dev; a.N = N; a.ds = ctx->ds; a.base = (uint64_t)ctx->opened;
+        // 16-byte vectors (2 p61 or 4 p32 elements) when every row is aligned
+        const size_t eb = sizeof(T);
+        constexpr int VV = std::is_same_v<F, F61> ? 2 : std::is_same_v<F, F32> ? 4 : 1;
+        const bool vec = VV > 1 && buf_vec_ok(x, eb) && ((uintptr_t)out_dev % 16 == 0);
         SPDZ_NP_SWITCH(ctx->n, {
-            auto kern = k_open<F, NP>;
-            kern<<<grid_for(ctx, (const void *)kern, 256, 0, N), 256, 0, ctx->stream>>>(a);
+            if (vec) {
+                auto kern = k_open<F, NP, VV>;
+                kern<<<grid_for(ctx, (const void *)kern, 256, 0, (N + VV - 1) / VV), 256, 0, ctx->stream>>>(a);
+            } else {
+                auto kern = k_open<F, NP, 1>;
+                kern<<<grid_for(ctx, (const void *)kern, 256, 0, N), 256, 0, ctx->stream>>>(a);
+            }
         });
     });
     if ((rc = check_launch(ctx, "open"))) return rc;

@@ -219,19 +219,22 @@ def test_linear_gates_match_oracle(p, n, N, off):
         S.spdz_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("p,n", [(O.P61, 3), (O.P127, 2), (O.P32, 3)])
-def test_open_and_check_match_oracle(p, n):
+@pytest.mark.parametrize("p,n,off", [(O.P61, 3, 0), (O.P127, 2, 0), (O.P32, 3, 0), (O.P61, 2, 1), (O.P32, 4, 3)])
+def test_open_and_check_match_oracle(p, n, off):
+    # off = 0 takes the 16-byte vector path with a ragged tail; an odd
+    # offset misaligns the rows and takes the one-element path
     N, seed, chk = 2049, 12, 3
     ctx = ctx_for(n, p)
     try:
-        dw = DeviceWorld(ctx, p, n, seed, N, 0)
+        dw = DeviceWorld(ctx, p, n, seed, N + off, 0)
         S.spdz_set_check_seed(ctx, chk)
         out = SH.zeros(dw.field, N)
-        S.spdz_open(ctx, dw.inputs[0].buf(), out, N)
+        S.spdz_open(ctx, dw.inputs[0].buf(off), out, N)
         sig = O.zeros(p, n)
         assert S.spdz_mac_check(ctx, sig)
-        ow = OracleWorld(p, n, seed, N, 0)
+        ow = OracleWorld(p, n, seed, N + off, 0)
         xv, xm, xs = ow.inputs[0]
+        xv, xm, xs = (np.ascontiguousarray(a) for a in (xv[:, off:], xm[:, off:], xs[off:]))
         assert_equal(host(out), xs, "opened values")
         _, osig, _, _ = O.mac_check(p, [O.OpenLog(O.open_(p, xv), xm)], ow.alpha_sh, chk, 0)
         assert_equal(sig, osig, "sigma")
