@@ -387,7 +387,7 @@ def run_ours(args, rank, world, local_rank):
     hbm, peak_src = peaks()
     dag = W.layered_dag(seed=2)
     steps, warmup = args.steps, args.warmup
-    e2e_n = min(steps, 5)
+    e2e_n = min(steps, 10)
     circ = Circuit(dag, seed=2 + 1000 * rank, runs=2 * (steps + warmup) + e2e_n, pool_runs=64)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     per_layer = S.plan(mode=S.SPDZ_SCHED_PER_LAYER, use_graph=0)
