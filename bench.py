@@ -893,6 +893,40 @@ def linear_gates_roofline(args, hbm):
         gbs = bpe * N / (ms * 1e-3) / 1e9
         out["open"] = {"ms": round(ms, 4), "bytes_per_elem": bpe, "achieved_gbs": round(gbs, 1),
                        "frac": round(gbs / hbm, 4), "kernel": "k_open<F61,3,2> (spdz_open)"}
+        # input sharing (spdz_input): reads x and the clear mask r, writes
+        # eps, reads and writes every party's mask shares (3 w + 4 n w = 120 B)
+        xin, eps = y.val[0], SH.zeros(f, N)
+        ts = []
+        for rep in range(max(args.warmup, 3) + 5):
+            e0, e1 = _events(torch)
+            e0.record()
+            S.spdz_input(ctx, xin, pub, x.buf(), z.buf(), N, eps)
+            e1.record()
+            torch.cuda.synchronize()
+            if rep >= max(args.warmup, 3):
+                ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        bpe = (3 + 4 * n) * 8
+        gbs = bpe * N / (ms * 1e-3) / 1e9
+        out["input"] = {"ms": round(ms, 4), "bytes_per_elem": bpe, "achieved_gbs": round(gbs, 1),
+                        "frac": round(gbs / hbm, 4), "kernel": "k_input<F61,3,2> (spdz_input)"}
+        # reveal (spdz_reveal): the open, the MAC check and the verdict read
+        # back before the values are released
+        ts, passed = [], True
+        for rep in range(max(args.warmup, 3) + 5):
+            e0, e1 = _events(torch)
+            e0.record()
+            passed = S.spdz_reveal(ctx, x.buf(), pub, N) and passed
+            e1.record()
+            torch.cuda.synchronize()
+            if rep >= max(args.warmup, 3):
+                ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        bpe = (2 * n + 1) * 8
+        gbs = bpe * N / (ms * 1e-3) / 1e9
+        out["reveal"] = {"ms": round(ms, 4), "bytes_per_elem": bpe, "achieved_gbs": round(gbs, 1),
+                         "frac": round(gbs / hbm, 4), "check_passed": bool(passed),
+                         "kernel": "k_open<F61,3,2> + k_check (spdz_reveal)"}
         return {"kernel": "k_linear<F61,3> (spdz_linear)", "N": N, "ops": out,
                 "l2": "inputs larger than L2 (2.4 GB per ADD)"}
     finally:

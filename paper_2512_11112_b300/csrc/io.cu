@@ -10,40 +10,83 @@
 // party adds alpha_i * eps to its MAC share.  Reveal: the shares are opened
 // (logged for the check), the check runs over the epoch, and the values are
 // released only if it passes.
+#include <type_traits>
+
 #include "dealer.cuh"
+#include "vec.cuh"
 
 namespace spdz {
 
 int launch_check(spdz_ctx *ctx, int final_check);
 
-template <class F, int NP>
-__global__ void k_input(const typename F::T *x, const typename F::T *r, const typename F::T *mv,
-                        const typename F::T *mm, int64_t ms, typename F::T *ov, typename F::T *om, int64_t os,
-                        int64_t N, typename F::T *eps_out, const DevState *ds) {
+template <class F> struct InArgs {
+    using T = typename F::T;
+    const T *x, *r, *mv, *mm;
+    int64_t ms;
+    T *ov, *om;
+    int64_t os;
+    int64_t N;
+    T *eps;       // optional: eps = x - r, published by the owner
+};
+
+// V consecutive elements: eps = x - r; party 0's value share gains eps,
+// every party's MAC share gains alpha_i * eps.
+template <class F, int NP, int V>
+__device__ __forceinline__ void input_elems(const InArgs<F> &a, int64_t j, const typename F::T (&alpha)[NP]) {
+    using T = typename F::T;
+    T x[V], r[V], e[V];
+    vld<F, V, true>(a.x + j, x);
+    vld<F, V, true>(a.r + j, r);
+#pragma unroll
+    for (int q = 0; q < V; ++q) e[q] = F::sub(x[q], r[q]);
+    if (a.eps) vst<F, V>(a.eps + j, e);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        T v[V], g[V];
+        vld<F, V, true>(a.mv + i * a.ms + j, v);
+        vld<F, V, true>(a.mm + i * a.ms + j, g);
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            if (i == 0) v[q] = F::add(v[q], e[q]);
+            g[q] = F::add(g[q], F::mul(alpha[i], e[q]));
+        }
+        vst<F, V>(a.ov + i * a.os + j, v);
+        vst<F, V>(a.om + i * a.os + j, g);
+    }
+}
+
+// V elements per thread (16-byte accesses when every row and vector is
+// 16-byte aligned), the N % V tail one element per thread.
+template <class F, int NP, int V>
+__global__ void __launch_bounds__(256) k_input(InArgs<F> a, const DevState *ds) {
     using T = typename F::T;
     T alpha[NP];
 #pragma unroll
     for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(ds, i);
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
-        const T e = F::sub(F::ld(x + j), F::ld(r + j));
-        if (eps_out) F::st(eps_out + j, e);
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            const T v = F::ld(mv + i * ms + j);
-            F::st(ov + i * os + j, i == 0 ? F::add(v, e) : v);
-            F::st(om + i * os + j, F::add(F::ld(mm + i * ms + j), F::mul(alpha[i], e)));
-        }
-    }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t ng = a.N / V;
+    for (int64_t g = tid; g < ng; g += stride) input_elems<F, NP, V>(a, g * V, alpha);
+    for (int64_t j = ng * V + tid; j < a.N; j += stride) input_elems<F, NP, 1>(a, j, alpha);
 }
 
 template <class F, int NP>
 static void launch_input(spdz_ctx *ctx, const void *x, const void *r, const spdz_buf *m, const spdz_buf *o, int64_t N,
                          void *eps) {
     using T = typename F::T;
-    auto kern = k_input<F, NP>;
-    kern<<<grid_for(ctx, (const void *)kern, 256, 0, N), 256, 0, ctx->stream>>>(
-        (const T *)x, (const T *)r, (const T *)m->val, (const T *)m->mac, m->stride, (T *)o->val, (T *)o->mac, o->stride,
-        N, (T *)eps, ctx->ds);
+    InArgs<F> a{(const T *)x, (const T *)r, (const T *)m->val, (const T *)m->mac, m->stride,
+                (T *)o->val, (T *)o->mac, o->stride, N, (T *)eps};
+    const size_t eb = sizeof(T);
+    auto al = [](const void *q) { return ((uintptr_t)q & 15) == 0; };
+    constexpr int VV = std::is_same_v<F, F61> ? 2 : std::is_same_v<F, F32> ? 4 : 1;
+    const bool vec = VV > 1 && buf_vec_ok(m, eb) && buf_vec_ok(o, eb) && al(x) && al(r) && (!eps || al(eps));
+    if (vec) {
+        auto kern = k_input<F, NP, VV>;
+        kern<<<grid_for(ctx, (const void *)kern, 256, 0, (N + VV - 1) / VV), 256, 0, ctx->stream>>>(a, ctx->ds);
+    } else {
+        auto kern = k_input<F, NP, 1>;
+        kern<<<grid_for(ctx, (const void *)kern, 256, 0, N), 256, 0, ctx->stream>>>(a, ctx->ds);
+    }
 }
 
 }  // namespace spdz

@@ -34,8 +34,12 @@ def clear_values(p, count, seed):
     return xs
 
 
-@pytest.mark.parametrize("p,n,count", [(O.P61, 2, 1000), (O.P127, 3, 333), (O.P32, 4, 4097)])
-def test_input_sharing_matches_oracle(p, n, count):
+@pytest.mark.parametrize("p,n,count,off", [(O.P61, 2, 1000, 0), (O.P127, 3, 333, 0), (O.P32, 4, 4097, 0),
+                                           (O.P61, 3, 1001, 1), (O.P32, 2, 999, 3)])
+def test_input_sharing_matches_oracle(p, n, count, off):
+    # off = 0: 16-byte vector accesses (with a ragged tail for odd counts);
+    # an output offset that breaks the rows' 16-byte alignment takes the
+    # one-element path
     seed, owner = 9, n - 1
     ctx = ctx_for(n, p)
     f = SH.field_of(p)
@@ -48,8 +52,8 @@ def test_input_sharing_matches_oracle(p, n, count):
         S.spdz_deal_input_masks(ctx, seed, owner, 0, count, ash, masks.buf(), r)
         xs = clear_values(p, count, p % 997)
         x = SH.from_host(O.to_array(p, xs), field=f)
-        out, eps = SH.alloc(f, n, count), SH.zeros(f, count)
-        S.spdz_input(ctx, x, r, masks.buf(), out.buf(), count, eps)
+        out, eps = SH.alloc(f, n, count + off), SH.zeros(f, count)
+        S.spdz_input(ctx, x, r, masks.buf(), out.buf(off), count, eps)
         alpha, oash = O.deal_alpha(p, n, seed)
         rv, rm, rc = O.deal_input_masks(p, n, seed, owner, 0, count, alpha)
         assert_equal(masks.host()[0], rv, "mask values")
@@ -57,21 +61,21 @@ def test_input_sharing_matches_oracle(p, n, count):
         assert_equal(SH.to_host(r), rc, "clear masks")
         xv, xm, oeps = O.input_share(p, O.to_array(p, xs), rc, rv, rm, oash)
         assert_equal(SH.to_host(eps), oeps, "eps")
-        assert_equal(out.host()[0], xv, "input value shares")
-        assert_equal(out.host()[1], xm, "input MAC shares")
+        assert_equal(out.host()[0][:, off:], xv, "input value shares")
+        assert_equal(out.host()[1][:, off:], xm, "input MAC shares")
         # the reveal releases exactly the inputs
         got = SH.zeros(f, count)
         sig = O.zeros(p, n)
-        assert S.spdz_reveal(ctx, out.buf(), got, count, sig)
+        assert S.spdz_reveal(ctx, out.buf(off), got, count, sig)
         assert_equal(SH.to_host(got), O.to_array(p, xs), "revealed")
         ok, osig, _, _ = O.mac_check(p, [O.OpenLog(O.to_array(p, xs), xm)], oash, 5, 0)
         assert ok
         assert_equal(sig, osig, "sigma of the reveal")
         assert sum(O.to_ints(p, sig)) % p == 0
         # a tampered share: the check fails and nothing is released
-        out.val[1, 7] = out.val[1, 8]
+        out.val[1, off + 7] = out.val[1, off + 8]
         got2 = SH.zeros(f, count)
-        assert not S.spdz_reveal(ctx, out.buf(), got2, count)
+        assert not S.spdz_reveal(ctx, out.buf(off), got2, count)
         assert not np.any(SH.to_host(got2))
     finally:
         S.spdz_ctx_destroy(ctx)
