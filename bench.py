@@ -831,12 +831,14 @@ def run_batch(args):
     sweep = batch_sweep(args, "p61", hbm)
     sweep32 = batch_sweep(args, "p32", hbm)
     linear = linear_gates_roofline(args, hbm)
+    ip = innerprod_roofline(args, hbm)
     line = {"metric": "Beaver mults/s, 2 parties, p=2^61-1, 2^16 products with one MAC check",
             "value": 2**16 / (sweep["2^16"]["with_check_us"] * 1e-6), "unit": "Beaver mults/s",
             "higher_is_better": True, "n_gpus": 1, "dtype": "u64", "data": "synthetic",
             "config": {"workload": "2^16 Beaver mults, n=2, p61, batch + MAC check (L2-resident: latency-bound); "
                                    "sweep to 2^26 for the bandwidth fraction", "bytes_per_mult": 192},
-            "sweep": sweep, "sweep_p32": sweep32, "linear_gates": linear, "hbm_peak_gbs": hbm,
+            "sweep": sweep, "sweep_p32": sweep32, "linear_gates": linear, "innerprod_p61": ip,
+            "hbm_peak_gbs": hbm,
             "peak_source": src}
     print(json.dumps(line), flush=True)
 
@@ -929,6 +931,49 @@ def linear_gates_roofline(args, hbm):
                          "kernel": "k_open<F61,3,2> + k_check (spdz_reveal)"}
         return {"kernel": "k_linear<F61,3> (spdz_linear)", "N": N, "ops": out,
                 "l2": "inputs larger than L2 (2.4 GB per ADD)"}
+    finally:
+        S.spdz_ctx_destroy(ctx)
+
+
+def innerprod_roofline(args, hbm):
+    """16,384 inner products of length 1024 (2^24 terms), n=3, p61, through
+    spdz_innerprod_batch: per term x, y and the triple (a, b, c) are read,
+    values and MACs (10 n w = 240 B; the 16,384 outputs add nothing
+    measurable).  Each call consumes its own 2^24 fresh triples."""
+    import torch
+    from paper_2512_11112_b300 import shares as SH
+    from paper_2512_11112_b300 import spdz as S
+    n, f, P, L = 3, S.SPDZ_F61, 16384, 1024
+    T = P * L
+    ctx = S.spdz_ctx_create(n, f, torch.cuda.current_stream().cuda_stream)
+    try:
+        ash = SH.zeros(f, n)
+        S.spdz_deal_alpha(ctx, 4, ash)
+        x, y = (SH.alloc(f, n, T) for _ in range(2))
+        S.spdz_deal_shared(ctx, 4, S.SPDZ_KIND_INPUT, 0, 0, T, ash, None, x.buf())
+        S.spdz_deal_shared(ctx, 4, S.SPDZ_KIND_INPUT, 1, 0, T, ash, None, y.buf())
+        zi = SH.alloc(f, n, P)
+        tri = [SH.alloc(f, n, T) for _ in range(3)]
+        ts, ok = [], True
+        for rep in range(max(args.warmup, 3) + 5):
+            S.spdz_deal_triples(ctx, 4, rep * T, T, ash, *[t.buf() for t in tri])
+            S.spdz_load_preproc(ctx, ash, *[t.buf() for t in tri], T)
+            torch.cuda.synchronize()
+            e0, e1 = _events(torch)
+            e0.record()
+            S.spdz_innerprod_batch(ctx, x.buf(), y.buf(), zi.buf(), P, L)
+            e1.record()
+            ok = S.spdz_mac_check(ctx) and ok
+            torch.cuda.synchronize()
+            if rep >= max(args.warmup, 3):
+                ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        bpt = 10 * n * 8
+        gbs = bpt * T / (ms * 1e-3) / 1e9
+        return {"kernel": "k_innerprod<F61,3> (spdz_innerprod_batch)", "products": P, "length": L,
+                "ms": round(ms, 4), "terms_per_s": T / (ms * 1e-3), "bytes_per_term": bpt,
+                "achieved_gbs": round(gbs, 1), "frac": round(gbs / hbm, 4), "mac_check_passed": bool(ok),
+                "l2": "inputs larger than L2 (4.0 GB per call)"}
     finally:
         S.spdz_ctx_destroy(ctx)
 

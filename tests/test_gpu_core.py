@@ -242,7 +242,7 @@ def test_open_and_check_match_oracle(p, n, off):
         S.spdz_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("p,P,L", [(O.P127, 37, 100), (O.P61, 64, 1024), (O.P61, 5, 7), (O.P32, 19, 300)])
+@pytest.mark.parametrize("p,P,L", [(O.P127, 37, 100), (O.P61, 64, 1024), (O.P61, 5, 7), (O.P61, 9, 70), (O.P32, 19, 300)])
 def test_innerprod_matches_oracle(p, P, L):
     n, seed, chk = 3, 8, 5
     ctx = ctx_for(n, p)
