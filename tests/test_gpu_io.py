@@ -119,3 +119,53 @@ def test_inputs_circuit_reveal_equals_cleartext(p, n):
         assert_equal(SH.to_host(got), clear[first:], "revealed outputs")
     finally:
         S.spdz_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("p", [O.P61, O.P32])
+def test_open_input_reveal_full_size_sampled(p):
+    """The sizes the batch benchmark times: 2^24 elements, 3 parties, one
+    call each on the full buffers (16-byte vector kernels).  The open of
+    dealt shares, the input sharing of the opened values and their reveal;
+    sampled elements (the ends, the middle, vector edges, random indices)
+    against the oracle dealing each sampled index from the same counters;
+    both checks pass and the first one's sigma sums to zero."""
+    n, N, seed, chk, owner = 3, 2**24, 57, 23, 1
+    f = SH.field_of(p)
+    ctx = ctx_for(n, p)
+    try:
+        ash = SH.zeros(f, n)
+        S.spdz_deal_alpha(ctx, seed, ash)
+        S.spdz_load_preproc(ctx, ash, None, None, None, 0)
+        S.spdz_set_check_seed(ctx, chk)
+        x = SH.alloc(f, n, N)
+        S.spdz_deal_shared(ctx, seed, S.SPDZ_KIND_INPUT, 0, 0, N, ash, None, x.buf())
+        pub = SH.zeros(f, N)
+        S.spdz_open(ctx, x.buf(), pub, N)
+        sigma = O.zeros(p, n)
+        assert S.spdz_mac_check(ctx, sigma)
+        assert sum(O.to_ints(p, sigma)) % p == 0
+        masks, r = SH.alloc(f, n, N), SH.zeros(f, N)
+        S.spdz_deal_input_masks(ctx, seed, owner, 0, N, ash, masks.buf(), r)
+        out, eps = SH.alloc(f, n, N), SH.zeros(f, N)
+        S.spdz_input(ctx, pub, r, masks.buf(), out.buf(), N, eps)
+        got = SH.zeros(f, N)
+        assert S.spdz_reveal(ctx, out.buf(), got, N)
+        rng = np.random.default_rng(5)
+        idx = np.unique(np.concatenate([[0, 1, 2, 3, 4, N // 2 - 1, N // 2, N - 5, N - 2, N - 1],
+                                        rng.integers(0, N, 20)])).astype(np.int64)
+        ti = torch.from_numpy(idx).to(pub.device)
+        g_pub, g_eps, g_rev = SH.to_host(pub[ti]), SH.to_host(eps[ti]), SH.to_host(got[ti])
+        g_ov, g_om = SH.to_host(out.val[:, ti]), SH.to_host(out.mac[:, ti])
+        alpha, oash = O.deal_alpha(p, n, seed)
+        for s_, j in enumerate(idx.tolist()):
+            xv, xm, xs = O.deal_shared(p, n, seed, O.K_INPUT, 0, j, 1, alpha)
+            assert_equal(g_pub[s_:s_ + 1], O.open_(p, xv), f"opened value at {j}")
+            assert_equal(g_pub[s_:s_ + 1], xs, f"opened value = dealt secret at {j}")
+            rv, rm, rc = O.deal_input_masks(p, n, seed, owner, j, 1, alpha)
+            iv, im, ieps = O.input_share(p, xs, rc, rv, rm, oash)
+            assert_equal(g_eps[s_:s_ + 1], ieps, f"eps at {j}")
+            assert_equal(g_ov[:, s_:s_ + 1], iv, f"input value shares at {j}")
+            assert_equal(g_om[:, s_:s_ + 1], im, f"input MAC shares at {j}")
+            assert_equal(g_rev[s_:s_ + 1], xs, f"revealed at {j}")
+    finally:
+        S.spdz_ctx_destroy(ctx)
