@@ -228,11 +228,9 @@ enum spdz_sched {
                                   no fence.  The copy is zeroed every 7 runs of the circuit so no
                                   stale word carries a current tag.  Plan fields used: block,
                                   ctas_per_sm, use_graph, spin_limit_us (bound of one barrier or
-                                  operand wait), poll_ns, record_layer_times,
-                                  barrier_extra_arrivals (testing: > 0 makes the first operand
-                                  of every gate after the first layer wait for a tag that is
-                                  never written, so the bounded wait runs out:
-                                  SPDZ_ERR_TIMEOUT); n_groups must be 0. */
+                                  operand wait), poll_ns, record_layer_times, barrier_slack
+                                  and test_unwritten_tag; n_groups and barrier_extra_arrivals
+                                  must be 0. */
 };
 
 /* Execution plan of a circuit run.  No plan changes any result bit. */
@@ -262,6 +260,10 @@ typedef struct {
                                               this many CTAs' arrivals are counted (operands
                                               still in flight validate by tag); 0 = a full
                                               barrier, at most the grid size */
+    int32_t test_unwritten_tag;            /* testing, tagged mode only: 1 makes the first operand
+                                              of every gate after the first layer wait for a tag
+                                              that no store writes, so the bounded operand wait
+                                              runs out (SPDZ_ERR_TIMEOUT); 0 in normal use */
 } spdz_plan;
 
 typedef struct {
@@ -326,7 +328,9 @@ int spdz_dag_layer_counts(const spdz_dag *dag, int32_t *counts_out);
  * of at most SPDZ_MAX_PARTIES parties; more parties are rejected with
  * SPDZ_ERR_ARG.  The first call on a device looks up the array's device
  * address (one cudaGetSymbolAddress, with that device current); make that
- * first call before any stream capture.  Every call shares the array and
+ * first call before any stream capture.  The address is kept until the
+ * process exits, so do not call this entry point on a device after
+ * cudaDeviceReset has torn down its context.  Every call shares the array and
  * clears it at its start: calls that overlap on the GPU (on different
  * streams, or from several host threads) race and give wrong results, so
  * order them on one stream.
@@ -339,7 +343,7 @@ int spdz_mul_check_noalloc(int n_parties, int field, void *stream, const spdz_bu
 
 /* ------------------------------------------------------ learned cost model
  * The scheduler's cost model (the autotuning the paper leaves to future work,
- * Sec. V-C): a fully connected network n_in -> hidden x hidden_layers -> 1
+ * Sec. V-D): a fully connected network n_in -> hidden x hidden_layers -> 1
  * with ReLU, FP32, trained on the device by the library's own forward,
  * backward (mean squared error) and Adam kernels.  Parameters are one flat
  * float array: per layer, W[out][in] row-major then b[out].  Initial weights
@@ -364,10 +368,16 @@ int spdz_mlp_loss_grad(spdz_mlp *m, const float *X_dev, const float *T_dev, int6
  * final mean squared error over all B rows. */
 int spdz_mlp_train(spdz_mlp *m, const float *X_dev, const float *T_dev, int64_t B, int32_t epochs,
                    int32_t batch, float lr, float *loss_host);
+/* One Adam step (as in spdz_mlp_train, Kingma and Ba 2015, Algorithm 1) on
+ * the caller's gradient grad_dev (device, spdz_mlp_num_params floats): the
+ * step counter t advances by one, the moments m, v are updated and the
+ * parameters move by lr * mhat / (sqrt(vhat) + 1e-8) with the bias
+ * corrections 1 - 0.9^t and 1 - 0.999^t.  Enqueued on the model's stream. */
+int spdz_mlp_adam_step(spdz_mlp *m, const float *grad_dev, float lr);
 
 /* ---------------------------------------------------------- scheduling
  * Execution plans for circuit runs (the slice/batch-size autotuning and
- * profile-guided selection the paper leaves to future work, Sec. V-C).  A
+ * profile-guided selection the paper leaves to future work, Sec. V-D).  A
  * plan never changes a result bit.  Every call below that runs the circuit
  * consumes triples from the context's pool (one run's worth per run) and needs
  * an empty check epoch, like spdz_run_dag.

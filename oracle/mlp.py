@@ -9,6 +9,8 @@ layer, W[out][in] row-major, then b[out].
 
 Pinned by tests/test_oracle_mlp.py against central finite differences and,
 for a network without hidden layers, the closed-form least-squares gradient.
+The Adam step is pinned by a two-step case worked by hand and by the closed
+forms of bias-corrected Adam under a constant gradient.
 """
 from __future__ import annotations
 
@@ -61,3 +63,19 @@ def loss_grad(params, dims, X, T):
             dz = (dz @ Ws[l]) * (pres[l - 1] > 0)
     flat = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
     return loss, flat
+
+
+def adam_step(params, grad, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma and Ba, "Adam: A Method for Stochastic
+    Optimization", ICLR 2015, Algorithm 1) in float64, step number t >= 1:
+    the moment estimates m <- b1 m + (1 - b1) g and v <- b2 v + (1 - b2) g^2,
+    their bias corrections m / (1 - b1^t) and v / (1 - b2^t), and the move
+    params <- params - lr * mhat / (sqrt(vhat) + eps).  Returns the new
+    (params, m, v); the inputs are not modified."""
+    g = np.asarray(grad, dtype=np.float64)
+    m = b1 * np.asarray(m, dtype=np.float64) + (1.0 - b1) * g
+    v = b2 * np.asarray(v, dtype=np.float64) + (1.0 - b2) * g * g
+    mhat = m / (1.0 - b1 ** t)
+    vhat = v / (1.0 - b2 ** t)
+    p = np.asarray(params, dtype=np.float64) - lr * mhat / (np.sqrt(vhat) + eps)
+    return p, m, v

@@ -87,6 +87,7 @@ static int enqueue_run(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, cons
     DagArgs<F> a = base_args<F>(ctx, dag, w);
     a.spin_ns = (uint64_t)(plan.spin_limit_us ? plan.spin_limit_us : 200000u) * 1000ull;
     a.extra_arrivals = plan.barrier_extra_arrivals > 0 ? (uint32_t)plan.barrier_extra_arrivals : 0u;
+    a.test_unwritten_tag = plan.test_unwritten_tag != 0;
     cudaStream_t saved = ctx->stream;
     ctx->stream = s;
     if (plan.mode == SPDZ_SCHED_PER_LAYER) {
@@ -262,7 +263,10 @@ static int validate_plan(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &p) {
         if (dag->field != SPDZ_F61) return set_err(ctx, SPDZ_ERR_ARG, "plan: tagged mode needs p = 2^61-1");
         if (p.n_groups != 0) return set_err(ctx, SPDZ_ERR_ARG, "plan: tagged mode has no layer groups");
         if (p.poll_ns > 50000) return set_err(ctx, SPDZ_ERR_ARG, "plan: poll_ns above 50 us");
+        if (p.barrier_extra_arrivals != 0) return set_err(ctx, SPDZ_ERR_ARG, "plan: tagged mode has no extra arrivals");
     }
+    if (p.test_unwritten_tag != 0 && (p.mode != SPDZ_SCHED_TAGGED || p.test_unwritten_tag != 1))
+        return set_err(ctx, SPDZ_ERR_ARG, "plan: test_unwritten_tag is 0 or 1, tagged mode only");
     if (p.block != 0 && (p.block < 32 || p.block > 256 || p.block % 32)) return set_err(ctx, SPDZ_ERR_ARG, "plan: block must be 32..256, a multiple of 32");
     if (p.n_groups < 0 || p.n_groups > SPDZ_MAX_GROUPS) return set_err(ctx, SPDZ_ERR_ARG, "plan: bad group count");
     if (p.barrier_extra_arrivals < 0 || p.barrier_extra_arrivals > 1024) return set_err(ctx, SPDZ_ERR_ARG, "plan: bad extra arrivals");

@@ -64,6 +64,7 @@ template <class F> struct DagArgs {
     int64_t n_in;                           // tagged: input wires copied into it
     uint32_t poll_ns;                       // tagged: first sleep between operand polls
     uint32_t slack;                         // tagged: arrivals a layer barrier does not wait for
+    int32_t test_unwritten_tag;             // testing (tagged): operands wait for a tag never written
 };
 
 // Operands of one gate that do not depend on earlier layers: its record,
@@ -657,8 +658,9 @@ __global__ void __launch_bounds__(256, 2) k_dag_tagged(DagArgs<F61> a) {
     if (!ok && threadIdx.x == 0 && blockIdx.x == 0) atomicOr(&a.ds->err_flags, ERR_TIMEOUT);
     unsigned int nb = 0;
     for (int32_t l = a.l0; l < a.l1; ++l) {
-        // testing: first operands after the first layer wait for a tag nobody writes
-        const uint64_t wtag = (a.extra_arrivals && l > a.l0) ? 8u : tag;
+        // testing: first operands after the first layer wait for a tag nobody
+        // writes (tags are 1..7; the three tag bits cannot hold 8)
+        const uint64_t wtag = (a.test_unwritten_tag && l > a.l0) ? 8u : tag;
         if (ok) ok = df_layer<NP>(a, L, r, staged, nthreads, st, tri_base, key, tag, wtag, alpha, acc, l == a.l0);
         if (l == a.l0 && !idle_copy) copy_inputs();
         staged = false;

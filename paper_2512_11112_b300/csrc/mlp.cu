@@ -268,6 +268,17 @@ int spdz_mlp_loss_grad(spdz_mlp *m, const float *X_dev, const float *T_dev, int6
     return cudaGetLastError() == cudaSuccess ? SPDZ_OK : SPDZ_ERR_CUDA;
 }
 
+// One Adam step (the same kernel and step counter as spdz_mlp_train) with a
+// gradient the caller supplies.
+int spdz_mlp_adam_step(spdz_mlp *m, const float *grad_dev, float lr) {
+    if (!m || !grad_dev) return SPDZ_ERR_ARG;
+    const float b1 = 0.9f, b2 = 0.999f;
+    ++m->adam_t;
+    const float c1 = 1.f - std::pow(b1, (float)m->adam_t), c2 = 1.f - std::pow(b2, (float)m->adam_t);
+    k_adam<<<nb(m->n_params), 256, 0, m->stream>>>(m->p, grad_dev, m->m, m->v, m->n_params, lr, b1, b2, 1e-8f, c1, c2);
+    return cudaGetLastError() == cudaSuccess ? SPDZ_OK : SPDZ_ERR_CUDA;
+}
+
 // Adam (beta1 0.9, beta2 0.999, eps 1e-8) over `epochs` passes of the data
 // in consecutive mini-batches of `batch` rows (the caller shuffles).
 int spdz_mlp_train(spdz_mlp *m, const float *X_dev, const float *T_dev, int64_t B, int32_t epochs, int32_t batch,

@@ -120,7 +120,10 @@ __global__ void k_na_finish(const NoallocState *s, typename F::T *result) {
 }
 
 // Device address of the scratch array, looked up once per device (host
-// code must not use the array's name as a device pointer).
+// code must not use the array's name as a device pointer).  The address is
+// kept for the life of the process: after cudaDeviceReset (or any teardown
+// of the device's primary context) it is stale, so a process that resets a
+// device must not call spdz_mul_check_noalloc on it again.
 static std::mutex g_na_mu;
 constexpr int NA_MAX_DEVICES = 64;
 static void *g_na_ptr[NA_MAX_DEVICES];
@@ -150,7 +153,10 @@ static int na_run(cudaStream_t st, const spdz_buf *x, const spdz_buf *y, const s
                   const spdz_buf *c, const void *alpha_sh, const spdz_buf *z, int64_t N, uint64_t key,
                   void *result, NoallocState *s) {
     using T = typename F::T;
+    // each launch's status is read right after it, so an error reported here
+    // belongs to this call's launches
     k_na_init<F><<<1, 64, 0, st>>>(s, (const T *)alpha_sh, NP, key);
+    if (cudaGetLastError() != cudaSuccess) return SPDZ_ERR_CUDA;
     if (N > 0) {
         NaArgs<F> g{};
         g.xv = (const T *)x->val; g.xm = (const T *)x->mac; g.xs = x->stride;
@@ -170,6 +176,7 @@ static int na_run(cudaStream_t st, const spdz_buf *x, const spdz_buf *y, const s
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_na_mul<F, NP>, 256, 0);
         const int64_t need = (N + 255) / 256, cap = (int64_t)(occ < 1 ? 1 : occ) * sms;
         k_na_mul<F, NP><<<(int)(need < cap ? need : cap), 256, 0, st>>>(g);
+        if (cudaGetLastError() != cudaSuccess) return SPDZ_ERR_CUDA;
     }
     k_na_finish<F, NP><<<1, 32, 0, st>>>(s, (T *)result);
     return cudaGetLastError() == cudaSuccess ? SPDZ_OK : SPDZ_ERR_CUDA;

@@ -1,5 +1,5 @@
 // sched.cu -- execution plans for circuit runs (the batch-size and slicing
-// autotuning the paper leaves to future work, Sec. V-C).
+// autotuning the paper leaves to future work, Sec. V-D).
 //
 // Two schedulers produce a spdz_plan for a circuit; neither changes any
 // result bit (every plan computes the same shares):

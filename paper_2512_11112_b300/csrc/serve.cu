@@ -636,9 +636,10 @@ int spdz_serve_run(spdz_server *s, const spdz_serve_request *reqs, int64_t count
                 h_ringwait += now_s(t0) - tw;
                 // device duration of the tick that used this slot
                 float ms = 0;
-                if (cudaEventElapsedTime(&ms, s->ring_start[ring], s->ring_ev[ring]) == cudaSuccess && ms > 0)
+                if (cudaEventElapsedTime(&ms, s->ring_start[ring], s->ring_ev[ring]) == cudaSuccess && ms > 0) {
                     s->tick_us_ema = s->tick_us_ema == 0 ? ms * 1e3 : 0.9 * s->tick_us_ema + 0.1 * ms * 1e3;
                     s->tick_us_min = s->tick_us_min == 0 ? ms * 1e3 : std::min(s->tick_us_min, (double)ms * 1e3);
+                }
             }
             int64_t need = 0;
             for (Live *L : ticking) {

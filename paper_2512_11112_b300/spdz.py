@@ -62,7 +62,7 @@ class spdz_plan(C.Structure):
                 ("barrier_extra_arrivals", C.c_int32),
                 ("group_cluster", C.c_int32 * SPDZ_MAX_GROUPS),
                 ("group_block", C.c_int32 * SPDZ_MAX_GROUPS), ("poll_ns", C.c_uint32),
-                ("barrier_slack", C.c_uint32)]
+                ("barrier_slack", C.c_uint32), ("test_unwritten_tag", C.c_int32)]
 
 
 class spdz_stats(C.Structure):
@@ -139,6 +139,7 @@ _SIGS = {
     "spdz_mlp_forward": [_vp, _vp, _i64, _vp],
     "spdz_mlp_loss_grad": [_vp, _vp, _vp, _i64, _vp, _vp],
     "spdz_mlp_train": [_vp, _vp, _vp, _i64, C.c_int32, C.c_int32, C.c_float, _vp],
+    "spdz_mlp_adam_step": [_vp, _vp, C.c_float],
     "spdz_sched_num_configs": [C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "spdz_sched_config_plan": [_vp, C.c_int32, C.POINTER(spdz_plan)],
     "spdz_sched_record": [_vp, _vp, _bufp, C.c_int32],
@@ -291,7 +292,7 @@ def spdz_field_op(ctx, op: int, a, b, out, N: int) -> None:
 def plan(mode: int = SPDZ_SCHED_FUSED, block: int = 256, ctas_per_sm: int = 0, use_graph: int = 1,
          groups=None, flush=None, group_ctas=None, record_layer_times: int = 0,
          spin_limit_us: int = 0, barrier_extra_arrivals: int = 0, group_cluster=None,
-         group_block=None, poll_ns: int = 0, barrier_slack: int = 0) -> spdz_plan:
+         group_block=None, poll_ns: int = 0, barrier_slack: int = 0, test_unwritten_tag: int = 0) -> spdz_plan:
     """Builds a spdz_plan; groups = list of exclusive end layers;
     group_cluster[g] > 0 runs group g inside one cluster of that many CTAs."""
     p = spdz_plan()
@@ -308,6 +309,7 @@ def plan(mode: int = SPDZ_SCHED_FUSED, block: int = 256, ctas_per_sm: int = 0, u
     p.barrier_extra_arrivals = barrier_extra_arrivals
     p.poll_ns = poll_ns
     p.barrier_slack = barrier_slack
+    p.test_unwritten_tag = test_unwritten_tag
     return p
 
 
@@ -423,6 +425,10 @@ def spdz_mlp_train(m, X, T, B: int, epochs: int, batch: int, lr: float) -> float
     loss = np.zeros(1, dtype=np.float32)
     _chk(None, lib.spdz_mlp_train(m, ptr(X), ptr(T), B, epochs, batch, lr, loss.ctypes.data))
     return float(loss[0])
+
+
+def spdz_mlp_adam_step(m, grad, lr: float) -> None:
+    _chk(None, lib.spdz_mlp_adam_step(m, ptr(grad), lr))
 
 
 # ------------------------------------------------------------- scheduling

@@ -303,10 +303,14 @@ def test_tagged_operand_wait_timeout_is_a_status_not_a_hang():
     dag = W.small_dag(seed=10, p=O.P61, n_inputs=64, widths=[200, 100, 50])
     dc = DeviceCircuit(dag, 3, seed=10, runs=2)
     try:
-        plan = S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=0, spin_limit_us=2000, barrier_extra_arrivals=1)
+        plan = S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=0, spin_limit_us=2000, test_unwritten_tag=1)
         with pytest.raises(S.SpdzError) as e:
             S.spdz_run_dag(dc.ctx, dc.h, plan, dc.wires.buf())
         assert e.value.code == S.SPDZ_ERR_TIMEOUT
+        # the barrier's extra-arrival hook means nothing in tagged mode: refused
+        with pytest.raises(S.SpdzError) as e:
+            S.spdz_run_dag(dc.ctx, dc.h, S.plan(mode=S.SPDZ_SCHED_TAGGED, barrier_extra_arrivals=1), dc.wires.buf())
+        assert e.value.code == S.SPDZ_ERR_ARG
         dc.deal_inputs()
         st, passed, sig = dc.run(S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=0))
         ev, em, ok, osig = oracle_run(dag, 3, seed=10, run_index=1)

@@ -1,8 +1,9 @@
 """The LinearLayer operator on the GPU against the CPU oracle: the device
 dealer's matrix-vector triples, the opened E and D, every share of y and
 gamma(y), and the check's sigma, bit-exact, on ragged shapes of both fields;
-at 4096 x 4096 (2 parties, 32-row tiles) on sampled rows the oracle computes
-one by one, with sigma from the oracle's streamed check sums."""
+at 4096 x 4096 and at the paper's 8192 x 8192 (2 parties, 32-row tiles) on
+sampled rows the oracle computes one by one, with sigma from the oracle's
+streamed check sums."""
 import numpy as np
 import pytest
 import torch
@@ -104,13 +105,17 @@ def test_linear_layer_matches_oracle(p, n, dout, din, R):
     assert_equal(d["sig"], osig, "sigma")
 
 
-@pytest.mark.parametrize("p", [O.P32, O.P61])
-def test_linear_layer_large_sampled_rows(p):
-    """4096 x 4096, 2 parties, 32-row tiles: 40 sampled rows (first, last,
-    tile edges, random) of every share of y against the oracle, the device
+@pytest.mark.parametrize("p,size", [(O.P32, 4096), (O.P61, 4096), (O.P32, 8192)])
+def test_linear_layer_large_sampled_rows(p, size):
+    """size x size, 2 parties, 32-row tiles: sampled rows (first, last, tile
+    edges, random) of every share of y against the oracle, the device
     triples' first row, and sigma against the oracle's streamed check sums
-    over all 16.9M opened values."""
-    n, dout, din, R = 2, 4096, 4096, 32
+    over all opened values (16.9M at 4096, 67.1M at 8192).  8192 x 8192 at
+    p = 2^32-5 is the paper's workload (Sec. IV-B); there the row kernel
+    gives each row to two warps and deals rows out in rounds over every
+    resident warp, so rows at the round boundaries of 148 SMs x 16 warps
+    (multiples of 2368 / 2 rows) are sampled as well."""
+    n, dout, din, R = 2, size, size, 32
     d = device_layer(p, n, dout, din, R, want_opened=False)
     assert d["passed"]
     O.set_threads(8)
@@ -119,7 +124,10 @@ def test_linear_layer_large_sampled_rows(p):
     assert_equal(d["B"][0], tri.bv, "B values")
     assert_equal(d["C"][1], tri.cm, "C MACs")
     rng = np.random.default_rng(4)
-    rows = np.concatenate([[0, dout - 1, R - 1, R, 31 * R, 31 * R + 1], rng.integers(0, dout, 34)]).astype(np.int64)
+    edges = [0, dout - 1, R - 1, R, 31 * R, 31 * R + 1]
+    if dout > 4096:
+        edges += [1183, 1184, 2367, 2368, 3551, 3552, 4735, 4736, 7103, 7104, 8160, 8191 - 31]
+    rows = np.unique(np.concatenate([edges, rng.integers(0, dout, 34)])).astype(np.int64)
     yv, ym = O.linear_layer(p, dout, din, R, W[:2], x[:2], b[:2], tri, ash, rows=rows)
     assert_equal(d["y"][0][:, rows], yv, "sampled y values")
     assert_equal(d["y"][1][:, rows], ym, "sampled y MACs")

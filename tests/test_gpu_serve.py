@@ -114,3 +114,73 @@ def test_two_hundred_request_trace_every_result_equals_oracle():
         assert res[k].passed == 1, k
         assert_equal(outs[k][0], ev, f"request {k} values")
         assert_equal(outs[k][1], em, f"request {k} MACs")
+
+
+@pytest.fixture(scope="module")
+def model_ctx():
+    """A p61 context whose cost model is trained (the library's own training
+    kernels) on per-layer timings it records of the calibration circuits."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2512_11112_b300 import shares as SH_
+    from paper_2512_11112_b300 import spdz as S_
+    p = O.P61
+    f = SH_.field_of(p)
+    ctx = S_.spdz_ctx_create(N, f, torch.cuda.current_stream().cuda_stream)
+    ash = SH_.zeros(f, N)
+    S_.spdz_deal_alpha(ctx, 3, ash)
+    dags = W.calibration_dags(p)
+    ncfg, _ = S_.spdz_sched_num_configs()
+    T = sum(d.n_mul for d in dags) * (ncfg + 2) * 2
+    tri = [SH_.alloc(f, N, T) for _ in range(3)]
+    S_.spdz_deal_triples(ctx, 3, 0, T, ash, *[t.buf() for t in tri])
+    S_.spdz_load_preproc(ctx, ash, *[t.buf() for t in tri], T)
+    for d in dags:
+        w = SH_.alloc(f, N, d.n_wires)
+        S_.spdz_deal_shared(ctx, 3, S_.SPDZ_KIND_INPUT, 16, 0, d.n_inputs, ash, None, w.buf())
+        h = S_.spdz_dag_create(ctx, d.n_inputs, d.layer_offsets, d.ops, d.in0, d.in1, d.kconst)
+        S_.spdz_sched_record(ctx, h, w.buf(), 1)
+        S_.spdz_dag_destroy(h)
+    loss = S_.spdz_sched_train(ctx, epochs=300, lr=2e-3, seed=1)
+    assert loss < 0.1, loss
+    yield ctx
+    S_.spdz_ctx_destroy(ctx)
+
+
+def test_learned_mode_every_result_equals_oracle(model_ctx):
+    """The learned serving mode (the cost model decides, per request, between
+    ticks and one cluster launch): every request of a mixed-field trace
+    equals the oracle's evaluation of that request alone, with its check
+    passed; the same requests alone give the same shares.  The p99 latency of
+    the learned, heuristic and batched modes on the same 200-request trace
+    is printed beside the result."""
+    trace = small_trace()
+    expect = [oracle_wires(r, d) for r, d in trace]
+    outs, res, st = serve(trace, S.SPDZ_SERVE_LEARNED, model_ctx=model_ctx)
+    assert st.requests == len(trace)
+    for k, ((ov, om), (ev, em)) in enumerate(zip(outs, expect)):
+        assert res[k].passed == 1 and res[k].mode in (0, 1), k
+        assert_equal(ov, ev, f"learned mode request {k} values")
+        assert_equal(om, em, f"learned mode request {k} MACs")
+    for k in (1, 4):
+        o1, r1, _ = serve([trace[k]], S.SPDZ_SERVE_LEARNED, arrivals=False, model_ctx=model_ctx)
+        assert r1[0].passed == 1
+        assert_equal(o1[0][0], expect[k][0], f"learned mode request {k} alone, values")
+        assert_equal(o1[0][1], expect[k][1], f"learned mode request {k} alone, MACs")
+
+    reqs = W.serving_requests(seed=77, count=200, rate_per_s=20000.0, gmin=64, gmax=4096, dmin=2, dmax=16)
+    big = [(r, W.request_dag(r)) for r in reqs]
+    outs, res, st = serve(big, S.SPDZ_SERVE_LEARNED, max_active=32, model_ctx=model_ctx)
+    assert st.requests == 200 and st.max_active > 1
+    O.set_threads(8)
+    for k, (r, d) in enumerate(big):
+        ev, em = oracle_wires(r, d)
+        assert res[k].passed == 1, k
+        assert_equal(outs[k][0], ev, f"learned mode, 200-request trace, request {k} values")
+        assert_equal(outs[k][1], em, f"learned mode, 200-request trace, request {k} MACs")
+    p99 = {"learned": st.p99_s * 1e3, "learned_cluster_requests": int(st.cluster_requests)}
+    for name, mode in (("heuristic", S.SPDZ_SERVE_HEURISTIC), ("batched", S.SPDZ_SERVE_BATCHED)):
+        _, r2, s2 = serve(big, mode, max_active=32, cluster_width=512)
+        assert all(x.passed == 1 for x in r2)
+        p99[name] = s2.p99_s * 1e3
+    print("p99 ms on the 200-request trace:", p99)

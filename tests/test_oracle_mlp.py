@@ -49,3 +49,34 @@ def test_relu_blocks_gradient_of_dead_units():
     X = np.array([[0.1, 0.2], [0.3, -0.1]])
     _, g = M.loss_grad(p, dims, X, np.array([1.0, 2.0]))
     assert np.all(g[:9] == 0) and np.all(g[9:12] == 0) and g[12] != 0
+
+
+def test_adam_two_steps_worked_by_hand():
+    """theta0 = 1, gradients 0.5 then -0.25, lr 0.1 (betas 0.9, 0.999, eps
+    1e-8), worked by hand: step 1 has m = 0.05, v = 0.00025, mhat = 0.5,
+    vhat = 0.25, so theta moves by 0.1 * 0.5 / 0.50000001; step 2 has
+    m = 0.045 - 0.025 = 0.02, v = 0.00024975 + 0.0000625 = 0.00031225,
+    mhat = 0.02 / 0.19, vhat = 0.00031225 / 0.001999 = 0.1562031016, whose root
+    is 0.3952253807, so theta moves by 0.0105263158 / 0.3952253907."""
+    p, m, v = np.array([1.0]), np.zeros(1), np.zeros(1)
+    p, m, v = M.adam_step(p, np.array([0.5]), m, v, 1, 0.1)
+    assert np.isclose(m[0], 0.05, rtol=0, atol=1e-15) and np.isclose(v[0], 0.00025, rtol=0, atol=1e-15)
+    assert abs(p[0] - 0.900000002) < 1e-12
+    p, m, v = M.adam_step(p, np.array([-0.25]), m, v, 2, 0.1)
+    assert abs(m[0] - 0.02) < 1e-15 and abs(v[0] - 0.00031225) < 1e-15
+    assert abs(p[0] - 0.8733662987) < 1e-9
+
+
+def test_adam_constant_gradient_closed_form():
+    """Under a constant gradient g the bias corrections are exact: mhat = g and
+    vhat = g^2 at every step, so each step moves a parameter by exactly
+    lr * g / (|g| + eps), and a zero gradient does not move it."""
+    rng = np.random.default_rng(2)
+    g = np.concatenate([rng.normal(size=6) * 10.0 ** rng.integers(-4, 3, size=6), [0.0]])
+    p0 = rng.normal(size=g.size)
+    p, m, v = p0.copy(), np.zeros_like(g), np.zeros_like(g)
+    lr = 3e-3
+    for t in range(1, 6):
+        p, m, v = M.adam_step(p, g, m, v, t, lr)
+        assert np.allclose(p, p0 - t * lr * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-13)
+    assert p[-1] == p0[-1]
