@@ -570,10 +570,11 @@ def run_serve(args):
 
     def trace(rate, n, burst=False):
         t = [0.0] * n if burst else [r.arrival_s / rate for r in base[:n]]   # base was drawn at rate 1
-        return [(shapes[k % nshape], fields[k % nshape], base[k].seed, t[k], None, None) for k in range(n)]
+        return [(cids[k % nshape], fields[k % nshape], base[k].seed, t[k], None, None) for k in range(n)]
 
     srv = S.spdz_serve_create(N_PARTIES, budget, 512, S.SPDZ_SERVE_BATCHED, None, 0, 4096)
-    S.spdz_serve_prepare(srv, list(zip(shapes, fields)))       # deployment: upload the circuits once
+    # deployment: the circuits are registered (uploaded into the arena) once
+    cids = [S.spdz_serve_register(srv, d, f) for d, f in zip(shapes, fields)]
 
     def run(mode, items):
         S.spdz_serve_set_mode(srv, mode, model_ctx if mode == S.SPDZ_SERVE_LEARNED else None, 4096)

@@ -432,15 +432,23 @@ int spdz_sched_choose(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int32
                       spdz_sched_report *rep);
 
 /* ------------------------------------------------------------- serving
- * A serving loop over circuit requests (configuration: n parties, mixed
- * fields p = 2^61-1 and p = 2^127-1; other fields are SPDZ_ERR_ARG).
- * Requests arrive at their arrival times (seconds after the start
- * of spdz_serve_run) and are admitted first come, first served while the
- * device-memory budget (one arena of budget_bytes for every admitted
- * request's wire shares and triples) and max_active slots allow; each
+ * A server for circuit requests (n parties; circuits over p = 2^61-1 or
+ * p = 2^127-1, mixed freely; other fields are SPDZ_ERR_ARG), after the
+ * paper's non-blocking scheduler over independently ready work (Sec. III-C)
+ * applied across requests.  spdz_serve_start starts the server on a host
+ * thread of its own; from then on callers submit requests at any time
+ * (spdz_serve_submit returns at once with the request's id) and collect each
+ * result when it is ready (spdz_serve_poll); spdz_serve_stop waits for every
+ * submitted request to complete, then stops the thread.  Requests are
+ * admitted first come, first served while the device-memory budget and
+ * max_active slots allow: one arena of budget_bytes, allocated at creation,
+ * holds every registered circuit's gate records and every admitted
+ * request's wire shares, triples and (one-off circuits) gate records.  Each
  * admitted request's preprocessing is dealt on the device from its seed
- * (dealer kinds as spdz_deal_*, circuit inputs with sub 16) on an offline
- * stream, and its shares stay on the device until it completes.  Execution:
+ * (dealer kinds as spdz_deal_*: alpha, triples, and circuit inputs with
+ * kind INPUT, sub 16, unless the caller passes the input shares) on an
+ * offline stream, and its shares stay on the device until it completes.
+ * Execution:
  *   SPDZ_SERVE_SEQUENTIAL: one request at a time, one launch per layer;
  *   SPDZ_SERVE_BATCHED: continuous batching -- each tick is one launch per
  *     field evaluating the next layer of every active request, and requests
@@ -450,24 +458,34 @@ int spdz_sched_choose(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int32
  *     side stream, overlapping the ticks;
  *   SPDZ_SERVE_LEARNED: as HEURISTIC, but the cluster launch is chosen when
  *     the cost model of model_ctx (trained with spdz_sched_train) predicts it
- *     faster than ticking.
+ *     to finish first, counting the cluster launches already waiting for the
+ *     side streams.
  * Every request is its own MAC-check epoch (key of epoch 0 under
  * check_seed); its result does not depend on the mode or on the other
- * requests.  Requests that pass the same spdz_dag_desc share one device copy
- * of its gate records (uploaded at first use, kept until the server is
- * destroyed, outside the budget).  After an error the server must be
- * destroyed. */
+ * requests.  While the server runs, model_ctx belongs to the server thread:
+ * the caller must not use it.  A CUDA failure ends the session: every request
+ * not completed reports it, and later calls return it. */
 enum spdz_serve_mode { SPDZ_SERVE_SEQUENTIAL = 0, SPDZ_SERVE_BATCHED = 1, SPDZ_SERVE_HEURISTIC = 2,
                        SPDZ_SERVE_LEARNED = 3 };
 
 typedef struct spdz_server spdz_server;
 
 typedef struct {
-    const spdz_dag_desc *dag;   /* host circuit (read at its first admission) */
-    int32_t field;
-    uint64_t seed;              /* dealer seed of the request */
-    double arrival_s;           /* arrival time, seconds after the run starts (non-decreasing) */
-    void *out_val_host;         /* optional: receives the request's wire value shares [n][W] */
+    const spdz_dag_desc *dag;   /* a one-off circuit (read during spdz_serve_submit; its gate
+                                   records then live in the request's arena block), or NULL */
+    int64_t circuit_id;         /* a circuit registered with spdz_serve_register, or -1 */
+    int32_t field;              /* SPDZ_F61 or SPDZ_F127 (a registered circuit's own field) */
+    uint64_t seed;              /* dealer seed of the request (alpha, triples, inputs) */
+    double arrival_s;           /* spdz_serve_run: arrival time in seconds after the start
+                                   (non-decreasing); spdz_serve_submit: 0 = now, or a past
+                                   time after the start */
+    const void *in_val_host;    /* optional: the input wires' value shares, host [n][n_inputs]
+                                   elements, MACed under the alpha of `seed`; read when the
+                                   request is admitted, so it must stay valid until the
+                                   request completes.  NULL: dealt from the seed */
+    const void *in_mac_host;    /* the input wires' MAC shares (required with in_val_host) */
+    void *out_val_host;         /* optional: receives the request's wire value shares [n][W]
+                                   (W = n_inputs + n_gates), written before it completes */
     void *out_mac_host;         /* optional: receives its wire MAC shares [n][W] */
 } spdz_serve_request;
 
@@ -476,28 +494,59 @@ typedef struct {
     double online_s;            /* preprocessing dealt -> result */
     int32_t passed;             /* MAC-check verdict */
     int32_t mode;               /* 0 ticks, 1 cluster launch */
+    int32_t status;             /* SPDZ_OK; SPDZ_ERR_MAC (check failed); SPDZ_ERR_OOM (can never
+                                   fit the budget: refused); SPDZ_ERR_CUDA (session failed) */
+    int32_t pad;
+    uint64_t req_id;
 } spdz_serve_result;
 
 typedef struct {
     double wall_s, gates_per_s, p50_s, p99_s, mean_s;
     int64_t requests, gates, ticks, cluster_requests;
     double dealer_s;            /* device time spent dealing preprocessing (offline) */
-    int64_t peak_bytes;         /* peak arena use */
+    int64_t peak_bytes;         /* peak arena use (registered circuits included) */
     int32_t max_active;
-    /* host time of the serving loop by phase (tracing) */
+    /* host time of the serving thread by phase (tracing) */
     double host_admit_s, host_tick_s, host_complete_s, host_idle_s, host_ring_wait_s;
 } spdz_serve_stats;
 
+/* Creates a stopped server on the current device.  Errors: SPDZ_ERR_ARG,
+ * SPDZ_ERR_OOM (the arena or the slot state cannot be allocated). */
 int spdz_serve_create(spdz_server **out, int n_parties, uint64_t budget_bytes, int32_t max_active, int32_t mode,
                       spdz_ctx *model_ctx, uint64_t check_seed, int64_t cluster_width);
-/* Builds and uploads circuits ahead of a run (their preparation is then not
- * part of any request's latency); fields[k] is the field of dags[k]. */
-int spdz_serve_prepare(spdz_server *s, const spdz_dag_desc *const *dags, const int32_t *fields, int64_t count);
-/* Changes the execution mode for the next run (circuits stay prepared). */
+/* Registers a circuit of `field` (validated as spdz_dag_create; read during
+ * the call) for any number of requests: its gate records are uploaded into
+ * the arena, counted against the budget, and stay until unregistered.  Only
+ * while stopped (SPDZ_ERR_STATE).  Errors: SPDZ_ERR_ARG, SPDZ_ERR_OOM (no room
+ * left in the budget). */
+int spdz_serve_register(spdz_server *s, const spdz_dag_desc *dag, int32_t field, int64_t *circuit_id);
+int spdz_serve_unregister(spdz_server *s, int64_t circuit_id);
+/* Changes the execution mode (only while stopped). */
 int spdz_serve_set_mode(spdz_server *s, int32_t mode, spdz_ctx *model_ctx, int64_t cluster_width);
-/* Serves the trace (blocking); results [count] may be NULL. */
+/* Starts the serving thread (SPDZ_ERR_STATE when already running); the
+ * statistics of spdz_serve_stop cover the requests completed from here. */
+int spdz_serve_start(spdz_server *s);
+/* Submits one request (thread-safe; returns without waiting).  Exactly one of
+ * r->dag and r->circuit_id >= 0 names the circuit.  The host buffers the
+ * request points to must stay valid until spdz_serve_poll reports it done.
+ * Errors: SPDZ_ERR_ARG (bad circuit, field or buffers), SPDZ_ERR_STATE (not
+ * running). */
+int spdz_serve_submit(spdz_server *s, const spdz_serve_request *r, uint64_t *req_id);
+/* *done = 1 and *result filled once the request has completed (its outputs
+ * are then in its host buffers); a result is handed out once.  *done = 0
+ * while it is pending.  SPDZ_ERR_ARG for an unknown or collected id. */
+int spdz_serve_poll(spdz_server *s, uint64_t req_id, int32_t *done, spdz_serve_result *result);
+/* Waits for every submitted request to complete, stops the thread and fills
+ * stats (may be NULL) over the session's completed requests; results not yet
+ * collected stay available to spdz_serve_poll. */
+int spdz_serve_stop(spdz_server *s, spdz_serve_stats *stats);
+/* Trace driver over the calls above: starts the server, submits each request
+ * at its arrival_s (seconds after the start) from the calling thread, stops,
+ * and collects results [count] (may be NULL).  Returns the first failing
+ * request status (for example SPDZ_ERR_OOM for a request that can never fit). */
 int spdz_serve_run(spdz_server *s, const spdz_serve_request *reqs, int64_t count, spdz_serve_result *results,
                    spdz_serve_stats *stats);
+/* Stops the server if it runs, then frees everything it holds. */
 int spdz_serve_destroy(spdz_server *s);
 
 /* ------------------------------------------------------- matrix products

@@ -83,12 +83,14 @@ TENSOR_PATH = True          # the library has the tensor-core matrix path
 
 
 class spdz_serve_request(C.Structure):
-    _fields_ = [("dag", C.POINTER(spdz_dag_desc)), ("field", C.c_int32), ("seed", C.c_uint64),
-                ("arrival_s", C.c_double), ("out_val_host", C.c_void_p), ("out_mac_host", C.c_void_p)]
+    _fields_ = [("dag", C.POINTER(spdz_dag_desc)), ("circuit_id", C.c_int64), ("field", C.c_int32),
+                ("seed", C.c_uint64), ("arrival_s", C.c_double), ("in_val_host", C.c_void_p),
+                ("in_mac_host", C.c_void_p), ("out_val_host", C.c_void_p), ("out_mac_host", C.c_void_p)]
 
 
 class spdz_serve_result(C.Structure):
-    _fields_ = [("latency_s", C.c_double), ("online_s", C.c_double), ("passed", C.c_int32), ("mode", C.c_int32)]
+    _fields_ = [("latency_s", C.c_double), ("online_s", C.c_double), ("passed", C.c_int32), ("mode", C.c_int32),
+                ("status", C.c_int32), ("pad", C.c_int32), ("req_id", C.c_uint64)]
 
 
 class spdz_serve_stats(C.Structure):
@@ -154,7 +156,12 @@ _SIGS = {
     "spdz_serve_run": [_vp, C.POINTER(spdz_serve_request), _i64, C.POINTER(spdz_serve_result),
                        C.POINTER(spdz_serve_stats)],
     "spdz_serve_destroy": [_vp],
-    "spdz_serve_prepare": [_vp, _vp, _vp, _i64],
+    "spdz_serve_register": [_vp, _vp, C.c_int32, C.POINTER(_i64)],
+    "spdz_serve_unregister": [_vp, _i64],
+    "spdz_serve_start": [_vp],
+    "spdz_serve_submit": [_vp, C.POINTER(spdz_serve_request), C.POINTER(_u64)],
+    "spdz_serve_poll": [_vp, _u64, C.POINTER(C.c_int32), C.POINTER(spdz_serve_result)],
+    "spdz_serve_stop": [_vp, C.POINTER(spdz_serve_stats)],
     "spdz_deal_matrix_triple": [_vp, _u64, _u64, _i64, _i64, _i64, _vp, _bufp, _bufp, _bufp],
     "spdz_load_matrix_preproc": [_vp, _bufp, _bufp, _bufp, _i64, _i64, _i64],
     "spdz_matmul": [_vp, _bufp, _bufp, _bufp, _i64, _i64, _i64, _int, _vp, _vp],
@@ -522,43 +529,89 @@ def dag_desc(dag):
     return d
 
 
-_DESC_CACHE = {}
+def spdz_serve_register(server, dag, field: int) -> int:
+    """Registers a circuit for any number of requests; returns its id."""
+    d = dag_desc(dag)
+    cid = C.c_int64()
+    _chk(None, lib.spdz_serve_register(server, C.byref(d), field, C.byref(cid)))
+    return cid.value
 
 
-def dag_desc_cached(dag):
-    """One spdz_dag_desc per circuit object, so that requests sharing a
-    circuit share the server's uploaded copy of it."""
-    d = _DESC_CACHE.get(id(dag))
-    if d is None or d[0] is not dag:
-        d = (dag, dag_desc(dag))
-        _DESC_CACHE[id(dag)] = d
-    return d[1]
-
-
-def spdz_serve_prepare(server, dags_fields) -> None:
-    descs = [dag_desc_cached(d) for d, _ in dags_fields]
-    arr = (C.c_void_p * max(1, len(descs)))(*[C.addressof(d) for d in descs])
-    fields = np.array([f for _, f in dags_fields], dtype=np.int32)
-    _chk(None, lib.spdz_serve_prepare(server, arr, fields.ctypes.data, len(descs)))
+def spdz_serve_unregister(server, circuit_id: int) -> None:
+    _chk(None, lib.spdz_serve_unregister(server, circuit_id))
 
 
 def spdz_serve_set_mode(server, mode: int, model_ctx=None, cluster_width: int = 0) -> None:
     _chk(None, lib.spdz_serve_set_mode(server, mode, model_ctx, cluster_width))
 
 
+def spdz_serve_start(server) -> None:
+    _chk(None, lib.spdz_serve_start(server))
+
+
+def _request(circuit, field: int, seed: int, arrival_s: float = 0.0, inputs=None, out=None):
+    """A spdz_serve_request: circuit is a registered id (int) or a circuit
+    object; inputs / out are (values, MACs) numpy arrays or None.  Returns the
+    struct and the objects it points into."""
+    r = spdz_serve_request()
+    keep = []
+    if isinstance(circuit, int):
+        r.dag, r.circuit_id = None, circuit
+    else:
+        d = dag_desc(circuit)
+        keep.append(d)
+        r.dag, r.circuit_id = C.pointer(d), -1
+    r.field, r.seed, r.arrival_s = field, seed, arrival_s
+    if inputs is not None:
+        iv, im = (np.ascontiguousarray(a) for a in inputs)
+        keep += [iv, im]
+        r.in_val_host, r.in_mac_host = iv.ctypes.data, im.ctypes.data
+    if out is not None:
+        assert out[0].flags.c_contiguous and out[1].flags.c_contiguous
+        keep += list(out)
+        r.out_val_host, r.out_mac_host = out[0].ctypes.data, out[1].ctypes.data
+    return r, keep
+
+
+_PENDING = {}
+
+
+def spdz_serve_submit(server, circuit, field: int, seed: int, inputs=None, out=None, arrival_s: float = 0.0) -> int:
+    """Submits one request; the buffers stay referenced until it is polled done."""
+    r, keep = _request(circuit, field, seed, arrival_s, inputs, out)
+    rid = C.c_uint64()
+    _chk(None, lib.spdz_serve_submit(server, C.byref(r), C.byref(rid)))
+    _PENDING[(server.value if hasattr(server, "value") else server, rid.value)] = (r, keep)
+    return rid.value
+
+
+def spdz_serve_poll(server, req_id: int):
+    """(done, spdz_serve_result or None)."""
+    done = C.c_int32()
+    res = spdz_serve_result()
+    _chk(None, lib.spdz_serve_poll(server, req_id, C.byref(done), C.byref(res)))
+    if done.value:
+        _PENDING.pop((server.value if hasattr(server, "value") else server, req_id), None)
+        return True, res
+    return False, None
+
+
+def spdz_serve_stop(server) -> spdz_serve_stats:
+    st = spdz_serve_stats()
+    _chk(None, lib.spdz_serve_stop(server, C.byref(st)))
+    return st
+
+
 def spdz_serve_run(server, requests):
-    """requests: list of (dag, field, seed, arrival_s, out_val or None,
-    out_mac or None).  Returns (results list, spdz_serve_stats)."""
+    """requests: list of (circuit or registered id, field, seed, arrival_s,
+    out_val or None, out_mac or None).  Returns (results list, spdz_serve_stats)."""
     n = len(requests)
     arr = (spdz_serve_request * max(1, n))()
     keep = []
-    for k, (dag, field, seed, t, ov, om) in enumerate(requests):
-        d = dag_desc_cached(dag)
-        keep.append(d)
-        arr[k].dag = C.pointer(d)
-        arr[k].field, arr[k].seed, arr[k].arrival_s = field, seed, t
-        arr[k].out_val_host = None if ov is None else ov.ctypes.data
-        arr[k].out_mac_host = None if om is None else om.ctypes.data
+    for k, (circ, field, seed, t, ov, om) in enumerate(requests):
+        r, kp = _request(circ, field, seed, t, None, None if ov is None else (ov, om))
+        keep.append(kp)
+        arr[k] = r
     res = (spdz_serve_result * max(1, n))()
     st = spdz_serve_stats()
     rc = lib.spdz_serve_run(server, arr, n, res, C.byref(st))

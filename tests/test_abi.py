@@ -22,7 +22,8 @@ def declared_functions():
 def test_header_declares_the_boundary_calls():
     names = declared_functions()
     for required in ("spdz_load_preproc", "spdz_linear", "spdz_mul_batch", "spdz_open",
-                     "spdz_mac_check"):
+                     "spdz_mac_check", "spdz_run_dag", "spdz_innerprod_batch", "spdz_matmul",
+                     "spdz_serve_start", "spdz_serve_submit", "spdz_serve_poll", "spdz_serve_stop"):
         assert required in names
 
 

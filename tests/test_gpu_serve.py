@@ -84,7 +84,7 @@ def test_admission_respects_the_memory_budget():
     per = []
     for r, d in trace:
         eb = 8 if r.p == O.P61 else 16
-        per.append(2 * N * d.n_wires * eb + 6 * N * max(1, d.n_mul) * eb + 16 * d.n_gates)
+        per.append(2 * N * d.n_wires * eb + 6 * N * max(1, d.n_mul) * eb + (16 + eb) * d.n_gates)
     budget = int(max(per) * 2.5) + (1 << 20)
     outs, res, st = serve(trace, S.SPDZ_SERVE_BATCHED, budget=budget)
     assert st.peak_bytes <= budget
@@ -184,3 +184,104 @@ def test_learned_mode_every_result_equals_oracle(model_ctx):
         assert all(x.passed == 1 for x in r2)
         p99[name] = s2.p99_s * 1e3
     print("p99 ms on the 200-request trace:", p99)
+
+
+def test_submit_while_others_run_poll_and_stop():
+    """The server's own calls: requests are submitted from the host while
+    earlier ones are still on the GPU (a poll just before each later
+    submission finds an earlier request not yet done), some by registered
+    circuit id and some as one-off circuits, some with the caller's own input
+    shares (the oracle's dealt shares, the same values the device dealer
+    would produce); every result, collected by polling, equals the oracle's
+    evaluation of that request alone."""
+    import time
+    reqs = W.serving_requests(seed=41, count=24, rate_per_s=1e6, gmin=2000, gmax=60000, dmin=6, dmax=24)
+    trace = [(r, W.request_dag(r)) for r in reqs]
+    server = S.spdz_serve_create(N, 2 << 30, 8, S.SPDZ_SERVE_HEURISTIC, None, 0, 2048)
+    try:
+        reg = {}
+        for k in range(0, len(trace), 3):
+            r, d = trace[k]
+            reg[k] = S.spdz_serve_register(server, d, S.SPDZ_F61 if r.p == O.P61 else S.SPDZ_F127)
+        S.spdz_serve_start(server)
+        ids, outs, overlapped = [], [], 0
+        for k, (r, d) in enumerate(trace):
+            field = S.SPDZ_F61 if r.p == O.P61 else S.SPDZ_F127
+            out = (O.zeros(r.p, N, d.n_wires), O.zeros(r.p, N, d.n_wires))
+            inputs = None
+            if k % 2 == 1:
+                alpha, _ = O.deal_alpha(r.p, N, r.seed)
+                iv, im, _ = O.deal_shared(r.p, N, r.seed, O.K_INPUT, 16, 0, d.n_inputs, alpha)
+                inputs = (iv, im)
+            if ids:
+                done, _ = S.spdz_serve_poll(server, ids[-1])
+                if not done:
+                    overlapped += 1
+                else:
+                    ids[-1] = -ids[-1]          # collected already (result checked below)
+            rid = S.spdz_serve_submit(server, reg.get(k, d), field, r.seed, inputs=inputs, out=out)
+            ids.append(rid)
+            outs.append(out)
+        assert overlapped > 0
+        results = {}
+        t0 = time.time()
+        while len(results) < sum(1 for i in ids if i > 0) and time.time() - t0 < 120:
+            for i in ids:
+                if i > 0 and i not in results:
+                    done, res = S.spdz_serve_poll(server, i)
+                    if done:
+                        results[i] = res
+            time.sleep(0.002)
+        st = S.spdz_serve_stop(server)
+        assert st.requests == len(trace) and st.max_active > 1
+        with pytest.raises(S.SpdzError) as e:                 # not running
+            S.spdz_serve_submit(server, trace[0][1], S.SPDZ_F61 if trace[0][0].p == O.P61 else S.SPDZ_F127, 1)
+        assert e.value.code == S.SPDZ_ERR_STATE
+        for i in results:
+            with pytest.raises(S.SpdzError):                  # handed out once
+                S.spdz_serve_poll(server, i)
+        O.set_threads(8)
+        for k, ((r, d), i, (ov, om)) in enumerate(zip(trace, ids, outs)):
+            if i > 0:
+                assert results[i].passed == 1 and results[i].status == S.SPDZ_OK, k
+            ev, em = oracle_wires(r, d)
+            assert_equal(ov, ev, f"submitted request {k} values")
+            assert_equal(om, em, f"submitted request {k} MACs")
+    finally:
+        S.spdz_serve_destroy(server)
+
+
+def test_registered_circuits_count_against_the_budget():
+    """A registered circuit's gate records live in the arena: registering more
+    than the budget holds is refused (SPDZ_ERR_OOM), unregistering gives the
+    room back, and registration is refused while the server runs."""
+    r = W.Request(rid=0, arrival_s=0.0, p=O.P61, gates=40000, depth=8, seed=3)
+    d = W.request_dag(r)
+    server = S.spdz_serve_create(N, 1 << 20, 4, S.SPDZ_SERVE_BATCHED, None, 0, 0)
+    try:
+        with pytest.raises(S.SpdzError) as e:
+            for _ in range(4):                                # 40k gates x 24 B: about 1 MB each
+                S.spdz_serve_register(server, d, S.SPDZ_F61)
+        assert e.value.code == S.SPDZ_ERR_OOM
+    finally:
+        S.spdz_serve_destroy(server)
+    server = S.spdz_serve_create(N, 64 << 20, 4, S.SPDZ_SERVE_BATCHED, None, 0, 0)
+    try:
+        cid = S.spdz_serve_register(server, d, S.SPDZ_F61)
+        S.spdz_serve_unregister(server, cid)
+        cid = S.spdz_serve_register(server, d, S.SPDZ_F61)
+        S.spdz_serve_start(server)
+        with pytest.raises(S.SpdzError) as e:
+            S.spdz_serve_register(server, d, S.SPDZ_F61)
+        assert e.value.code == S.SPDZ_ERR_STATE
+        out = (O.zeros(r.p, N, d.n_wires), O.zeros(r.p, N, d.n_wires))
+        rid = S.spdz_serve_submit(server, cid, S.SPDZ_F61, r.seed, out=out)
+        st = S.spdz_serve_stop(server)
+        done, res = S.spdz_serve_poll(server, rid)
+        assert done and res.passed == 1 and st.requests == 1
+        assert st.peak_bytes <= 64 << 20
+        ev, em = oracle_wires(r, d)
+        assert_equal(out[0], ev, "registered circuit values")
+        assert_equal(out[1], em, "registered circuit MACs")
+    finally:
+        S.spdz_serve_destroy(server)
