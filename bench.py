@@ -1059,6 +1059,25 @@ def run_profile(args):
         S.spdz_ctx_destroy(ctx)
     elif args.profile == "beaver127":
         beaver_roofline(torch, S, SH, peaks()[0], N=2**24, calls=args.steps, field=S.SPDZ_F127)
+    elif args.profile == "heavy_small":
+        # p127, 3 parties: 2^21 Beaver products, then 2048 inner products of
+        # length 1024 (2^21 terms), `steps` times; about 1.8 GB on the device
+        n, f, N, P, L = N_PARTIES, S.SPDZ_F127, 2**21, 2048, 1024
+        ctx = S.spdz_ctx_create(n, f, torch.cuda.current_stream().cuda_stream)
+        ash = SH.zeros(f, n)
+        S.spdz_deal_alpha(ctx, 3, ash)
+        x, y, z = (SH.alloc(f, n, N) for _ in range(3))
+        S.spdz_deal_shared(ctx, 3, S.SPDZ_KIND_INPUT, 0, 0, N, ash, None, x.buf())
+        S.spdz_deal_shared(ctx, 3, S.SPDZ_KIND_INPUT, 1, 0, N, ash, None, y.buf())
+        zi = SH.alloc(f, n, P)
+        tri = [SH.alloc(f, n, 2 * N) for _ in range(3)]
+        for rep in range(args.steps):
+            S.spdz_deal_triples(ctx, 3, rep * 2 * N, 2 * N, ash, *[t.buf() for t in tri])
+            S.spdz_load_preproc(ctx, ash, *[t.buf() for t in tri], 2 * N)
+            S.spdz_mul_batch(ctx, x.buf(), y.buf(), z.buf(), N)
+            S.spdz_innerprod_batch(ctx, x.buf(), y.buf(), zi.buf(), P, L)
+            assert S.spdz_mac_check(ctx)
+        S.spdz_ctx_destroy(ctx)
     else:
         beaver_roofline(torch, S, SH, peaks()[0], N=2**24, calls=args.steps)
 
@@ -1074,7 +1093,7 @@ def main():
                     help="circuit: the benchmark circuit (default); serve, matmul, heavy, batch: the other "
                          "workloads, one JSON line each")
     ap.add_argument("--serve-requests", type=int, default=10000)
-    ap.add_argument("--profile", default=None, choices=["dag", "tagged", "beaver", "beaver127", "matmul", "linear"],
+    ap.add_argument("--profile", default=None, choices=["dag", "tagged", "beaver", "beaver127", "heavy_small", "matmul", "linear"],
                     help="small run of one kernel for an ncu capture (prints nothing)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

@@ -146,6 +146,85 @@ __device__ __forceinline__ void beaver_core(const MulArgs<F> &a, int64_t e, int6
     }
 }
 
+// p127 form of one Beaver product at element e.  The opened values' check
+// terms go into exact three-word sums that stay unreduced across every
+// element a thread handles (acc[0] = A, acc[1+i] = S_i); z and gamma(z) are
+// one exact sum each, reduced once.  With sums != nullptr the outputs are not
+// reduced either: they are added to sums[i] / sums[NP + i] (inner products).
+template <int NP>
+__device__ __forceinline__ void beaver_core127(const MulArgs<F127> &a, int64_t e, uint64_t key,
+                                               const u128v (&alpha)[NP], W127 (&acc)[NP + 1], u128v (&z)[NP],
+                                               u128v (&gz)[NP], u128v &eps, u128v &dlt, W127 *sums) {
+    using F = F127;
+    u128v av[NP], bv[NP];
+    eps = dlt = F::zero();
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        u128v x[1], y[1], ta[1], tb[1];
+        vld<F, 1, false>(a.xv + i * a.xs + e, x);
+        vld<F, 1, false>(a.yv + i * a.ys + e, y);
+        vld<F, 1, true>(a.av + i * a.as + e, ta);
+        vld<F, 1, true>(a.bv + i * a.bs + e, tb);
+        av[i] = ta[0];
+        bv[i] = tb[0];
+        eps = F::add(eps, F::sub(x[0], av[i]));
+        dlt = F::add(dlt, F::sub(y[0], bv[i]));
+    }
+    const u128v de = W127::prod(eps, dlt).reduce();
+    const uint64_t j = a.base + 2 * (uint64_t)e;
+    const u128v re = Draw<F>::at(key, j), rd = Draw<F>::at(key, j + 1);
+    {
+        // each product formed on its own; one three-word add into a sum
+        W127 q = W127::prod(re, eps);
+        q.add(W127::prod(rd, dlt));
+        acc[0].add(q);
+    }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        u128v c[1], gx[1], gy[1], ga[1], gb[1], gc[1];
+        vld<F, 1, true>(a.cv + i * a.cs + e, c);
+        vld<F, 1, false>(a.xm + i * a.xs + e, gx);
+        vld<F, 1, false>(a.ym + i * a.ys + e, gy);
+        vld<F, 1, true>(a.am + i * a.as + e, ga);
+        vld<F, 1, true>(a.bm + i * a.bs + e, gb);
+        vld<F, 1, true>(a.cm + i * a.cs + e, gc);
+        W127 v = W127::prod(eps, bv[i]), m = W127::prod(eps, gb[0]), m2 = W127::prod(alpha[i], de);
+        v.add(W127::prod(dlt, av[i]));
+        v.add(c[0]);
+        if (i == 0) v.add(de);
+        m.add(W127::prod(dlt, ga[0]));
+        m2.add(gc[0]);
+        m.add(m2);
+        W127 q = W127::prod(re, F::sub(gx[0], ga[0]));
+        q.add(W127::prod(rd, F::sub(gy[0], gb[0])));
+        acc[1 + i].add(q);
+        if (sums) {
+            sums[i].add(v);
+            sums[NP + i].add(m);
+        } else {
+            z[i] = v.reduce();
+            gz[i] = m.reduce();
+        }
+    }
+}
+
+template <int NP>
+__device__ __forceinline__ void mul_elem127(const MulArgs<F127> &a, int64_t e, uint64_t key, const u128v (&alpha)[NP],
+                                            W127 (&acc)[NP + 1]) {
+    using F = F127;
+    u128v z[NP], gz[NP], eps, dlt;
+    beaver_core127<NP>(a, e, key, alpha, acc, z, gz, eps, dlt, nullptr);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        F::st(a.zv + i * a.zs + e, z[i]);
+        F::st(a.zm + i * a.zs + e, gz[i]);
+    }
+    if (a.opened) {
+        F::st(a.opened + 2 * e, eps);
+        F::st(a.opened + 2 * e + 1, dlt);
+    }
+}
+
 template <class F, int NP, int V>
 __device__ __forceinline__ void mul_elems(const MulArgs<F> &a, int64_t e, uint64_t key,
                                           const typename F::T (&alpha)[NP], typename F::T (&acc)[NP + 1]) {
@@ -168,67 +247,120 @@ __device__ __forceinline__ void mul_elems(const MulArgs<F> &a, int64_t e, uint64
 
 // Two CTAs of 256 threads per SM (at most 128 registers) while a thread's
 // NP x V products fit them; larger instances keep one.
-template <int NP, int V> constexpr int mul_min_blocks() { return NP * V <= 12 ? 2 : 1; }
+// p127 keeps its unreduced three-word check sums live across elements: one.
+template <class F, int NP, int V> constexpr int mul_min_blocks() {
+    return std::is_same_v<F, F127> ? 1 : NP * V <= 12 ? 2 : 1;
+}
 
 template <class F, int NP, int V>
-__global__ void __launch_bounds__(256, mul_min_blocks<NP, V>()) k_mul(MulArgs<F> a) {
+__global__ void __launch_bounds__(256, (mul_min_blocks<F, NP, V>())) k_mul(MulArgs<F> a) {
     using T = typename F::T;
     const uint64_t key = a.ds->key;
-    T alpha[NP], acc[NP + 1];
+    if constexpr (std::is_same_v<F, F127>) {
+        u128v alpha[NP], acc[NP + 1];
+        W127 wacc[NP + 1];
 #pragma unroll
-    for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
+        for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a.N; e += stride)
+            mul_elem127<NP>(a, e, key, alpha, wacc);
 #pragma unroll
-    for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t ng = a.N / V;
-    for (int64_t g = tid; g < ng; g += stride) mul_elems<F, NP, V>(a, g * V, key, alpha, acc);
-    for (int64_t e = ng * V + tid; e < a.N; e += stride) mul_elems<F, NP, 1>(a, e, key, alpha, acc);
-    block_accumulate<F, NP + 1>(acc, a.ds->acc);
+        for (int k = 0; k < NP + 1; ++k) acc[k] = wacc[k].reduce();
+        block_accumulate<F, NP + 1>(acc, a.ds->acc);
+    } else {
+        T alpha[NP], acc[NP + 1];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
+#pragma unroll
+        for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        const int64_t ng = a.N / V;
+        for (int64_t g = tid; g < ng; g += stride) mul_elems<F, NP, V>(a, g * V, key, alpha, acc);
+        for (int64_t e = ng * V + tid; e < a.N; e += stride) mul_elems<F, NP, 1>(a, e, key, alpha, acc);
+        block_accumulate<F, NP + 1>(acc, a.ds->acc);
+    }
 }
 
 // Inner products: one warp per product t; lane l takes terms l, l+32, ...;
 // the per-party sums of the term products (value and MAC) are reduced
 // across the warp and stored by lane 0.  N = number of products.
+// Two CTAs per SM: latency of the lanes' term loads is hidden by more
+// resident warps (p127 then keeps its sums in 128 registers with a few
+// spilled, and is faster than with one CTA and no spill).
 template <class F, int NP>
-__global__ void __launch_bounds__(256) k_innerprod(MulArgs<F> a) {
+__global__ void __launch_bounds__(256, 2) k_innerprod(MulArgs<F> a) {
     using T = typename F::T;
     const uint64_t key = a.ds->key;
-    T alpha[NP], acc[NP + 1];
+    if constexpr (std::is_same_v<F, F127>) {
+        // the term products' shares are summed unreduced across a lane's
+        // terms and reduced once per product before the warp sum
+        u128v alpha[NP], acc[NP + 1];
+        W127 wacc[NP + 1];
 #pragma unroll
-    for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
-#pragma unroll
-    for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
-    const int lane = threadIdx.x & 31;
-    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < a.N; t += wstride) {
-        T sz[NP], sg[NP];
-#pragma unroll
-        for (int i = 0; i < NP; ++i) sz[i] = sg[i] = F::zero();
-        for (int64_t k = lane; k < a.len; k += 32) {
-            const int64_t e = t * a.len + k;
-            T z[NP][1], gz[NP][1], eps[1], dlt[1];
-            beaver_core<F, NP, 1>(a, e, e, key, alpha, acc, z, gz, eps, dlt);
+        for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
+        const int lane = threadIdx.x & 31;
+        const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < a.N; t += wstride) {
+            W127 sums[2 * NP];
+            for (int64_t k = lane; k < a.len; k += 32) {
+                u128v z[NP], gz[NP], eps, dlt;
+                beaver_core127<NP>(a, t * a.len + k, key, alpha, wacc, z, gz, eps, dlt, sums);
+            }
+            u128v sz[NP], sg[NP];
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
-                sz[i] = F::add(sz[i], z[i][0]);
-                sg[i] = F::add(sg[i], gz[i][0]);
+                sz[i] = warp_sum<F>(sums[i].reduce());
+                sg[i] = warp_sum<F>(sums[NP + i].reduce());
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    F::st(a.zv + i * a.zs + t, sz[i]);
+                    F::st(a.zm + i * a.zs + t, sg[i]);
+                }
             }
         }
 #pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            sz[i] = warp_sum<F>(sz[i]);
-            sg[i] = warp_sum<F>(sg[i]);
-        }
-        if (lane == 0) {
+        for (int k = 0; k < NP + 1; ++k) acc[k] = wacc[k].reduce();
+        block_accumulate<F, NP + 1>(acc, a.ds->acc);
+    } else {
+        T alpha[NP], acc[NP + 1];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
+#pragma unroll
+        for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
+        const int lane = threadIdx.x & 31;
+        const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < a.N; t += wstride) {
+            T sz[NP], sg[NP];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) sz[i] = sg[i] = F::zero();
+            for (int64_t k = lane; k < a.len; k += 32) {
+                const int64_t e = t * a.len + k;
+                T z[NP][1], gz[NP][1], eps[1], dlt[1];
+                beaver_core<F, NP, 1>(a, e, e, key, alpha, acc, z, gz, eps, dlt);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    sz[i] = F::add(sz[i], z[i][0]);
+                    sg[i] = F::add(sg[i], gz[i][0]);
+                }
+            }
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
-                F::st(a.zv + i * a.zs + t, sz[i]);
-                F::st(a.zm + i * a.zs + t, sg[i]);
+                sz[i] = warp_sum<F>(sz[i]);
+                sg[i] = warp_sum<F>(sg[i]);
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    F::st(a.zv + i * a.zs + t, sz[i]);
+                    F::st(a.zm + i * a.zs + t, sg[i]);
+                }
             }
         }
+        block_accumulate<F, NP + 1>(acc, a.ds->acc);
     }
-    block_accumulate<F, NP + 1>(acc, a.ds->acc);
 }
 
 // ----------------------------------------------------------------- open

@@ -236,4 +236,74 @@ struct F127 {
     }
 };
 
+// Deferred reduction for p127: an exact sum below 2^190 in three words,
+// reduced once.  A product of a, b < 2^127 enters as three word-aligned
+// pieces congruent to it: with a = a1 2^64 + a0, b = b1 2^64 + b0 and
+// m = a1 b0 + a0 b1 = mh 2^64 + ml (below 2^128), 2^128 == 2 (mod p) gives
+//   a b == a0 b0 + ml 2^64 + 2 (a1 b1 + mh),
+// each piece below 2^128, so no product is folded at bit 127 on its own.
+struct W127 {
+    uint64_t w0 = 0, w1 = 0, w2 = 0;
+    // += c, c below 2^128
+    __device__ __forceinline__ void add(u128v c) {
+        asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, 0;"
+            : "+l"(w0), "+l"(w1), "+l"(w2) : "l"(c.lo), "l"(c.hi));
+    }
+    // += another three-word sum
+    __device__ __forceinline__ void add(const W127 &q) {
+        asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, %5;"
+            : "+l"(w0), "+l"(w1), "+l"(w2) : "l"(q.w0), "l"(q.w1), "l"(q.w2));
+    }
+    // A three-word value congruent to a * b (mod p), a and b below 2^127
+    // (below 3 * 2^128): the product's pieces are summed here, so several
+    // products can be formed independently before they meet in one sum.
+    __device__ __forceinline__ static W127 prod(u128v a, u128v b) {
+        const uint64_t p0l = a.lo * b.lo, p0h = __umul64hi(a.lo, b.lo);
+        uint64_t ml = a.hi * b.lo, mh = __umul64hi(a.hi, b.lo);
+        const uint64_t ql = a.lo * b.hi, qh = __umul64hi(a.lo, b.hi);
+        asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(ml), "+l"(mh) : "l"(ql), "l"(qh));
+        uint64_t tl = a.hi * b.hi, th = __umul64hi(a.hi, b.hi);     // a1 b1 < 2^126
+        asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(tl), "+l"(th) : "l"(mh));   // < 2^127
+        W127 q;
+        q.w0 = tl << 1;
+        q.w1 = (th << 1) | (tl >> 63);
+        asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, 0, 0;\n\t"
+            "add.cc.u64 %1, %1, %5;\n\taddc.u64 %2, %2, 0;"
+            : "+l"(q.w0), "+l"(q.w1), "=l"(q.w2) : "l"(p0l), "l"(p0h), "l"(ml));
+        return q;
+    }
+    // += a * b (mod p), a and b below 2^127
+    __device__ __forceinline__ void mac(u128v a, u128v b) { add(prod(a, b)); }
+    // The sum mod 2^127 - 1: w2 2^128 == 2 w2; the 128-bit rest and its carry
+    // are folded at bit 127 (below 2^127 + 3 after the fold), and s >= p
+    // exactly when s + 1 reaches 2^127, where s - p = s + 1 - 2^127.
+    __device__ __forceinline__ u128v reduce() const {
+        uint64_t x0 = w0, x1 = w1, c;
+        asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, 0;\n\taddc.u64 %2, 0, 0;"
+            : "+l"(x0), "+l"(x1), "=l"(c) : "l"(w2 << 1));
+        uint64_t s0 = x0, s1 = x1 & F127::PHI;
+        asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(s0), "+l"(s1) : "l"((x1 >> 63) + 2 * c));
+        uint64_t t0 = s0, t1 = s1;
+        asm("add.cc.u64 %0, %0, 1;\n\taddc.u64 %1, %1, 0;" : "+l"(t0), "+l"(t1));
+        if (t1 >> 63) return {t0, t1 & F127::PHI};
+        return {s0, s1};
+    }
+};
+
+template <> struct Fma<F127> {
+    __device__ __forceinline__ static u128v f2(u128v c, u128v a1, u128v b1, u128v a2, u128v b2) {
+        W127 w = W127::prod(a1, b1);
+        w.add(W127::prod(a2, b2));
+        w.add(c);
+        return w.reduce();
+    }
+    __device__ __forceinline__ static u128v f3(u128v c, u128v a1, u128v b1, u128v a2, u128v b2, u128v a3, u128v b3) {
+        W127 w = W127::prod(a1, b1), v = W127::prod(a2, b2);
+        w.add(W127::prod(a3, b3));
+        v.add(c);
+        w.add(v);
+        return w.reduce();
+    }
+};
+
 }  // namespace spdz
