@@ -637,6 +637,22 @@ int spdz_load_matvec_preproc(spdz_ctx *ctx, const spdz_buf *A, const spdz_buf *B
 int spdz_linear_layer(spdz_ctx *ctx, const spdz_buf *W, const spdz_buf *x, const spdz_buf *b, const spdz_buf *y,
                       int64_t dout, int64_t din, int64_t tile_rows, void *D_out_dev, void *E_out_dev);
 
+/* ------------------------------------------------------------ measurement
+ * Integer issue-rate microbenchmark (no counterpart in the paper; the
+ * compute-side denominator of the roofline of kernels bound by integer
+ * arithmetic, such as the p = 2^127-1 products): every thread of a grid of
+ * 8 CTAs x 256 threads per SM runs eight independent chains of one
+ * instruction kind for `iters` x 4 rounds:
+ *   kind 0: 32-bit multiply-add, low half (mad.lo.u32);
+ *   kind 1: 32 x 32 + 64 -> 64 multiply-add (mad.wide.u32);
+ *   kind 2: high half of a 32 x 32 product then an add (mul.hi.u32, add.u32);
+ *   kind 3: integer add then xor (add.u32, xor.b32).
+ * *ops_per_s receives thread-level instructions per second (both
+ * instructions of a kind-2 or kind-3 pair counted).  scratch_dev: device
+ * buffer of at least 8 x 256 x SMs uint32 (written).  Synchronises the
+ * stream.  Errors: SPDZ_ERR_ARG, SPDZ_ERR_CUDA. */
+int spdz_int_peak(int kind, int64_t iters, void *stream, void *scratch_dev, double *ops_per_s);
+
 #ifdef __cplusplus
 }
 #endif

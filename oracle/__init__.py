@@ -396,6 +396,33 @@ def dag_eval(p: int, dag, wv, wm, tri: Triples, alpha_sh):
     return eps, dlt, interleave_log(p, eps, dlt, em, dm)
 
 
+def dag_eval_layers(p: int, dag, wv, wm, tri: Triples, alpha_sh):
+    """The same evaluation as dag_eval, layer by layer with each layer's gates
+    spread over the oracle's threads (set_threads); returns the same
+    (eps, dlt, OpenLog)."""
+    n = wv.shape[0]
+    T = tri.av.shape[1]
+    nm = int(np.count_nonzero(dag.ops == OP_MUL))
+    eps, dlt = zeros(p, nm), zeros(p, nm)
+    em, dm = zeros(p, n, nm), zeros(p, n, nm)
+    ops = np.ascontiguousarray(dag.ops, dtype=np.uint8)
+    in0 = np.ascontiguousarray(dag.in0, dtype=np.uint32)
+    in1 = np.ascontiguousarray(dag.in1, dtype=np.uint32)
+    k = np.ascontiguousarray(dag.kconst, dtype=np.uint64)
+    off = np.ascontiguousarray(dag.layer_offsets, dtype=np.int64)
+    rc = lib().orc_dag_eval_layers(*_pp(p), C.c_int(n), C.c_int64(dag.n_inputs), C.c_int64(dag.n_gates),
+                                   C.c_int(off.size - 1), off.ctypes.data_as(C.POINTER(C.c_int64)),
+                                   ops.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                   in0.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                   in1.ctypes.data_as(C.POINTER(C.c_uint32)), _ptr(k), _ptr(alpha_sh),
+                                   _ptr(wv), _ptr(wm), C.c_int64(T), _ptr(tri.av), _ptr(tri.am),
+                                   _ptr(tri.bv), _ptr(tri.bm), _ptr(tri.cv), _ptr(tri.cm),
+                                   _ptr(eps), _ptr(dlt), _ptr(em), _ptr(dm))
+    if rc != 0:
+        raise ValueError("dag_eval_layers: an operand is not written before its layer")
+    return eps, dlt, interleave_log(p, eps, dlt, em, dm)
+
+
 def dag_clear(p: int, dag, inputs) -> np.ndarray:
     """Cleartext evaluation: wires [W] from the input secrets [n_inputs]."""
     wires = zeros(p, dag.n_wires)

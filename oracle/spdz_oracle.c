@@ -829,6 +829,82 @@ void orc_input(u64 plo, u64 phi, int n, int64_t count, const u64 *x, const u64 *
  * one field element per gate (used by CMUL and CADD).  eps/dlt are [n_mul]
  * and eps_mac/dlt_mac [n][n_mul], n_mul = number of MUL gates.
  */
+typedef struct {
+    u128 p; int w, n;
+    int64_t n_in, W, T, n_mul;
+    const uint8_t *ops; const uint32_t *in0, *in1;
+    const u64 *kconst, *alpha_sh;
+    u64 *wv, *wm;
+    const u64 *av, *am, *bv, *bm, *cv, *cm;
+    u64 *eps, *dlt, *eps_mac, *dlt_mac;
+    const int64_t *mul_rank;     /* layer-parallel form: MUL rank of each gate */
+    int64_t g0;                  /* layer-parallel form: first gate of the layer */
+} dag_ctx;
+
+/* Gate g; t = its MUL rank (the triple it consumes when it is a MUL gate). */
+static void dag_gate(const dag_ctx *c, int64_t g, int64_t t) {
+    u128 p = c->p; int w = c->w, n = c->n;
+    int64_t W = c->W, T = c->T, n_mul = c->n_mul;
+    int64_t out = c->n_in + g, a0 = c->in0[g], a1 = c->in1[g];
+    int op = c->ops[g];
+    u64 *wv = c->wv, *wm = c->wm;
+    if (op == OP_MUL) {
+        u128 d = 0, e = 0;
+        for (int i = 0; i < n; ++i) {
+            d = f_add(d, f_sub(ld(wv, i * W + a0, w), ld(c->av, i * T + t, w), p), p);
+            e = f_add(e, f_sub(ld(wv, i * W + a1, w), ld(c->bv, i * T + t, w), p), p);
+        }
+        u128 de = f_mul(d, e, p);
+        for (int i = 0; i < n; ++i) {
+            int64_t q = i * T + t;
+            u128 z = f_add(ld(c->cv, q, w), f_add(f_mul(d, ld(c->bv, q, w), p), f_mul(e, ld(c->av, q, w), p), p), p);
+            if (i == 0) z = f_add(z, de, p);
+            u128 gz = f_add(ld(c->cm, q, w), f_add(f_mul(d, ld(c->bm, q, w), p), f_mul(e, ld(c->am, q, w), p), p), p);
+            gz = f_add(gz, f_mul(ld(c->alpha_sh, i, w), de, p), p);
+            if (c->eps_mac) st(c->eps_mac, (int64_t)i * n_mul + t, w, f_sub(ld(wm, i * W + a0, w), ld(c->am, q, w), p));
+            if (c->dlt_mac) st(c->dlt_mac, (int64_t)i * n_mul + t, w, f_sub(ld(wm, i * W + a1, w), ld(c->bm, q, w), p));
+            st(wv, i * W + out, w, z);
+            st(wm, i * W + out, w, gz);
+        }
+        if (c->eps) st(c->eps, t, w, d);
+        if (c->dlt) st(c->dlt, t, w, e);
+    } else {
+        u128 k = ld(c->kconst, g, w);
+        for (int i = 0; i < n; ++i) {
+            u128 x = ld(wv, i * W + a0, w), gx = ld(wm, i * W + a0, w), z, gz;
+            if (op == OP_ADD) {
+                z = f_add(x, ld(wv, i * W + a1, w), p); gz = f_add(gx, ld(wm, i * W + a1, w), p);
+            } else if (op == OP_SUB) {
+                z = f_sub(x, ld(wv, i * W + a1, w), p); gz = f_sub(gx, ld(wm, i * W + a1, w), p);
+            } else if (op == OP_CMUL) {
+                z = f_mul(k, x, p); gz = f_mul(k, gx, p);
+            } else {
+                z = (i == 0) ? f_add(x, k, p) : x;
+                gz = f_add(gx, f_mul(ld(c->alpha_sh, i, w), k, p), p);
+            }
+            st(wv, i * W + out, w, z);
+            st(wm, i * W + out, w, gz);
+        }
+    }
+}
+
+static dag_ctx dag_ctx_make(u64 plo, u64 phi, int n, int64_t n_in, int64_t n_gates,
+                            const uint8_t *ops, const uint32_t *in0, const uint32_t *in1,
+                            const u64 *kconst, const u64 *alpha_sh, u64 *wv, u64 *wm,
+                            int64_t T, const u64 *av, const u64 *am, const u64 *bv, const u64 *bm,
+                            const u64 *cv, const u64 *cm, u64 *eps, u64 *dlt, u64 *eps_mac, u64 *dlt_mac) {
+    dag_ctx c;
+    c.p = mkp(plo, phi); c.w = words_of(c.p); c.n = n;
+    c.n_in = n_in; c.W = n_in + n_gates; c.T = T;
+    c.n_mul = 0;
+    for (int64_t g = 0; g < n_gates; ++g) c.n_mul += (ops[g] == OP_MUL);
+    c.ops = ops; c.in0 = in0; c.in1 = in1; c.kconst = kconst; c.alpha_sh = alpha_sh;
+    c.wv = wv; c.wm = wm; c.av = av; c.am = am; c.bv = bv; c.bm = bm; c.cv = cv; c.cm = cm;
+    c.eps = eps; c.dlt = dlt; c.eps_mac = eps_mac; c.dlt_mac = dlt_mac;
+    c.mul_rank = NULL; c.g0 = 0;
+    return c;
+}
+
 void orc_dag_eval(u64 plo, u64 phi, int n, int64_t n_in, int64_t n_gates,
                   const uint8_t *ops, const uint32_t *in0, const uint32_t *in1,
                   const u64 *kconst, const u64 *alpha_sh,
@@ -836,53 +912,59 @@ void orc_dag_eval(u64 plo, u64 phi, int n, int64_t n_in, int64_t n_gates,
                   int64_t T, const u64 *av, const u64 *am, const u64 *bv, const u64 *bm,
                   const u64 *cv, const u64 *cm,
                   u64 *eps, u64 *dlt, u64 *eps_mac, u64 *dlt_mac) {
-    u128 p = mkp(plo, phi); int w = words_of(p);
-    int64_t W = n_in + n_gates;
-    int64_t n_mul = 0, t = 0;
-    for (int64_t g = 0; g < n_gates; ++g) n_mul += (ops[g] == OP_MUL);
+    dag_ctx c = dag_ctx_make(plo, phi, n, n_in, n_gates, ops, in0, in1, kconst, alpha_sh, wv, wm, T,
+                             av, am, bv, bm, cv, cm, eps, dlt, eps_mac, dlt_mac);
+    int64_t t = 0;
     for (int64_t g = 0; g < n_gates; ++g) {
-        int64_t out = n_in + g, a0 = in0[g], a1 = in1[g];
-        int op = ops[g];
-        if (op == OP_MUL) {
-            u128 d = 0, e = 0;
-            for (int i = 0; i < n; ++i) {
-                d = f_add(d, f_sub(ld(wv, i * W + a0, w), ld(av, i * T + t, w), p), p);
-                e = f_add(e, f_sub(ld(wv, i * W + a1, w), ld(bv, i * T + t, w), p), p);
-            }
-            u128 de = f_mul(d, e, p);
-            for (int i = 0; i < n; ++i) {
-                int64_t q = i * T + t;
-                u128 z = f_add(ld(cv, q, w), f_add(f_mul(d, ld(bv, q, w), p), f_mul(e, ld(av, q, w), p), p), p);
-                if (i == 0) z = f_add(z, de, p);
-                u128 gz = f_add(ld(cm, q, w), f_add(f_mul(d, ld(bm, q, w), p), f_mul(e, ld(am, q, w), p), p), p);
-                gz = f_add(gz, f_mul(ld(alpha_sh, i, w), de, p), p);
-                if (eps_mac) st(eps_mac, (int64_t)i * n_mul + t, w, f_sub(ld(wm, i * W + a0, w), ld(am, q, w), p));
-                if (dlt_mac) st(dlt_mac, (int64_t)i * n_mul + t, w, f_sub(ld(wm, i * W + a1, w), ld(bm, q, w), p));
-                st(wv, i * W + out, w, z);
-                st(wm, i * W + out, w, gz);
-            }
-            if (eps) st(eps, t, w, d);
-            if (dlt) st(dlt, t, w, e);
-            ++t;
-        } else {
-            u128 k = ld(kconst, g, w);
-            for (int i = 0; i < n; ++i) {
-                u128 x = ld(wv, i * W + a0, w), gx = ld(wm, i * W + a0, w), z, gz;
-                if (op == OP_ADD) {
-                    z = f_add(x, ld(wv, i * W + a1, w), p); gz = f_add(gx, ld(wm, i * W + a1, w), p);
-                } else if (op == OP_SUB) {
-                    z = f_sub(x, ld(wv, i * W + a1, w), p); gz = f_sub(gx, ld(wm, i * W + a1, w), p);
-                } else if (op == OP_CMUL) {
-                    z = f_mul(k, x, p); gz = f_mul(k, gx, p);
-                } else {
-                    z = (i == 0) ? f_add(x, k, p) : x;
-                    gz = f_add(gx, f_mul(ld(alpha_sh, i, w), k, p), p);
-                }
-                st(wv, i * W + out, w, z);
-                st(wm, i * W + out, w, gz);
-            }
+        dag_gate(&c, g, t);
+        if (ops[g] == OP_MUL) ++t;
+    }
+}
+
+static void dag_layer_range(void *ctx, int64_t lo, int64_t hi) {
+    const dag_ctx *c = (const dag_ctx *)ctx;
+    for (int64_t k = lo; k < hi; ++k) dag_gate(c, c->g0 + k, c->mul_rank[c->g0 + k]);
+}
+
+/* The same evaluation, layer by layer, with the gates of a layer spread over
+ * the oracle's threads (layer l = gates [off[l], off[l+1])): a gate's triple
+ * is still its MUL rank in gate order, so every share equals orc_dag_eval's.
+ * Every operand of a layer's gates must be written before the layer (an
+ * input or an earlier layer's output); returns -1 (nothing evaluated) when
+ * one is not, 0 otherwise. */
+int orc_dag_eval_layers(u64 plo, u64 phi, int n, int64_t n_in, int64_t n_gates, int depth,
+                        const int64_t *layer_offsets,
+                        const uint8_t *ops, const uint32_t *in0, const uint32_t *in1,
+                        const u64 *kconst, const u64 *alpha_sh,
+                        u64 *wv, u64 *wm,
+                        int64_t T, const u64 *av, const u64 *am, const u64 *bv, const u64 *bm,
+                        const u64 *cv, const u64 *cm,
+                        u64 *eps, u64 *dlt, u64 *eps_mac, u64 *dlt_mac) {
+    if (depth < 0 || layer_offsets[0] != 0 || layer_offsets[depth] != n_gates) return -1;
+    for (int l = 0; l < depth; ++l) {
+        if (layer_offsets[l + 1] < layer_offsets[l]) return -1;
+        for (int64_t g = layer_offsets[l]; g < layer_offsets[l + 1]; ++g) {
+            int binary = ops[g] == OP_ADD || ops[g] == OP_SUB || ops[g] == OP_MUL;
+            if ((int64_t)in0[g] >= n_in + layer_offsets[l] || (binary && (int64_t)in1[g] >= n_in + layer_offsets[l]))
+                return -1;
         }
     }
+    int64_t *rank = (int64_t *)malloc((size_t)(n_gates > 0 ? n_gates : 1) * sizeof(int64_t));
+    if (!rank) return -1;
+    int64_t t = 0;
+    for (int64_t g = 0; g < n_gates; ++g) {
+        rank[g] = t;
+        if (ops[g] == OP_MUL) ++t;
+    }
+    dag_ctx c = dag_ctx_make(plo, phi, n, n_in, n_gates, ops, in0, in1, kconst, alpha_sh, wv, wm, T,
+                             av, am, bv, bm, cv, cm, eps, dlt, eps_mac, dlt_mac);
+    c.mul_rank = rank;
+    for (int l = 0; l < depth; ++l) {
+        c.g0 = layer_offsets[l];
+        parallel_for(layer_offsets[l + 1] - layer_offsets[l], dag_layer_range, &c);
+    }
+    free(rank);
+    return 0;
 }
 
 /* Cleartext evaluation of the same circuit on the secrets, for the

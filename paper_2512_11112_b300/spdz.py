@@ -142,6 +142,7 @@ _SIGS = {
     "spdz_mlp_loss_grad": [_vp, _vp, _vp, _i64, _vp, _vp],
     "spdz_mlp_train": [_vp, _vp, _vp, _i64, C.c_int32, C.c_int32, C.c_float, _vp],
     "spdz_mlp_adam_step": [_vp, _vp, C.c_float],
+    "spdz_int_peak": [_int, _i64, _vp, _vp, C.POINTER(C.c_double)],
     "spdz_sched_num_configs": [C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "spdz_sched_config_plan": [_vp, C.c_int32, C.POINTER(spdz_plan)],
     "spdz_sched_record": [_vp, _vp, _bufp, C.c_int32],
@@ -675,3 +676,12 @@ def spdz_reveal(ctx, x: spdz_buf, out, N: int, sigma_host=None) -> bool:
     if rc not in (SPDZ_OK, SPDZ_ERR_MAC):
         _chk(ctx, rc)
     return bool(ok.value)
+
+
+# ------------------------------------------------------------ measurement
+
+def spdz_int_peak(kind: int, iters: int, stream, scratch) -> float:
+    """Thread-level integer instructions per second of one kind (see spdz.h)."""
+    r = C.c_double()
+    _chk(None, lib.spdz_int_peak(kind, iters, stream, ptr(scratch), C.byref(r)))
+    return r.value

@@ -351,6 +351,36 @@ def test_dag_shared_equals_cleartext(p):
     assert ok
 
 
+@pytest.mark.parametrize("p,widths", [(O.P61, [5000, 7, 1, 6000, 4097]), (O.P127, [4500, 300, 4100]),
+                                      (O.P32, [9000, 1, 8192])])
+def test_layer_parallel_eval_equals_gate_order(p, widths):
+    """The layer-parallel evaluation on 4 threads (layers wide enough to be
+    split) gives every wire share and every opened value and MAC share of the
+    gate-order evaluation; a gate whose operand is written in its own layer
+    is refused."""
+    n = 3
+    dag = W.small_dag(seed=21, p=p, n_inputs=512, widths=widths)
+    alpha, ash = O.deal_alpha(p, n, 21)
+    iv, im, _ = O.deal_shared(p, n, 21, O.K_INPUT, 16, 0, dag.n_inputs, alpha)
+    tri = O.deal_triples(p, n, 21, 0, dag.n_mul, alpha)
+    outs = []
+    for fn, threads in ((O.dag_eval, 1), (O.dag_eval_layers, 4)):
+        O.set_threads(threads)
+        wv, wm = O.zeros(p, n, dag.n_wires), O.zeros(p, n, dag.n_wires)
+        wv[:, :dag.n_inputs], wm[:, :dag.n_inputs] = iv, im
+        eps, dlt, log = fn(p, dag, wv, wm, tri, ash)
+        outs.append((wv, wm, eps, dlt, log.vals, log.macs))
+    O.set_threads(1)
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    bad = W.small_dag(seed=21, p=p, n_inputs=512, widths=widths)
+    g = int(bad.layer_offsets[1]) + 3
+    bad.in0[g] = bad.n_inputs + g - 1                 # an output of the same layer
+    wv, wm = O.zeros(p, n, dag.n_wires), O.zeros(p, n, dag.n_wires)
+    with pytest.raises(ValueError):
+        O.dag_eval_layers(p, bad, wv, wm, tri, ash)
+
+
 # ---------------------------------------------------------- workload shapes
 
 def test_benchmark_dag_shape():
