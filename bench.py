@@ -306,77 +306,71 @@ def beaver_roofline(torch, S, SH, hbm_peak, N=2**24, calls=4, field=None):
 
 
 def e2e_steps(circ, plan, steps):
-    """Same metric through the public call with host buffers: each step
-    copies its input shares and the triples it consumes from pinned host
-    memory, runs, and copies the last layer's output shares back.  The
-    triples of step k+1 (their own pool slots) are copied on a second stream
-    while step k runs; the inputs (the same wires every step) are copied
-    after step k on the run's stream.  Every run checks its MACs on the
-    device; the verdict of the last one is read after the last step."""
+    """Same metric through the library's host-buffer call (spdz_run_dag_host):
+    each step hands it page-locked host buffers holding the step's input
+    shares and the triples it consumes, and receives the last layer's output
+    shares back in host memory.  The library copies a step's triples on its
+    own copy stream, so they overlap the step before; the inputs and outputs
+    move on the run's stream.  Every run checks its MACs on the device; the
+    verdict of the last one is read after the last step."""
     torch = circ.torch
     dag, S = circ.dag, circ.S
     nin, nm = dag.n_inputs, dag.n_mul
     out_lo = dag.n_inputs + int(dag.layer_offsets[-2])
+    cnt = dag.n_wires - out_lo
     h_in = [circ.wires.val[:, :nin].cpu().pin_memory(), circ.wires.mac[:, :nin].cpu().pin_memory()]
     circ.ensure(steps)
-    base = circ.S.spdz_triples_left(circ.ctx)
-    c0 = circ.T - base
-    # each step's own triples (a triple is never reused), staged in pinned memory
+    c0 = circ.T - circ.S.spdz_triples_left(circ.ctx)
+    # each step's own triples (a triple is never reused), staged in pinned
+    # memory (the offline phase, before the timed region)
     h_tri = []
     for k in range(steps):
         lo = c0 + k * nm
-        h_tri.append([part[:, lo:lo + nm].cpu().pin_memory() for t in circ.tri for part in (t.val, t.mac)])
-    h_out = [[torch.empty_like(circ.wires.val[:, out_lo:dag.n_wires], device="cpu").pin_memory()
-              for _ in range(2)] for _ in range(2)]
+        h_tri.append([part[:, lo:lo + nm].contiguous().cpu().pin_memory() for t in circ.tri for part in (t.val, t.mac)])
+    h_out = [[torch.empty((N_PARTIES, cnt), dtype=torch.int64).pin_memory() for _ in range(2)] for _ in range(2)]
     bi = sum(x.numel() * 8 for x in h_in) + sum(x.numel() * 8 for x in h_tri[0])
     bo = sum(x.numel() * 8 for x in h_out[0]) + 4
-    side = torch.cuda.Stream()
-    ready = [torch.cuda.Event() for _ in range(steps)]
-
-    def copy_triples(k):
-        with torch.cuda.stream(side):
-            lo, j = c0 + k * nm, 0
-            for t in circ.tri:
-                for part in (t.val, t.mac):
-                    part[:, lo:lo + nm].copy_(h_tri[k][j], non_blocking=True)
-                    j += 1
-            ready[k].record(side)
-
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    copy_triples(0)
     for k in range(steps):
-        if k + 1 < steps:
-            copy_triples(k + 1)
-        circ.wires.val[:, :nin].copy_(h_in[0], non_blocking=True)
-        circ.wires.mac[:, :nin].copy_(h_in[1], non_blocking=True)
-        circ.stream.wait_event(ready[k])
-        circ.run(plan)
-        h_out[k % 2][0].copy_(circ.wires.val[:, out_lo:dag.n_wires], non_blocking=True)
-        h_out[k % 2][1].copy_(circ.wires.mac[:, out_lo:dag.n_wires], non_blocking=True)
-    torch.cuda.synchronize()
-    ok = S.spdz_check_result(circ.ctx)
+        o = h_out[k % 2]
+        S.spdz_run_dag_host(circ.ctx, circ.h, plan, circ.wires.buf(), h_in[0], h_in[1], h_tri[k], out_lo, cnt,
+                            o[0], o[1])
+        circ.used += 1
+    ok = S.spdz_check_result(circ.ctx)       # synchronises the stream
     dt = time.perf_counter() - t0
     return dt, bi, bo, ok
 
 
-def cpu_baseline(dag, seed):
-    """The CPU oracle as it stands: one evaluation of the whole circuit
-    (gate order, one thread) on the oracle's own dealt shares."""
+def cpu_baseline(dag, seed, reps=3):
+    """The CPU oracle as it stands on the benchmark circuit, on the oracle's own
+    dealt shares: the layer-parallel evaluation on every host core (median of
+    `reps` full evaluations), and the gate-order evaluation on one core (one
+    full evaluation)."""
     import oracle as O
     p, n = dag.p, N_PARTIES
+    cores = os.cpu_count() or 1
     alpha, ash = O.deal_alpha(p, n, seed)
     iv, im, _ = O.deal_shared(p, n, seed, O.K_INPUT, INPUT_SUB, 0, dag.n_inputs, alpha)
-    wv, wm = O.zeros(p, n, dag.n_wires), O.zeros(p, n, dag.n_wires)
-    wv[:, :dag.n_inputs], wm[:, :dag.n_inputs] = iv, im
     tri = O.deal_triples(p, n, seed, 0, dag.n_mul, alpha)
-    t0 = time.perf_counter()
-    O.dag_eval(p, dag, wv, wm, tri, ash)
-    dt = time.perf_counter() - t0
-    return {"value": dag.n_mul / dt, "unit": "Beaver mults/s", "cores": 1, "kind": "oracle",
-            "sample": f"one full evaluation of the benchmark circuit ({dag.n_gates} gates, "
-                      f"{dag.n_mul} Beaver mults, 3 parties) by the oracle's gate-order loop, "
-                      f"{dt:.2f} s"}
+
+    def one(fn, threads):
+        O.set_threads(threads)
+        wv, wm = O.zeros(p, n, dag.n_wires), O.zeros(p, n, dag.n_wires)
+        wv[:, :dag.n_inputs], wm[:, :dag.n_inputs] = iv, im
+        t0 = time.perf_counter()
+        fn(p, dag, wv, wm, tri, ash)
+        return time.perf_counter() - t0
+
+    t_all = statistics.median([one(O.dag_eval_layers, cores) for _ in range(reps)])
+    t_one = one(O.dag_eval, 1)
+    O.set_threads(1)
+    return {"value": dag.n_mul / t_all, "unit": "Beaver mults/s", "cores": cores, "kind": "oracle",
+            "sample": f"full evaluations of the benchmark circuit ({dag.n_gates} gates, {dag.n_mul} Beaver mults, "
+                      f"3 parties) by the oracle's layer-parallel loop on {cores} threads, median of {reps} "
+                      f"({t_all:.3f} s each)",
+            "single_core": {"value": dag.n_mul / t_one, "unit": "Beaver mults/s", "cores": 1,
+                            "sample": f"one full evaluation by the oracle's gate-order loop, {t_one:.3f} s"}}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -391,6 +385,7 @@ def run_ours(args, rank, world, local_rank):
     circ = Circuit(dag, seed=2 + 1000 * rank, runs=2 * (steps + warmup) + e2e_n, pool_runs=64)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     per_layer = S.plan(mode=S.SPDZ_SCHED_PER_LAYER, use_graph=0)
+    per_layer_graph = S.plan(mode=S.SPDZ_SCHED_PER_LAYER, use_graph=1)
     sched = schedule(circ)
     scheduled = None          # plan-less runs use the plan the scheduler chose
 
@@ -409,7 +404,9 @@ def run_ours(args, rank, world, local_rank):
     t_p, ok_p = time_steps(circ, per_layer, steps, warmup, flush)
     barrier()
     torch.cuda.cudart().cudaProfilerStop()
-    tot_f, tot_p = max_over_ranks([sum(t_f), sum(t_p)], world)
+    t_pg, ok_pg = time_steps(circ, per_layer_graph, steps, warmup, flush)
+    barrier()
+    tot_f, tot_p, tot_pg = max_over_ranks([sum(t_f), sum(t_p), sum(t_pg)], world)
     e2e_dt, bi, bo, ok_e = e2e_steps(circ, scheduled, e2e_n)
     (e2e_dt,) = max_over_ranks([e2e_dt], world)
     if rank != 0:
@@ -437,6 +434,9 @@ def run_ours(args, rank, world, local_rank):
             and g["cluster"] == cap.get("cluster") for g in groups))
         traffic = tr.get("k_dag_fused") if same else None
     beaver = beaver_roofline(torch, S, SH, hbm)
+    del circ
+    torch.cuda.empty_cache()
+    extras = all_configs(args) if world == 1 and not args.no_extras else None
     cpu = cpu_baseline(dag, seed=2) if not args.no_cpu_baseline else None
     line = {
         "metric": METRIC,
@@ -457,9 +457,13 @@ def run_ours(args, rank, world, local_rank):
                    "scheduler": "fused persistent kernels + CUDA graph, plan chosen by the learned scheduler "
                                 "(checked against the autotuned plan)", "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas x{world}", "widths": dag.meta["widths"]},
-        "mac_check_passed": bool(ok_f and ok_p and ok_e),
+        "mac_check_passed": bool(ok_f and ok_p and ok_pg and ok_e),
         "per_layer": {"value": per_layer_value, "ms_per_step": tot_p / steps,
-                      "speedup_of_scheduled_form": tot_p / tot_f},
+                      "speedup_of_scheduled_form": tot_p / tot_f,
+                      "note": "one launch per layer and gate class, stream-ordered, no graph"},
+        "per_layer_graphed": {"value": world * nm * steps / (tot_pg * 1e-3), "ms_per_step": tot_pg / steps,
+                              "speedup_of_scheduled_form": tot_pg / tot_f,
+                              "note": "the same launches captured once as a CUDA graph and replayed"},
         "scheduler": sched,
         "e2e": {"value": world * nm * e2e_n / e2e_dt, "unit": "Beaver mults/s",
                 "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
@@ -475,46 +479,95 @@ def run_ours(args, rank, world, local_rank):
     }
     if cpu:
         line["cpu_baseline"] = cpu
+    if extras:
+        line["configs"] = extras
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------- reference
 
+def all_configs(args):
+    """The other configurations of the workload, each measured in this run and
+    attached to the bench line (every figure device-timed with CUDA events):
+      c1: 2 parties, p61, 2^16 Beaver products with their MAC check (and the
+          batch kernel at 2^26 against HBM);
+      c3: p127, 3 parties, 2^24 products + 16,384 inner products of length
+          1024, one check, against HBM and the measured integer peaks;
+      c4: the 2048^3 secret-shared matrix product, tensor and CUDA-core paths;
+      c5: serving (1,500 requests, four modes, burst capacity, binding budget);
+      linear_layer: the paper's LinearLayer, 8192 x 8192, 2 parties,
+          p = 2^32-5, 32-row tiles."""
+    import torch
+    from paper_2512_11112_b300 import spdz as S
+    hbm, _ = peaks()
+    out = {}
+
+    def c1():
+        sw = batch_sweep(args, "p61", hbm, lgs=(16, 26))
+        return {"workload": "2^16 Beaver mults, n=2, p61, with one MAC check (L2-resident: launch-bound), and the "
+                            "batch kernel at 2^26 (inputs larger than L2)",
+                "mults_per_s_with_check": 2**16 / (sw["2^16"]["with_check_us"] * 1e-6), "points": sw}
+
+    def linear():
+        from paper_2512_11112_b300 import shares as SH
+        ms, cms, ok = linear_layer_case(torch, S, SH, S.SPDZ_F32, 2, 8192, 8192, 32, 3, 10)
+        by = 4 * 2 * 8192 * 8192 * 4
+        return {"workload": "LinearLayer y = Wx + b, W 8192x8192, n=2, p=2^32-5, 32-row tiles, fresh triples each call",
+                "ms": ms, "mac_check_ms": cms, "mac_check_passed": ok, "algorithmic_bytes": by,
+                "achieved_gbs": by / (ms * 1e-3) / 1e9, "frac_of_hbm": by / (ms * 1e-3) / 1e9 / hbm,
+                "paper_runtime_s": PAPER_LINEAR_S}
+
+    ipk = None
+    for key, fn in (("int_peaks", lambda: int_peaks(torch, S)), ("c1_batch_n2_p61", c1),
+                    ("c3_heavy_p127", lambda: heavy_metrics(args, ipk)), ("c4_matmul_2048", lambda: matmul_metrics(args)),
+                    ("c5_serving", lambda: serve_metrics(args.extras_requests)), ("linear_layer_8192", linear)):
+        t0 = time.time()
+        try:
+            out[key] = fn()
+        except Exception as e:   # noqa: BLE001
+            out[key] = {"error": repr(e)[:400]}
+        out[key]["bench_wall_s"] = round(time.time() - t0, 1)
+        if key == "int_peaks" and "error" not in out[key]:
+            ipk = out[key]
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args, rank, world):
-    """The reference arm: the CPU oracle as it stands, each step one bounded
-    sample of the benchmark circuit (its first layers, up to 2^18 gates)."""
+    """The reference arm: the CPU oracle as it stands, each step one full
+    evaluation of the benchmark circuit by its layer-parallel loop on every
+    host core (the same workload, metric and unit as the GPU arm)."""
     if rank != 0:
         return
     import oracle as O
     dag = W.layered_dag(seed=2)
-    offs = dag.layer_offsets
-    L = int(np.searchsorted(offs, 2**18, side="right") - 1)
-    L = max(1, L)
-    G = int(offs[L])
-    sub = W.Dag(p=dag.p, n_inputs=dag.n_inputs, ops=dag.ops[:G], in0=dag.in0[:G], in1=dag.in1[:G],
-                kconst=dag.kconst[:G], layer_offsets=offs[:L + 1], seed=dag.seed)
     p, n = dag.p, N_PARTIES
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
     alpha, ash = O.deal_alpha(p, n, 2)
-    iv, im, _ = O.deal_shared(p, n, 2, O.K_INPUT, INPUT_SUB, 0, sub.n_inputs, alpha)
-    tri = O.deal_triples(p, n, 2, 0, sub.n_mul, alpha)
+    iv, im, _ = O.deal_shared(p, n, 2, O.K_INPUT, INPUT_SUB, 0, dag.n_inputs, alpha)
+    tri = O.deal_triples(p, n, 2, 0, dag.n_mul, alpha)
     times = []
     for k in range(args.warmup + args.steps):
-        wv, wm = O.zeros(p, n, sub.n_wires), O.zeros(p, n, sub.n_wires)
-        wv[:, :sub.n_inputs], wm[:, :sub.n_inputs] = iv, im
+        wv, wm = O.zeros(p, n, dag.n_wires), O.zeros(p, n, dag.n_wires)
+        wv[:, :dag.n_inputs], wm[:, :dag.n_inputs] = iv, im
         t0 = time.perf_counter()
-        O.dag_eval(p, sub, wv, wm, tri, ash)
+        O.dag_eval_layers(p, dag, wv, wm, tri, ash)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             times.append(dt)
     tot = sum(times)
-    value = sub.n_mul * len(times) / tot
-    sample = f"first {L} layers of the benchmark circuit ({G} gates, {sub.n_mul} Beaver mults, 3 parties)"
+    value = dag.n_mul * len(times) / tot
+    sample = (f"one full evaluation of the benchmark circuit per step ({dag.n_gates} gates, {dag.n_mul} Beaver "
+              f"mults, 3 parties) by the oracle's layer-parallel loop on {cores} threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Beaver mults/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-            "data": "synthetic", "config": {"workload": "layered circuit (sample), n=3, p=2^61-1",
-                                            "sample": sample},
-            "cpu_baseline": {"value": value, "unit": "Beaver mults/s", "cores": 1, "kind": "oracle",
+            "data": "synthetic", "config": {"workload": "layered circuit: 2^20 gates, 32 layers, widths log-uniform "
+                                                        "[1k,64k], 60% mul / 15% add / 15% sub / 10% const-mul, n=3, "
+                                                        "p=2^61-1", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "Beaver mults/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "Beaver mults/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -550,60 +603,82 @@ def calibrate_both_fields(torch, S, SH, reps=2, epochs=400):
     return ctxs[W.P61], loss
 
 
-def run_serve(args):
-    """The serving workload: 10,000 circuit requests with Poisson arrivals,
-    gate counts log-uniform in [2^10, 2^22], depths uniform in [4, 64], p61 or
-    p127; a 100 GB budget of shares and triples.  Requests draw their circuit
-    from 64 shapes of that distribution (each request keeps its own seed and
-    arrival time).  The arrival rate puts the offered load at 0.7 of the
-    sequential form's measured capacity."""
+def serve_metrics(count, nshape=64, tight_budget_gb=4):
+    """The serving workload: circuit requests with Poisson arrivals, gate
+    counts log-uniform in [2^10, 2^22], depths uniform in [4, 64], p61 or
+    p127; requests draw their circuit from `nshape` registered shapes of that
+    distribution (each request keeps its own seed and arrival time).  The
+    arrival rate puts the offered load at 0.7 of the sequential form's
+    measured capacity; every mode serves the same trace under a 100 GB
+    budget.  Beside it: each mode's capacity on a burst of 200 requests, and
+    the learned mode under a budget that binds (queueing counted in its
+    latency)."""
     import torch
     from paper_2512_11112_b300 import shares as SH
     from paper_2512_11112_b300 import spdz as S
-    count, nshape = args.serve_requests, 64
     base = W.serving_requests(seed=5, count=count, rate_per_s=1.0)
     shapes = [W.request_dag(r) for r in base[:nshape]]
     fields = [S.SPDZ_F61 if r.p == W.P61 else S.SPDZ_F127 for r in base[:nshape]]
     mean_gates = float(np.mean([shapes[k % nshape].n_gates for k in range(count)]))
     model_ctx, loss = calibrate_both_fields(torch, S, SH)
-    budget = 100 << 30
 
-    def trace(rate, n, burst=False):
+    def trace(cids, rate, n, burst=False):
         t = [0.0] * n if burst else [r.arrival_s / rate for r in base[:n]]   # base was drawn at rate 1
         return [(cids[k % nshape], fields[k % nshape], base[k].seed, t[k], None, None) for k in range(n)]
 
-    srv = S.spdz_serve_create(N_PARTIES, budget, 512, S.SPDZ_SERVE_BATCHED, None, 0, 4096)
-    # deployment: the circuits are registered (uploaded into the arena) once
-    cids = [S.spdz_serve_register(srv, d, f) for d, f in zip(shapes, fields)]
-
-    def run(mode, items):
+    def run(srv, mode, items):
         S.spdz_serve_set_mode(srv, mode, model_ctx if mode == S.SPDZ_SERVE_LEARNED else None, 4096)
         res, st = S.spdz_serve_run(srv, items)
-        ok = all(r.passed == 1 for r in res)
+        wait = sorted(1e3 * (r.latency_s - r.online_s) for r in res)
         return {"p50_ms": st.p50_s * 1e3, "p99_ms": st.p99_s * 1e3, "mean_ms": st.mean_s * 1e3,
                 "gates_per_s": st.gates_per_s, "wall_s": st.wall_s, "ticks": st.ticks,
                 "cluster_requests": st.cluster_requests, "dealer_s": st.dealer_s,
-                "peak_gb": st.peak_bytes / 2**30, "max_active": st.max_active, "all_checks_passed": ok,
+                "peak_gb": st.peak_bytes / 2**30, "max_active": st.max_active,
+                "all_checks_passed": all(r.passed == 1 for r in res),
+                "admission_wait_p99_ms": wait[min(len(wait) - 1, int(0.99 * (len(wait) - 1) + 0.5))] if wait else 0.0,
                 "host_s": {"admit": st.host_admit_s, "tick": st.host_tick_s, "complete": st.host_complete_s,
                            "idle": st.host_idle_s, "ring_wait": st.host_ring_wait_s}}
 
-    # capacity of the sequential form on a burst of requests
-    cap = run(S.SPDZ_SERVE_SEQUENTIAL, trace(1.0, min(200, count), burst=True))
-    rate = 0.7 * cap["gates_per_s"] / mean_gates
-    items = trace(rate, count)
     modes = {"sequential": S.SPDZ_SERVE_SEQUENTIAL, "batched": S.SPDZ_SERVE_BATCHED,
              "heuristic": S.SPDZ_SERVE_HEURISTIC, "learned": S.SPDZ_SERVE_LEARNED}
-    out = {name: run(m, items) for name, m in modes.items()}
-    S.spdz_serve_destroy(srv)
+    srv = S.spdz_serve_create(N_PARTIES, 100 << 30, 512, S.SPDZ_SERVE_BATCHED, None, 0, 4096)
+    try:
+        # deployment: the circuits are registered (uploaded into the arena) once
+        cids = [S.spdz_serve_register(srv, d, f) for d, f in zip(shapes, fields)]
+        burst = trace(cids, 1.0, min(200, count), burst=True)
+        cap = {name: run(srv, m, burst) for name, m in modes.items()}
+        rate = 0.7 * cap["sequential"]["gates_per_s"] / mean_gates
+        items = trace(cids, rate, count)
+        out = {name: run(srv, m, items) for name, m in modes.items()}
+    finally:
+        S.spdz_serve_destroy(srv)
+    tight = None
+    srv = S.spdz_serve_create(N_PARTIES, tight_budget_gb << 30, 512, S.SPDZ_SERVE_LEARNED, model_ctx, 0, 4096)
+    try:
+        cids = [S.spdz_serve_register(srv, d, f) for d, f in zip(shapes, fields)]
+        tight = run(srv, S.SPDZ_SERVE_LEARNED, trace(cids, rate, count))
+        tight["budget_gb"] = tight_budget_gb
+    except Exception as e:   # noqa: BLE001
+        tight = {"error": repr(e)[:300]}
+    finally:
+        S.spdz_serve_destroy(srv)
     S.spdz_ctx_destroy(model_ctx)
+    torch.cuda.empty_cache()
+    return {"workload": f"{count} circuit requests, Poisson arrivals at {rate:.1f}/s (0.7 x sequential capacity), "
+                        f"gates log-uniform [2^10, 2^22], depth [4, 64], p61/p127, n=3, budget 100 GB, {nshape} "
+                        f"registered circuit shapes", "mean_gates": mean_gates, "arrival_rate_per_s": rate,
+            "cost_model_loss": loss, "modes": out,
+            "capacity_burst_200": {k: {"gates_per_s": v["gates_per_s"], "wall_s": v["wall_s"],
+                                       "cluster_requests": v["cluster_requests"]} for k, v in cap.items()},
+            "learned_under_binding_budget": tight}
+
+
+def run_serve(args):
+    m = serve_metrics(args.serve_requests)
     line = {"metric": "served p99 latency and gates/s, continuous batching + learned scheduler vs sequential",
-            "value": out["learned"]["p99_ms"], "unit": "ms (p99 latency)", "higher_is_better": False,
-            "n_gpus": 1, "data": "synthetic", "dtype": "u64",
-            "config": {"workload": f"{count} circuit requests, Poisson arrivals at {rate:.1f}/s (0.7 x sequential "
-                                   f"capacity), gates log-uniform [2^10, 2^22], depth [4, 64], p61/p127, n=3, "
-                                   f"budget 100 GB, {nshape} circuit shapes", "mean_gates": mean_gates,
-                       "sequential_capacity_gates_per_s": cap["gates_per_s"], "cost_model_loss": loss},
-            "modes": out}
+            "value": m["modes"]["learned"]["p99_ms"], "unit": "ms (p99 latency)", "higher_is_better": False,
+            "n_gpus": 1, "data": "synthetic", "dtype": "u64", "config": {"workload": m["workload"]}}
+    line.update(m)
     print(json.dumps(line), flush=True)
 
 
@@ -611,11 +686,15 @@ def _events(torch):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def run_matmul(args):
+BF16_FLOPS_PER_LAUNCH_2048 = 2 * 2048 * 2048 * (2 * 2048) * 64   # digit-pair products of one share matrix
+
+
+def matmul_metrics(args, reps=3):
     """Secret-shared matrix product X[2048x2048] * Y[2048x2048], 3 parties,
-    p61, with a Beaver matrix triple: CUDA-core path (and tensor path when
-    available).  The unit of work is a modular multiply-accumulate: 12
-    modular GEMMs of 2048^3 (4 per party) per product."""
+    p61, with a Beaver matrix triple: CUDA-core path and tensor path.  The
+    unit of work is a modular multiply-accumulate: 12 modular GEMMs of 2048^3
+    (4 per party) per product; the tensor path also in bf16 digit-pair FLOPs
+    (2n launches of 2 m n (2k) 64) against the measured bf16 burst peak."""
     import torch
     from paper_2512_11112_b300 import shares as SH
     from paper_2512_11112_b300 import spdz as S
@@ -630,10 +709,15 @@ def run_matmul(args):
     A, B, Cm = (SH.alloc(f, n, dim * dim) for _ in range(3))
     macs = 4 * n * dim ** 3
     out = {}
+    try:
+        bf16 = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        bf16 = 1800.0
+    warm = min(args.warmup, 2)
     for name, path in (("cuda_core", S.SPDZ_MATMUL_CUDA_CORE), ("tensor", S.SPDZ_MATMUL_TENSOR)):
         ts = []
         try:
-            for rep in range(args.warmup + 3):
+            for rep in range(warm + reps):
                 S.spdz_deal_matrix_triple(ctx, 4, rep, dim, dim, dim, ash, A.buf(), B.buf(), Cm.buf())
                 S.spdz_load_matrix_preproc(ctx, A.buf(), B.buf(), Cm.buf(), dim, dim, dim)
                 torch.cuda.synchronize()
@@ -643,18 +727,32 @@ def run_matmul(args):
                 e1.record()
                 torch.cuda.synchronize()
                 ok = S.spdz_mac_check(ctx)
-                if rep >= args.warmup:
+                if rep >= warm:
                     ts.append(e0.elapsed_time(e1))
             ms = statistics.median(ts)
             out[name] = {"ms": ms, "modular_macs_per_s": macs / (ms * 1e-3), "mac_check_passed": ok}
+            if name == "tensor":
+                tf = 2 * n * BF16_FLOPS_PER_LAUNCH_2048 / (ms * 1e-3) / 1e12
+                out[name].update({"bf16_digit_pair_tflops": round(tf, 1), "bf16_burst_peak_tflops": bf16,
+                                  "frac_of_bf16_burst": round(tf / bf16, 4)})
         except Exception as e:   # noqa: BLE001
             out[name] = {"unavailable": str(e)}
     S.spdz_ctx_destroy(ctx)
+    del X, Y, Z, A, B, Cm
+    torch.cuda.empty_cache()
+    if "ms" in out.get("tensor", {}) and "ms" in out.get("cuda_core", {}):
+        out["tensor_speedup"] = out["cuda_core"]["ms"] / out["tensor"]["ms"]
+    out["modular_macs"] = macs
+    return out
+
+
+def run_matmul(args):
+    out = matmul_metrics(args)
     line = {"metric": "secret-shared 2048^3 matrix product time (Beaver matrix triple, 3 parties, p=2^61-1)",
-            "value": min(v.get("ms", 1e9) for v in out.values()), "unit": "ms", "higher_is_better": False,
-            "n_gpus": 1, "dtype": "u64", "data": "synthetic",
+            "value": min(v.get("ms", 1e9) for v in out.values() if isinstance(v, dict)), "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "u64", "data": "synthetic",
             "config": {"workload": "X, Y 2048x2048 uniform, 3 parties, p61, dealer matrix triple",
-                       "modular_macs": macs}, "paths": out}
+                       "modular_macs": out["modular_macs"]}, "paths": out}
     print(json.dumps(line), flush=True)
 
 
@@ -773,9 +871,32 @@ def linear_cpu_baseline(rows_sample=512, dout=8192, din=8192, R=32, n=2):
                       f"p=2^32-5), {dt:.2f} s, scaled by {dout // rows_sample} to the whole layer"}
 
 
-def run_heavy(args):
+def read_pipes():
+    """Per-unit instruction counts of the p127 kernels from the committed ncu
+    capture (thread-level: one unit per thread)."""
+    try:
+        return json.load(open(os.path.join(ROOT, "profiles", "pipes_p127.json")))
+    except Exception:
+        return {}
+
+
+def int_peaks(torch, S):
+    """Measured integer issue rates (thread-level instructions per second):
+    32-bit multiply-adds (the multiply pipe) and add/xor pairs (every issue
+    slot)."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    scr = torch.zeros(8 * 256 * sms, dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    names = ("imad_lo", "imad_wide", "imad_hi_add", "alu_add_xor")
+    return {nm: max(S.spdz_int_peak(k, 20000, st, scr) for _ in range(2)) for k, nm in enumerate(names)}
+
+
+def heavy_metrics(args, ipk=None):
     """p127, 3 parties: 2^24 Beaver multiplications, then 16,384 inner products
-    of length 1024, one MAC check over all 2^26 opened values."""
+    of length 1024, one MAC check over all 2^26 opened values.  Each kernel is
+    set against the slower of its HBM bound and its integer bounds (multiply
+    pipe and issue), from its instruction counts per unit (profiles/) and the
+    measured integer peaks."""
     import torch
     from paper_2512_11112_b300 import shares as SH
     from paper_2512_11112_b300 import spdz as S
@@ -789,7 +910,8 @@ def run_heavy(args):
     zi = SH.alloc(f, n, P)
     tri = [SH.alloc(f, n, 2 * N) for _ in range(3)]
     res = {"mul": [], "ip": [], "check": []}
-    for rep in range(args.warmup + 3):
+    oks = []
+    for rep in range(min(args.warmup, 3) + 3):
         S.spdz_deal_triples(ctx, 3, rep * 2 * N, 2 * N, ash, *[t.buf() for t in tri])
         S.spdz_load_preproc(ctx, ash, *[t.buf() for t in tri], 2 * N)
         torch.cuda.synchronize()
@@ -801,26 +923,51 @@ def run_heavy(args):
         S.spdz_innerprod_batch(ctx, x.buf(), y.buf(), zi.buf(), P, L)
         ev[1][1].record()
         ev[2][0].record()
-        ok = S.spdz_mac_check(ctx)
+        oks.append(S.spdz_mac_check(ctx))
         ev[2][1].record()
         torch.cuda.synchronize()
-        if rep >= args.warmup:
+        if rep >= min(args.warmup, 3):
             for k, key in enumerate(("mul", "ip", "check")):
                 res[key].append(ev[k][0].elapsed_time(ev[k][1]))
     S.spdz_ctx_destroy(ctx)
+    del x, y, z, zi, tri
+    torch.cuda.empty_cache()
     hbm, src = peaks()
     mul_ms, ip_ms = statistics.median(res["mul"]), statistics.median(res["ip"])
+    pipes = read_pipes()
+    roof = {}
+    for name, kern, ms, units, per in (("mul", "k_mul<F127,3,1>", mul_ms, N, 576),
+                                       ("innerprod", "k_innerprod<F127,3>", ip_ms, P * L, 480)):
+        t_hbm = per * units / (hbm * 1e9)
+        d = {"kernel": kern, "unit_bytes": per, "achieved_gbs": round(per * units / (ms * 1e-3) / 1e9, 1),
+             "hbm_peak_gbs": hbm, "hbm_frac": round(t_hbm / (ms * 1e-3), 4), "hbm_bound_ms": round(t_hbm * 1e3, 4)}
+        pc = pipes.get(kern)
+        if pc and ipk:
+            t_fma = units * pc["fmaheavy_per_unit"] / ipk["imad_lo"]
+            t_issue = units * pc["inst_per_unit"] / ipk["alu_add_xor"]
+            bound = max(("hbm", t_hbm), ("multiply pipe", t_fma), ("issue", t_issue), key=lambda kv: kv[1])
+            d.update({"multiply_pipe_bound_ms": round(t_fma * 1e3, 4), "issue_bound_ms": round(t_issue * 1e3, 4),
+                      "bound": bound[0], "frac": round(bound[1] / (ms * 1e-3), 4),
+                      "per_unit_instructions": pc})
+        else:
+            d.update({"bound": "hbm", "frac": d["hbm_frac"]})
+        roof[name] = d
+    return {"mul_ms": mul_ms, "mults_per_s": N / (mul_ms * 1e-3), "innerprod_ms": ip_ms,
+            "innerprod_terms_per_s": P * L / (ip_ms * 1e-3), "mac_check_ms": statistics.median(res["check"]),
+            "mac_check_passed": all(oks), "roofline": roof, "peak_source": src}
+
+
+def run_heavy(args):
+    import torch
+    from paper_2512_11112_b300 import spdz as S
+    ipk = int_peaks(torch, S)
+    h = heavy_metrics(args, ipk)
     line = {"metric": "Beaver mults/s at n=3, p=2^127-1 (2^24 products) and inner-product terms/s",
-            "value": N / (mul_ms * 1e-3), "unit": "Beaver mults/s", "higher_is_better": True, "n_gpus": 1,
+            "value": h["mults_per_s"], "unit": "Beaver mults/s", "higher_is_better": True, "n_gpus": 1,
             "dtype": "u128", "data": "synthetic",
             "config": {"workload": "2^24 Beaver mults + 16384 inner products of length 1024, n=3, p127, one MAC "
-                                   "check over 2^26 opened values"},
-            "mul_ms": mul_ms, "innerprod_ms": ip_ms, "innerprod_terms_per_s": P * L / (ip_ms * 1e-3),
-            "mac_check_ms": statistics.median(res["check"]), "mac_check_passed": ok,
-            "roofline": {"mul": {"bytes_per_mult": 576, "achieved_gbs": 576 * N / (mul_ms * 1e-3) / 1e9, "peak": hbm,
-                                 "frac": 576 * N / (mul_ms * 1e-3) / 1e9 / hbm},
-                         "innerprod": {"bytes_per_term": 480, "achieved_gbs": 480 * P * L / (ip_ms * 1e-3) / 1e9,
-                                       "peak": hbm, "frac": 480 * P * L / (ip_ms * 1e-3) / 1e9 / hbm}}}
+                                   "check over 2^26 opened values"}, "int_peaks": ipk}
+    line.update(h)
     print(json.dumps(line), flush=True)
 
 
@@ -979,7 +1126,7 @@ def innerprod_roofline(args, hbm):
         S.spdz_ctx_destroy(ctx)
 
 
-def batch_sweep(args, field, hbm):
+def batch_sweep(args, field, hbm, lgs=(16, 18, 20, 22, 24, 26)):
     import torch
     from paper_2512_11112_b300 import shares as SH
     from paper_2512_11112_b300 import spdz as S
@@ -988,13 +1135,13 @@ def batch_sweep(args, field, hbm):
     ctx = S.spdz_ctx_create(n, f, torch.cuda.current_stream().cuda_stream)
     ash = SH.zeros(f, n)
     S.spdz_deal_alpha(ctx, 1, ash)
-    NMAX = 2**26
+    NMAX = 2**max(lgs)
     x, y, z = (SH.alloc(f, n, NMAX) for _ in range(3))
     S.spdz_deal_shared(ctx, 1, S.SPDZ_KIND_INPUT, 0, 0, NMAX, ash, None, x.buf())
     S.spdz_deal_shared(ctx, 1, S.SPDZ_KIND_INPUT, 1, 0, NMAX, ash, None, y.buf())
     tri = [SH.alloc(f, n, NMAX) for _ in range(3)]
     sweep = {}
-    for lg in (16, 18, 20, 22, 24, 26):
+    for lg in lgs:
         N = 2**lg
         ts_mul, ts_all = [], []
         for rep in range(args.warmup + 5):
@@ -1093,6 +1240,9 @@ def main():
                     help="circuit: the benchmark circuit (default); serve, matmul, heavy, batch: the other "
                          "workloads, one JSON line each")
     ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="circuit workload only (skip the other configurations attached to the line)")
+    ap.add_argument("--extras-requests", type=int, default=1500, help="serving requests of the attached run")
     ap.add_argument("--profile", default=None, choices=["dag", "tagged", "beaver", "beaver127", "heavy_small", "matmul", "linear"],
                     help="small run of one kernel for an ncu capture (prints nothing)")
     args = ap.parse_args()

@@ -291,6 +291,25 @@ int spdz_dag_destroy(spdz_dag *dag);
  * SPDZ_ERR_TIMEOUT: a device barrier wait hit its bound (results invalid). */
 int spdz_run_dag(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan *plan, const spdz_buf *wires,
                  spdz_stats *stats);
+/* The same run from host buffers, for callers whose shares live in host
+ * memory (p = 2^61-1 and p = 2^127-1, whose host and device element formats
+ * agree; SPDZ_ERR_ARG for p = 2^32-5).  Enqueues, without waiting:
+ *   - the run's n_mul triples, host arrays tri_host[0..5] = a, gamma(a), b,
+ *     gamma(b), c, gamma(c), each [n][n_mul] (party rows of n_mul elements),
+ *     copied into the registered pool at the slots the run consumes, on a
+ *     copy stream of the context that waits only for the work enqueued before
+ *     the pool was registered (so the next call's copy overlaps this run);
+ *   - the input shares in_val_host / in_mac_host ([n][n_inputs] each) into
+ *     wires, then the run (as spdz_run_dag with stats == NULL), on the
+ *     context's stream;
+ *   - wires [out_first, out_first + out_count) of every party (values and
+ *     MACs) back to out_val_host / out_mac_host ([n][out_count] each).
+ * Every host buffer must stay valid and unchanged until the stream has
+ * passed this run (spdz_check_result synchronises); copies are asynchronous
+ * only from and to page-locked host memory.  Errors as spdz_run_dag. */
+int spdz_run_dag_host(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan *plan, const spdz_buf *wires,
+                      const void *in_val_host, const void *in_mac_host, const void *const *tri_host, int64_t out_first,
+                      int64_t out_count, void *out_val_host, void *out_mac_host);
 /* Verdict and sigma (host, [n] elements, may be NULL) of the last completed
  * check on the context; synchronises the stream. */
 int spdz_check_result(spdz_ctx *ctx, int *passed, void *sigma_host);
@@ -504,7 +523,7 @@ typedef struct {
     double wall_s, gates_per_s, p50_s, p99_s, mean_s;
     int64_t requests, gates, ticks, cluster_requests;
     double dealer_s;            /* device time spent dealing preprocessing (offline) */
-    int64_t peak_bytes;         /* peak arena use (registered circuits included) */
+    int64_t peak_bytes;         /* peak arena use of the session (registered circuits included) */
     int32_t max_active;
     /* host time of the serving thread by phase (tracing) */
     double host_admit_s, host_tick_s, host_complete_s, host_idle_s, host_ring_wait_s;

@@ -225,6 +225,13 @@ struct spdz_ctx {
     void *sched = nullptr;               // scheduler state (sched.cu)
     void *mat = nullptr;                 // matrix-product state (matmul.cu)
     void *ll = nullptr;                  // linear-layer state (linear_layer.cu)
+    // host-buffer circuit runs: a copy stream for the triples, the event of
+    // the last pool registration (copies into the pool wait for it) and a
+    // ring of copy-done events
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t pool_ev = nullptr;
+    cudaEvent_t copy_ev[4] = {};
+    int copy_k = 0;
 };
 
 namespace spdz {

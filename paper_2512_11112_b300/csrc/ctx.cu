@@ -160,6 +160,13 @@ int spdz_ctx_destroy(spdz_ctx *ctx) {
     sched_destroy(ctx);
     mat_destroy(ctx);
     ll_destroy(ctx);
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
+    if (ctx->pool_ev) cudaEventDestroy(ctx->pool_ev);
+    for (auto e : ctx->copy_ev)
+        if (e) cudaEventDestroy(e);
     delete ctx;
     return SPDZ_OK;
 }
@@ -243,6 +250,12 @@ int spdz_load_preproc(spdz_ctx *ctx, const void *alpha_shares_dev, const spdz_bu
     SPDZ_FIELD_SWITCH(ctx->field,
                       (k_load_alpha<F><<<1, 32, 0, ctx->stream>>>(ctx->ds, (const typename F::T *)alpha_shares_dev, ctx->n)));
     if ((rc = check_launch(ctx, "load alpha"))) return rc;
+    // host-buffer runs copy triples into this pool on their own stream, after
+    // everything enqueued before the registration (which may still use the
+    // same memory)
+    if (!ctx->pool_ev && (rc = check_cuda(ctx, cudaEventCreateWithFlags(&ctx->pool_ev, cudaEventDisableTiming), "pool event")))
+        return rc;
+    if ((rc = check_cuda(ctx, cudaEventRecord(ctx->pool_ev, ctx->stream), "pool event"))) return rc;
     ctx->alpha_loaded = true;
     return SPDZ_OK;
 }

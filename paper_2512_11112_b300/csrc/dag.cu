@@ -508,6 +508,79 @@ int spdz_run_dag(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan *plan_in, const s
     return SPDZ_OK;
 }
 
+int spdz_run_dag_host(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan *plan, const spdz_buf *wires,
+                      const void *in_val_host, const void *in_mac_host, const void *const *tri_host, int64_t out_first,
+                      int64_t out_count, void *out_val_host, void *out_mac_host) {
+    if (!ctx || !dag || !wires) return set_err(ctx, SPDZ_ERR_ARG, "run_dag_host: null argument");
+    if (ctx->field == SPDZ_F32)
+        return set_err(ctx, SPDZ_ERR_ARG, "run_dag_host: host and device element formats differ for p = 2^32-5");
+    const int n = ctx->n;
+    const int64_t nin = dag->n_inputs, nm = dag->n_mul, W = dag->n_inputs + dag->n_gates;
+    if (nin > 0 && (!in_val_host || !in_mac_host)) return set_err(ctx, SPDZ_ERR_ARG, "run_dag_host: no input shares");
+    if (nm > 0) {
+        if (!tri_host) return set_err(ctx, SPDZ_ERR_ARG, "run_dag_host: no triples");
+        for (int k = 0; k < 6; ++k)
+            if (!tri_host[k]) return set_err(ctx, SPDZ_ERR_ARG, "run_dag_host: triple array %d is null", k);
+    }
+    if (out_first < 0 || out_count < 0 || out_first + out_count > W ||
+        (out_count > 0 && (!out_val_host || !out_mac_host)))
+        return set_err(ctx, SPDZ_ERR_ARG, "run_dag_host: bad output range");
+    int rc = validate_buf(ctx, wires, W, "run_dag_host.wires");
+    if (rc) return rc;
+    if (!ctx->alpha_loaded || !ctx->pool_ev) return set_err(ctx, SPDZ_ERR_STATE, "run_dag_host: preprocessing not loaded");
+    if (ctx->opened != 0) return set_err(ctx, SPDZ_ERR_STATE, "run_dag_host: values opened since the last check");
+    if (ctx->tri_total - ctx->tri_cursor < nm)
+        return set_err(ctx, SPDZ_ERR_TRIPLES, "run_dag_host: need %lld triples, %lld left", (long long)nm,
+                       (long long)(ctx->tri_total - ctx->tri_cursor));
+    const size_t eb = elem_bytes(ctx->field);
+    if (!ctx->copy_stream) {
+        if ((rc = check_cuda(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking), "copy stream")))
+            return rc;
+        for (auto &e : ctx->copy_ev)
+            if ((rc = check_cuda(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "copy event"))) return rc;
+    }
+    // the run's triples into the pool slots it consumes, on the copy stream
+    // (so the next call's copy overlaps this run)
+    if (nm > 0) {
+        if ((rc = check_cuda(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->pool_ev, 0), "copy wait"))) return rc;
+        const spdz_buf *tb[3] = {&ctx->ta, &ctx->tb, &ctx->tc};
+        for (int k = 0; k < 6; ++k) {
+            const spdz_buf &b = *tb[k / 2];
+            char *dst = (char *)(k % 2 == 0 ? b.val : b.mac) + (size_t)ctx->tri_cursor * eb;
+            if ((rc = check_cuda(ctx, cudaMemcpy2DAsync(dst, (size_t)b.stride * eb, tri_host[k], (size_t)nm * eb,
+                                                         (size_t)nm * eb, (size_t)n, cudaMemcpyHostToDevice,
+                                                         ctx->copy_stream), "triple copy")))
+                return rc;
+        }
+    }
+    cudaEvent_t ev = ctx->copy_ev[ctx->copy_k];
+    ctx->copy_k = (ctx->copy_k + 1) % 4;
+    if ((rc = check_cuda(ctx, cudaEventRecord(ev, ctx->copy_stream), "copy event"))) return rc;
+    // the inputs, on the run's stream (after any earlier run that reads them)
+    if (nin > 0) {
+        if ((rc = check_cuda(ctx, cudaMemcpy2DAsync(wires->val, (size_t)wires->stride * eb, in_val_host, (size_t)nin * eb,
+                                                     (size_t)nin * eb, (size_t)n, cudaMemcpyHostToDevice, ctx->stream),
+                             "input copy")) ||
+            (rc = check_cuda(ctx, cudaMemcpy2DAsync(wires->mac, (size_t)wires->stride * eb, in_mac_host, (size_t)nin * eb,
+                                                     (size_t)nin * eb, (size_t)n, cudaMemcpyHostToDevice, ctx->stream),
+                             "input copy")))
+            return rc;
+    }
+    if ((rc = check_cuda(ctx, cudaStreamWaitEvent(ctx->stream, ev, 0), "copy wait"))) return rc;
+    if ((rc = spdz_run_dag(ctx, dag, plan, wires, nullptr))) return rc;
+    if (out_count > 0) {
+        const size_t off = (size_t)out_first * eb;
+        if ((rc = check_cuda(ctx, cudaMemcpy2DAsync(out_val_host, (size_t)out_count * eb, (const char *)wires->val + off,
+                                                     (size_t)wires->stride * eb, (size_t)out_count * eb, (size_t)n,
+                                                     cudaMemcpyDeviceToHost, ctx->stream), "output copy")) ||
+            (rc = check_cuda(ctx, cudaMemcpy2DAsync(out_mac_host, (size_t)out_count * eb, (const char *)wires->mac + off,
+                                                     (size_t)wires->stride * eb, (size_t)out_count * eb, (size_t)n,
+                                                     cudaMemcpyDeviceToHost, ctx->stream), "output copy")))
+            return rc;
+    }
+    return SPDZ_OK;
+}
+
 int spdz_check_result(spdz_ctx *ctx, int *passed, void *sigma_host) {
     if (!ctx || !passed) return set_err(ctx, SPDZ_ERR_ARG, "check_result: null argument");
     int rc;

@@ -193,6 +193,7 @@ class Arena {
     }
     char *ptr(size_t off) const { return (char *)base_ + off; }
     size_t peak() const { return peak_; }
+    void reset_peak() { peak_ = used_; }
     size_t size() const { return size_; }
 
   private:
@@ -944,6 +945,7 @@ int spdz_serve_start(spdz_server *s) {
     s->st_max_active = 0;
     s->h_admit = s->h_tick = s->h_done = s->h_idle = s->h_ringwait = 0;
     s->cluster_backlog_us = 0;
+    s->arena.reset_peak();
     for (auto &kv : s->circuits) kv.second->users = 0;
     s->worker = std::thread([s] { s->loop(); });
     return SPDZ_OK;

@@ -142,6 +142,7 @@ _SIGS = {
     "spdz_mlp_loss_grad": [_vp, _vp, _vp, _i64, _vp, _vp],
     "spdz_mlp_train": [_vp, _vp, _vp, _i64, C.c_int32, C.c_int32, C.c_float, _vp],
     "spdz_mlp_adam_step": [_vp, _vp, C.c_float],
+    "spdz_run_dag_host": [_vp, _vp, C.POINTER(spdz_plan), _bufp, _vp, _vp, C.POINTER(_vp), _i64, _i64, _vp, _vp],
     "spdz_int_peak": [_int, _i64, _vp, _vp, C.POINTER(C.c_double)],
     "spdz_sched_num_configs": [C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "spdz_sched_config_plan": [_vp, C.c_int32, C.POINTER(spdz_plan)],
@@ -348,6 +349,16 @@ def spdz_run_dag(ctx, dag, plan_: spdz_plan | None, wires: spdz_buf, want_stats:
     if rc not in (SPDZ_OK, SPDZ_ERR_MAC):
         _chk(ctx, rc)
     return st
+
+
+def spdz_run_dag_host(ctx, dag, plan_: spdz_plan | None, wires: spdz_buf, in_val, in_mac, tri, out_first: int,
+                      out_count: int, out_val, out_mac) -> None:
+    """Host-buffer circuit run (asynchronous): in_val / in_mac, the six triple
+    arrays `tri` and out_val / out_mac are host tensors or arrays (pinned for
+    asynchronous copies) that must outlive the run."""
+    arr = (_vp * 6)(*[ptr(t) for t in tri]) if tri is not None else None
+    _chk(ctx, lib.spdz_run_dag_host(ctx, dag, C.byref(plan_) if plan_ is not None else None, C.byref(wires),
+                                    ptr(in_val), ptr(in_mac), arr, out_first, out_count, ptr(out_val), ptr(out_mac)))
 
 
 def spdz_check_result(ctx, sigma_host: np.ndarray | None = None) -> bool:

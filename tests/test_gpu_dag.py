@@ -348,3 +348,53 @@ def test_invalid_circuit_rejected():
         assert e.value.code == S.SPDZ_ERR_ARG
     finally:
         S.spdz_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("p", [O.P61, O.P127])
+def test_host_buffer_runs_match_oracle(p):
+    """spdz_run_dag_host: three runs in a row whose input shares and triples
+    come from page-locked host memory (the oracle's own dealt shares; the
+    device pool is registered but never dealt, so only the host copies can
+    fill it) and whose last-layer output shares are copied back: every copied
+    share equals the oracle's run, and every run's check passes.  The calls
+    are enqueued back to back, so a run's triple copy overlaps the run
+    before it."""
+    n, seed, runs = 3, 8, 3
+    dag = W.small_dag(seed=8, p=p, n_inputs=300, widths=[500, 64, 1, 900, 33])
+    field = SH.field_of(p)
+    ctx = ctx_for(n, p)
+    try:
+        ash = SH.zeros(field, n)
+        S.spdz_deal_alpha(ctx, seed, ash)
+        wires = SH.alloc(field, n, dag.n_wires)
+        pool = [SH.alloc(field, n, runs * dag.n_mul) for _ in range(3)]
+        S.spdz_load_preproc(ctx, ash, *[t.buf() for t in pool], runs * dag.n_mul)
+        S.spdz_set_check_seed(ctx, 7)
+        h = S.spdz_dag_create(ctx, dag.n_inputs, dag.layer_offsets, dag.ops, dag.in0, dag.in1, dag.kconst)
+        alpha, _ = O.deal_alpha(p, n, seed)
+        iv, im, _ = O.deal_shared(p, n, seed, O.K_INPUT, INPUT_SUB, 0, dag.n_inputs, alpha)
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).pin_memory()  # noqa: E731
+        h_in = [pin(iv), pin(im)]
+        out_lo = dag.n_inputs + int(dag.layer_offsets[-2])
+        cnt = dag.n_wires - out_lo
+        keep, outs = [], []
+        for r in range(runs):
+            t = O.deal_triples(p, n, seed, r * dag.n_mul, dag.n_mul, alpha)
+            h_tri = [pin(a) for a in (t.av, t.am, t.bv, t.bm, t.cv, t.cm)]
+            ov, om = pin(O.zeros(p, n, cnt)), pin(O.zeros(p, n, cnt))
+            keep.append(h_tri)
+            outs.append((ov, om))
+            S.spdz_run_dag_host(ctx, h, S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=1), wires.buf(), h_in[0], h_in[1],
+                                h_tri, out_lo, cnt, ov, om)
+        assert S.spdz_check_result(ctx)
+        for r in range(runs):
+            ev, em, ok, _ = oracle_run(dag, n, seed, run_index=r)
+            assert ok
+            gv = outs[r][0].numpy().view(np.uint64).reshape(ev[:, out_lo:].shape)
+            gm = outs[r][1].numpy().view(np.uint64).reshape(em[:, out_lo:].shape)
+            assert_equal(gv, ev[:, out_lo:], f"host run {r} output values")
+            assert_equal(gm, em[:, out_lo:], f"host run {r} output MACs")
+        assert S.spdz_triples_left(ctx) == 0
+        S.spdz_dag_destroy(h)
+    finally:
+        S.spdz_ctx_destroy(ctx)
