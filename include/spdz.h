@@ -656,6 +656,51 @@ int spdz_load_matvec_preproc(spdz_ctx *ctx, const spdz_buf *A, const spdz_buf *B
 int spdz_linear_layer(spdz_ctx *ctx, const spdz_buf *W, const spdz_buf *x, const spdz_buf *b, const spdz_buf *y,
                       int64_t dout, int64_t din, int64_t tile_rows, void *D_out_dev, void *E_out_dev);
 
+/* ------------------------------------------------------ party per GPU
+ * One party of the online phase whose shares live on its own GPU (one
+ * process and one GPU per party: the paper runs its parties as separate
+ * processes, Sec. IV-A, and names a GPU per party as future work, Sec. V-B).
+ * Only the party's own rows are touched; the exchange between parties (the
+ * open: every party's eps_i, delta_i rows; the check: every sigma_i) is the
+ * caller's, for example an all-gather over NCCL.  A Beaver batch is
+ *   spdz_party_mask -> exchange -> spdz_party_open_sum -> spdz_party_combine
+ * and the batched MAC check of an epoch is spdz_party_sigma on every party,
+ * an exchange of the sigmas, and "pass iff they sum to zero mod p".  The
+ * opened values, their check coefficients and the formulas are those of
+ * spdz_mul_batch / spdz_mac_check (eps_j at epoch index 2j, delta_j at
+ * 2j+1, coefficient key of epoch e under the check seed), so the parties
+ * together compute exactly what one context computes for all of them.
+ * Single-party buffers: spdz_buf with the party's value and MAC rows (stride
+ * unused).  Every call enqueues on the party's stream; spdz_party_sigma
+ * synchronises it.  Errors: SPDZ_ERR_ARG, SPDZ_ERR_ALIGN (an element
+ * pointer not aligned to its element size), SPDZ_ERR_STATE, SPDZ_ERR_OOM,
+ * SPDZ_ERR_CUDA. */
+typedef struct spdz_party spdz_party;
+int spdz_party_create(spdz_party **out, int party, int n_parties, int field, void *stream);
+int spdz_party_destroy(spdz_party *p);
+/* This party's MAC-key share alpha_i (device, one element); resets the
+ * epoch's sums. */
+int spdz_party_load_alpha(spdz_party *p, const void *alpha_share_dev);
+/* Seed of the check coefficients; epoch 0 (SPDZ_ERR_STATE with values opened). */
+int spdz_party_set_check_seed(spdz_party *p, uint64_t seed);
+/* eps_i = x_i - a_i and delta_i = y_i - b_i (value rows, N elements each) into
+ * eps_dev, dlt_dev: this party's contribution to the open. */
+int spdz_party_mask(spdz_party *p, const spdz_buf *x, const spdz_buf *y, const spdz_buf *a, const spdz_buf *b,
+                    void *eps_dev, void *dlt_dev, int64_t N);
+/* out[j] = sum_k rows[k*N + j] over the n parties' gathered rows (device,
+ * [n][N] contiguous): the opened public values. */
+int spdz_party_open_sum(spdz_party *p, const void *rows_dev, int64_t N, void *out_dev);
+/* With the public eps, delta ([N] each, device): z_i and gamma(z)_i as in
+ * spdz_mul_batch for this party (party 0 adds eps delta to its value), and
+ * the check sums A += r eps + r' delta, S_i += r (gamma(x)_i - gamma(a)_i)
+ * + r' (gamma(y)_i - gamma(b)_i) for the 2N values opened. */
+int spdz_party_combine(spdz_party *p, const void *eps_dev, const void *dlt_dev, const spdz_buf *x, const spdz_buf *y,
+                       const spdz_buf *a, const spdz_buf *b, const spdz_buf *c, const spdz_buf *z, int64_t N);
+/* sigma_i = S_i - alpha_i A over the epoch (host, one element; two 64-bit
+ * words for p127), *opened_out (may be NULL) = values opened in it; then
+ * the next epoch starts.  Synchronises the party's stream. */
+int spdz_party_sigma(spdz_party *p, void *sigma_host, int64_t *opened_out);
+
 /* ------------------------------------------------------------ measurement
  * Integer issue-rate microbenchmark (no counterpart in the paper; the
  * compute-side denominator of the roofline of kernels bound by integer

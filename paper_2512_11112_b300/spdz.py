@@ -144,6 +144,14 @@ _SIGS = {
     "spdz_mlp_adam_step": [_vp, _vp, C.c_float],
     "spdz_run_dag_host": [_vp, _vp, C.POINTER(spdz_plan), _bufp, _vp, _vp, C.POINTER(_vp), _i64, _i64, _vp, _vp],
     "spdz_int_peak": [_int, _i64, _vp, _vp, C.POINTER(C.c_double)],
+    "spdz_party_create": [C.POINTER(_vp), _int, _int, _int, _vp],
+    "spdz_party_destroy": [_vp],
+    "spdz_party_load_alpha": [_vp, _vp],
+    "spdz_party_set_check_seed": [_vp, _u64],
+    "spdz_party_mask": [_vp, _bufp, _bufp, _bufp, _bufp, _vp, _vp, _i64],
+    "spdz_party_open_sum": [_vp, _vp, _i64, _vp],
+    "spdz_party_combine": [_vp, _vp, _vp, _bufp, _bufp, _bufp, _bufp, _bufp, _bufp, _i64],
+    "spdz_party_sigma": [_vp, _vp, C.POINTER(_i64)],
     "spdz_sched_num_configs": [C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "spdz_sched_config_plan": [_vp, C.c_int32, C.POINTER(spdz_plan)],
     "spdz_sched_record": [_vp, _vp, _bufp, C.c_int32],
@@ -696,3 +704,45 @@ def spdz_int_peak(kind: int, iters: int, stream, scratch) -> float:
     r = C.c_double()
     _chk(None, lib.spdz_int_peak(kind, iters, stream, ptr(scratch), C.byref(r)))
     return r.value
+
+
+# ------------------------------------------------------------ party per GPU
+
+def spdz_party_create(party: int, n_parties: int, field: int, stream=None):
+    h = _vp()
+    _chk(None, lib.spdz_party_create(C.byref(h), party, n_parties, field, stream))
+    return h
+
+
+def spdz_party_destroy(p) -> None:
+    lib.spdz_party_destroy(p)
+
+
+def spdz_party_load_alpha(p, alpha_share) -> None:
+    _chk(None, lib.spdz_party_load_alpha(p, ptr(alpha_share)))
+
+
+def spdz_party_set_check_seed(p, seed: int) -> None:
+    _chk(None, lib.spdz_party_set_check_seed(p, seed))
+
+
+def spdz_party_mask(p, x: spdz_buf, y: spdz_buf, a: spdz_buf, b: spdz_buf, eps, dlt, N: int) -> None:
+    _chk(None, lib.spdz_party_mask(p, C.byref(x), C.byref(y), C.byref(a), C.byref(b), ptr(eps), ptr(dlt), N))
+
+
+def spdz_party_open_sum(p, rows, N: int, out) -> None:
+    _chk(None, lib.spdz_party_open_sum(p, ptr(rows), N, ptr(out)))
+
+
+def spdz_party_combine(p, eps, dlt, x: spdz_buf, y: spdz_buf, a: spdz_buf, b: spdz_buf, c: spdz_buf, z: spdz_buf,
+                       N: int) -> None:
+    _chk(None, lib.spdz_party_combine(p, ptr(eps), ptr(dlt), C.byref(x), C.byref(y), C.byref(a), C.byref(b),
+                                      C.byref(c), C.byref(z), N))
+
+
+def spdz_party_sigma(p, words: int):
+    """(sigma_i as 64-bit words [words], values opened in the epoch)."""
+    out = np.zeros(words, dtype=np.uint64)
+    opened = _i64()
+    _chk(None, lib.spdz_party_sigma(p, out.ctypes.data, C.byref(opened)))
+    return out, opened.value
