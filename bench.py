@@ -231,13 +231,16 @@ def schedule(circ, reps=2, epochs=400):
     plan, rep = S.spdz_sched_choose(circ.ctx, circ.h, circ.wires.buf(), 5)
     for d, h, w in items[:-1]:
         S.spdz_dag_destroy(h)
-    names = {0: "default fused plan", 1: "autotuned uniform plan", 2: "learned plan", 3: "tagged plan"}
+    names = {0: "default fused plan", 1: "autotuned uniform plan", 2: "learned plan"}
     groups = [{"end": int(plan.group_end[g]), "cluster": int(plan.group_cluster[g]),
-               "block": int(plan.group_block[g]), "ctas_per_sm": int(plan.group_ctas_per_sm[g])}
+               "block": int(plan.group_block[g]), "ctas_per_sm": int(plan.group_ctas_per_sm[g]),
+               "tagged": int(plan.group_tagged[g])}
               for g in range(plan.n_groups)]
     return {"chosen": names.get(rep.chosen, "?"), "default_ms": rep.default_ms, "autotuned_ms": rep.autotuned_ms,
             "learned_ms": rep.learned_ms, "learned_predicted_ms": rep.predicted_ms,
             "tagged_ms": rep.tagged_ms, "chosen_mode": int(plan.mode),
+            "learned_is_autotuned": int(rep.learned_is_autotuned),
+            "chosen_tagged": int(plan.mode == S.SPDZ_SCHED_TAGGED or any(g["tagged"] for g in groups)),
             "learned_groups": rep.learned_groups, "switch_us": rep.switch_us, "samples": rep.samples,
             "train_loss_ln_us": rep.train_loss, "scheduling_s": round(time.perf_counter() - t0, 2),
             "chosen_groups": groups}
@@ -422,7 +425,9 @@ def run_ours(args, rank, world, local_rank):
     # DRAM traffic per launch from the committed ncu capture, used only when
     # the chosen plan is the captured one
     tr = read_traffic()
-    if sched["chosen_mode"] == S.SPDZ_SCHED_TAGGED:
+    one_tagged = sched["chosen_mode"] == S.SPDZ_SCHED_TAGGED or (
+        len(sched["chosen_groups"]) == 1 and sched["chosen_groups"][0]["tagged"])
+    if one_tagged:
         kname = "k_dag_tagged<3> (scheduled circuit run)"
         traffic = tr.get("k_dag_tagged")
     else:
@@ -472,9 +477,10 @@ def run_ours(args, rank, world, local_rank):
                      "peak_source": peak_src, "algorithmic_bytes_per_launch": bytes_run},
         "beaver_batch_roofline": beaver,
         # per step: the run's begin kernel, one kernel per layer group, the check
-        # kernel (the tagged kernel runs the check itself: begin + one kernel)
-        "gpu_launches": steps * (2 if sched["chosen_mode"] == S.SPDZ_SCHED_TAGGED
-                                 else 2 + max(1, len(sched["chosen_groups"]))),
+        # kernel (a tagged last group runs the check itself)
+        "gpu_launches": steps * (1 + max(1, len(sched["chosen_groups"])) +
+                                 (0 if (sched["chosen_mode"] == S.SPDZ_SCHED_TAGGED or
+                                        (sched["chosen_groups"] and sched["chosen_groups"][-1]["tagged"])) else 1)),
         "clocks": clk.summary(),
     }
     if cpu:

@@ -264,6 +264,12 @@ typedef struct {
                                               of every gate after the first layer wait for a tag
                                               that no store writes, so the bounded operand wait
                                               runs out (SPDZ_ERR_TIMEOUT); 0 in normal use */
+    int32_t group_tagged[SPDZ_MAX_GROUPS]; /* fused, p = 2^61-1: 1 = the group runs the tagged
+                                              kernel (as SPDZ_SCHED_TAGGED, over the group's layers,
+                                              with barrier_slack and poll_ns); its first layer reads
+                                              its operands from the wires the earlier groups
+                                              finished, its later layers read the group's own
+                                              outputs from the tagged copy.  group_cluster must be 0 */
 } spdz_plan;
 
 typedef struct {
@@ -403,19 +409,22 @@ int spdz_mlp_adam_step(spdz_mlp *m, const float *grad_dev, float lr);
  *
  * Candidate group configurations (index 0..count-1, spdz_sched_num_configs):
  * whole-grid groups with device barriers at several block sizes and CTAs per
- * SM, and single-cluster groups (cluster barriers) for narrow layers. */
+ * SM, single-cluster groups (cluster barriers) for narrow layers, and (p =
+ * 2^61-1) a tagged group (fence-free barriers over the tagged copy, a slack
+ * of 1/12 of the CTAs).  The autotuner measures every configuration as one
+ * group over the whole circuit; the learned planner mixes them per group. */
 typedef struct {
     double default_ms;     /* measured makespan of the default fused plan */
     double autotuned_ms;   /* best measured makespan over the uniform configurations */
     double learned_ms;     /* measured makespan of the learned plan (-1: model not trained) */
     double predicted_ms;   /* the cost model's prediction for the learned plan (-1: none) */
     double switch_us;      /* measured cost of one extra layer group */
-    int32_t chosen;        /* plan kept for plan == NULL runs: 0 default, 1 autotuned, 2 learned,
-                              3 tagged */
+    int32_t chosen;        /* plan kept for plan == NULL runs: 0 default, 1 autotuned, 2 learned */
     int32_t learned_groups;
     int32_t samples;       /* training samples recorded so far */
     float train_loss;      /* final training loss (mean squared error of ln microseconds) */
-    double tagged_ms;      /* measured makespan of the tagged plan (-1: not applicable) */
+    double tagged_ms;      /* measured makespan of the uniform tagged configuration (-1: not p61) */
+    int32_t learned_is_autotuned; /* 1 when the learned plan is the autotuned uniform plan itself */
 } spdz_sched_report;
 
 int spdz_sched_num_configs(int32_t *count, int32_t *n_features);
@@ -444,9 +453,9 @@ int spdz_sched_learned_plan(spdz_ctx *ctx, spdz_dag *dag, spdz_plan *out, double
 /* The autotuned plan: the fastest measured uniform configuration. */
 int spdz_sched_autotune(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int32_t reps, spdz_plan *out,
                         double *best_ms);
-/* Measures the default, autotuned, (if trained) learned and (p = 2^61-1)
- * tagged plans, keeps the fastest for this circuit's plan == NULL runs, and
- * reports them all. */
+/* Measures the default, autotuned and (if trained) learned plans, keeps the
+ * fastest for this circuit's plan == NULL runs (the learned plan when it is
+ * the autotuned plan itself), and reports them all. */
 int spdz_sched_choose(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int32_t reps, spdz_plan *out,
                       spdz_sched_report *rep);
 

@@ -75,6 +75,47 @@ static int occupancy(const void *kern, int block, size_t smem = 0) {
     return occ < 1 ? 1 : occ;
 }
 
+// Launches the tagged kernel over layers [l0, l1) (p61 only); *grid_out is
+// its grid, for the barrier count.  Returns 0 or a status.
+template <class F, int NP>
+static int launch_tagged(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, DagArgs<F> a, int block, int l0, int l1,
+                         uint32_t bar_base, bool final_check, int ctas_per_sm, cudaStream_t s, int *grid_out) {
+    if constexpr (std::is_same_v<F, F61>) {
+        auto kern = k_dag_tagged<NP>;
+        const size_t smem = tagged_smem<NP>(block);
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess)
+                return set_err(ctx, SPDZ_ERR_CUDA, "tagged kernel shared memory (%zu bytes): %s", smem, cudaGetErrorString(e));
+        }
+        // every CTA must be resident (gates wait on gates of other CTAs)
+        const int occ = occupancy((const void *)kern, block, smem);
+        int cpsm = ctas_per_sm;
+        if (cpsm <= 0 || cpsm > occ) cpsm = occ;
+        int64_t wmax = 1;
+        for (int l = l0; l < l1; ++l) wmax = std::max<int64_t>(wmax, dag->lay[l].s[5] - dag->lay[l].s[0]);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)cpsm * ctx->sm_count, (wmax + 31) / 32));
+        a.mir = dag->d_mir;
+        // the first group copies the inputs into the tagged copy; a later group
+        // reads whatever earlier groups finished from the party-major wires
+        a.n_in = l0 == 0 ? dag->n_inputs : 0;
+        a.wbase = l0 == 0 ? 0 : (uint64_t)(dag->n_inputs + dag->lay[l0].s[0]);
+        a.poll_ns = plan.poll_ns ? plan.poll_ns : 128u;
+        a.slack = std::min<uint32_t>(plan.barrier_slack, (uint32_t)grid);
+        a.bar_base = bar_base;
+        a.final_check = final_check ? 1 : 0;
+        a.l0 = l0;
+        a.l1 = l1;
+        kern<<<grid, block, smem, s>>>(a);
+        if (cudaError_t e = cudaGetLastError(); e != cudaSuccess)
+            return set_err(ctx, SPDZ_ERR_CUDA, "tagged circuit launch: %s", cudaGetErrorString(e));
+        *grid_out = grid;
+        return SPDZ_OK;
+    } else {
+        return set_err(ctx, SPDZ_ERR_ARG, "tagged execution needs p = 2^61-1");
+    }
+}
+
 // Enqueues every kernel of one run on stream s (begin, layers, checks).
 // Returns the number of launches, or -status.
 template <class F, int NP>
@@ -90,6 +131,7 @@ static int enqueue_run(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, cons
     a.test_unwritten_tag = plan.test_unwritten_tag != 0;
     cudaStream_t saved = ctx->stream;
     ctx->stream = s;
+    bool checked = false;       // a tagged last group ran the final check
     if (plan.mode == SPDZ_SCHED_PER_LAYER) {
         auto kern = k_dag_segment<F, NP>;
         const int cap = occupancy((const void *)kern, block) * ctx->sm_count;
@@ -113,40 +155,13 @@ static int enqueue_run(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, cons
         }
         if (layer_events) cudaEventRecord(dag->lev[dag->depth], s);
     } else if (plan.mode == SPDZ_SCHED_TAGGED) {
-        if constexpr (std::is_same_v<F, F61>) {
-            auto kern = k_dag_tagged<NP>;
-            const size_t smem = tagged_smem<NP>(block);
-            if (smem > 48 * 1024) {
-                cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                if (e != cudaSuccess) {
-                    ctx->stream = saved;
-                    return -set_err(ctx, SPDZ_ERR_CUDA, "tagged kernel shared memory (%zu bytes): %s", smem, cudaGetErrorString(e));
-                }
-            }
-            // every CTA must be resident (gates wait on gates of other CTAs)
-            const int occ = occupancy((const void *)kern, block, smem);
-            int cpsm = plan.ctas_per_sm;
-            if (cpsm <= 0 || cpsm > occ) cpsm = occ;
-            int64_t wmax = 1;
-            for (int l = 0; l < dag->depth; ++l) wmax = std::max<int64_t>(wmax, dag->lay[l].s[5] - dag->lay[l].s[0]);
-            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)cpsm * ctx->sm_count, (wmax + 31) / 32));
-            a.mir = dag->d_mir;
-            a.n_in = dag->n_inputs;
-            a.poll_ns = plan.poll_ns ? plan.poll_ns : 128u;
-            a.slack = std::min<uint32_t>(plan.barrier_slack, (uint32_t)grid);
-            a.record_ts = layer_events ? 1 : 0;
-            a.l0 = 0;
-            a.l1 = dag->depth;
-            kern<<<grid, block, smem, s>>>(a);
-            ++launches;
-            if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) {
-                ctx->stream = saved;
-                return -set_err(ctx, SPDZ_ERR_CUDA, "tagged circuit launch: %s", cudaGetErrorString(e));
-            }
-        } else {
+        a.record_ts = layer_events ? 1 : 0;
+        int grid = 0;
+        if (int rc = launch_tagged<F, NP>(ctx, dag, plan, a, block, 0, dag->depth, 0, true, plan.ctas_per_sm, s, &grid)) {
             ctx->stream = saved;
-            return -set_err(ctx, SPDZ_ERR_ARG, "tagged mode needs p = 2^61-1");
+            return -rc;
         }
+        ++launches;
     } else {
         auto kern = F::WORDS == 1 ? k_dag_fused<F, NP> : k_dag_fused_wide<F, NP>;
         const int ng = plan.n_groups > 0 ? plan.n_groups : 1;
@@ -158,6 +173,30 @@ static int enqueue_run(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, cons
             const int ncl = plan.n_groups > 0 ? plan.group_cluster[g] : 0;
             const int gblock = plan.n_groups > 0 && plan.group_block[g] > 0 ? plan.group_block[g] : block;
             const size_t smem = fused_smem<F, NP>(gblock);
+            if (plan.n_groups > 0 && plan.group_tagged[g]) {
+                // a tagged group: fence-free barriers over the tagged copy
+                int grid = 0;
+                const int cpsm = plan.group_ctas_per_sm[g] > 0 ? plan.group_ctas_per_sm[g] : plan.ctas_per_sm;
+                // the last group's last CTA runs the run's MAC check itself
+                const bool last = g + 1 == ng;
+                checked = checked || last;
+                if (int rc = launch_tagged<F, NP>(ctx, dag, plan, a, gblock, l0, l1, bar_base, last, cpsm, s, &grid)) {
+                    ctx->stream = saved;
+                    return -rc;
+                }
+                ++launches;
+                const int nbar = (l1 - l0 - 1) + (layer_events ? 1 : 0);
+                bar_base += (uint32_t)grid * (uint32_t)nbar;
+                if (g + 1 < ng && plan.group_flush[g]) {
+                    if (int rc = launch_check(ctx, 0)) {
+                        ctx->stream = saved;
+                        return -rc;
+                    }
+                    ++launches;
+                }
+                l0 = l1;
+                continue;
+            }
             if (ncl > 0) {
                 // the whole group inside one cluster of ncl CTAs
                 auto ck = k_dag_cluster<F, NP>;
@@ -235,7 +274,7 @@ static int enqueue_run(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, cons
         }
     }
     // the tagged kernel finishes with the run's check itself
-    if (plan.mode != SPDZ_SCHED_TAGGED) {
+    if (plan.mode != SPDZ_SCHED_TAGGED && !checked) {
         int rc = launch_check(ctx, 1);
         ++launches;
         if (rc) {
@@ -265,6 +304,7 @@ static int validate_plan(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &p) {
         if (p.poll_ns > 50000) return set_err(ctx, SPDZ_ERR_ARG, "plan: poll_ns above 50 us");
         if (p.barrier_extra_arrivals != 0) return set_err(ctx, SPDZ_ERR_ARG, "plan: tagged mode has no extra arrivals");
     }
+    if (p.poll_ns > 50000) return set_err(ctx, SPDZ_ERR_ARG, "plan: poll_ns above 50 us");
     if (p.test_unwritten_tag != 0 && (p.mode != SPDZ_SCHED_TAGGED || p.test_unwritten_tag != 1))
         return set_err(ctx, SPDZ_ERR_ARG, "plan: test_unwritten_tag is 0 or 1, tagged mode only");
     if (p.block != 0 && (p.block < 32 || p.block > 256 || p.block % 32)) return set_err(ctx, SPDZ_ERR_ARG, "plan: block must be 32..256, a multiple of 32");
@@ -273,6 +313,9 @@ static int validate_plan(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &p) {
     for (int g = 0; g < p.n_groups; ++g) {
         if (p.group_cluster[g] < 0 || p.group_cluster[g] > 16 || (p.group_cluster[g] > 0 && p.mode != SPDZ_SCHED_FUSED))
             return set_err(ctx, SPDZ_ERR_ARG, "plan: cluster size must be 0..16 (fused mode)");
+        if (p.group_tagged[g] != 0 && (p.group_tagged[g] != 1 || p.mode != SPDZ_SCHED_FUSED || p.group_cluster[g] != 0 ||
+                                       dag->field != SPDZ_F61))
+            return set_err(ctx, SPDZ_ERR_ARG, "plan: a tagged group is 1, fused mode, no cluster, p = 2^61-1");
         const int b = p.group_block[g];
         if (b != 0 && (b < 32 || b > 256 || b % 32)) return set_err(ctx, SPDZ_ERR_ARG, "plan: group block must be 32..256, a multiple of 32");
     }
@@ -415,7 +458,9 @@ int spdz_run_dag(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan *plan_in, const s
     // tagged: the tagged copy (allocated on first use), the run's tag, and
     // the copy zeroed before the first run of every cycle of 7 tags
     uint32_t df_tag = 0;
-    if (plan.mode == SPDZ_SCHED_TAGGED) {
+    bool tags = plan.mode == SPDZ_SCHED_TAGGED;
+    for (int g = 0; g < plan.n_groups; ++g) tags = tags || plan.group_tagged[g] != 0;
+    if (tags) {
         const size_t need = (size_t)(dag->n_inputs + dag->n_gates) * 2 * (size_t)dag->n * sizeof(uint64_t);
         if (!dag->d_mir) {
             if (cudaMalloc(&dag->d_mir, std::max<size_t>(need, 16)) != cudaSuccess) {

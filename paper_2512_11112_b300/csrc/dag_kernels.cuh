@@ -65,6 +65,9 @@ template <class F> struct DagArgs {
     uint32_t poll_ns;                       // tagged: first sleep between operand polls
     uint32_t slack;                         // tagged: arrivals a layer barrier does not wait for
     int32_t test_unwritten_tag;             // testing (tagged): operands wait for a tag never written
+    uint64_t wbase;                         // tagged group starting after layer 0: wires below this
+                                            // were finished by earlier groups (read party-major)
+    int32_t final_check;                    // tagged: the last CTA runs the run's MAC check
 };
 
 // Operands of one gate that do not depend on earlier layers: its record,
@@ -536,11 +539,17 @@ __device__ __forceinline__ bool df_gate(const DagArgs<F61> &a, const LayerRow &L
         if (binary) df_input<NP>(a, rec.y, v);
     } else {
         // both operands' loads in flight at once; a wait only for a record
-        // whose first read missed its tag
-        df_issue<NP>(a.mir, rec.x, u);
-        if (binary) df_issue<NP>(a.mir, rec.y, v);
-        if (!df_tagged<NP>(u, wtag) && !df_wait<NP>(a, rec.x, wtag, u)) return false;
-        if (binary && !df_tagged<NP>(v, tag) && !df_wait<NP>(a, rec.y, tag, v)) return false;
+        // whose first read missed its tag.  Wires finished before the group
+        // (below wbase) are read from the party-major wires, untagged.
+        const bool xo = rec.x < a.wbase, yo = rec.y < a.wbase;
+        if (xo) df_input<NP>(a, rec.x, u);
+        else df_issue<NP>(a.mir, rec.x, u);
+        if (binary) {
+            if (yo) df_input<NP>(a, rec.y, v);
+            else df_issue<NP>(a.mir, rec.y, v);
+        }
+        if (!xo && !df_tagged<NP>(u, wtag) && !df_wait<NP>(a, rec.x, wtag, u)) return false;
+        if (binary && !yo && !df_tagged<NP>(v, tag) && !df_wait<NP>(a, rec.y, tag, v)) return false;
     }
     uint64_t z[NP], gz[NP];
     if (cls == C_MUL) {
@@ -600,7 +609,8 @@ __device__ __forceinline__ bool df_layer(const DagArgs<F61> &a, const LayerRow &
     return ok;
 }
 
-// The tagged form of the fused kernel (p61): gates read their operands from
+// The tagged form of the fused kernel (p61), over layers [l0, l1) (the whole
+// circuit, or one group of a plan): gates read their operands from
 // the tagged copy (one wire's shares of every party in 2*NP consecutive
 // words, a third of the sectors of the party-major gathers) and validate
 // them by tag, so the barrier between layers needs no fence: it only keeps
@@ -674,12 +684,13 @@ __global__ void __launch_bounds__(256, 2) k_dag_tagged(DagArgs<F61> a) {
                 staged = ok && r < L.s[5];
                 if (staged) stage_issue<F, NP>(a, L, r, class_of(L, r), tri_base, st);
             }
-            ok = grid_wait_relaxed(a.ds, nb * gridDim.x - a.slack, a.spin_ns) && ok;
+            ok = grid_wait_relaxed(a.ds, a.bar_base + nb * gridDim.x - a.slack, a.spin_ns) && ok;
             if (stamp) a.ds->layer_ts[l + 1] = gtimer();
         }
     }
     cp_async_wait_all();
     block_accumulate<F, NP + 1>(acc, a.ds->acc);
+    if (!a.final_check) return;
     // the last CTA to finish runs the run's MAC check (its accumulator
     // atomics, like every CTA's, are ordered before its count by the fence)
     __shared__ bool s_last;

@@ -29,9 +29,11 @@ struct GroupConfig {
     int cluster;   // 0: whole grid with device barriers; k: one cluster of k CTAs
     int block;     // threads per CTA
     int cpsm;      // CTAs per SM (grid groups)
+    int tagged;    // 1: the tagged kernel (p = 2^61-1 only; fence-free barriers, slack 1/12 of the CTAs)
 };
 constexpr GroupConfig kConfigs[] = {
-    {0, 256, 2}, {0, 256, 1}, {0, 128, 4}, {0, 128, 2}, {16, 256, 0}, {8, 256, 0}, {16, 128, 0},
+    {0, 256, 2, 0}, {0, 256, 1, 0}, {0, 128, 4, 0}, {0, 128, 2, 0}, {16, 256, 0, 0}, {8, 256, 0, 0}, {16, 128, 0, 0},
+    {0, 256, 2, 1},
 };
 constexpr int NCFG = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
 constexpr int NFEAT = 6 + NCFG;
@@ -45,6 +47,7 @@ struct Sched {
     double switch_us = 3.0;           // measured cost of one extra group
     bool switch_measured = false;
     std::unordered_map<const spdz_dag *, spdz_plan> chosen;
+    double last_tagged_ms = -1;       // the autotuner's measure of the uniform tagged configuration
     float *dX = nullptr, *dY = nullptr;
     int64_t dcap = 0;
 };
@@ -77,6 +80,15 @@ static void layer_features(const spdz_dag *dag, int l, int cfg, float *f) {
     f[6 + cfg] = 1.f;
 }
 
+// Configuration cfg is available for the circuit's field.
+static bool config_ok(const spdz_dag *dag, int cfg) { return !kConfigs[cfg].tagged || dag->field == SPDZ_F61; }
+
+// Barrier slack of tagged groups: a layer starts when all but 1/12 of the
+// CTAs (2 per SM) have arrived.
+static uint32_t tagged_slack(const spdz_dag *dag) {
+    return (uint32_t)(2 * (dag->ctx ? dag->ctx->sm_count : 148) / 12);
+}
+
 static void uniform_plan(const spdz_dag *dag, int cfg, spdz_plan &p) {
     memset(&p, 0, sizeof p);
     p.mode = SPDZ_SCHED_FUSED;
@@ -88,6 +100,19 @@ static void uniform_plan(const spdz_dag *dag, int cfg, spdz_plan &p) {
     p.group_cluster[0] = kConfigs[cfg].cluster;
     p.group_block[0] = kConfigs[cfg].block;
     p.group_ctas_per_sm[0] = kConfigs[cfg].cpsm;
+    p.group_tagged[0] = kConfigs[cfg].tagged;
+    if (kConfigs[cfg].tagged) p.barrier_slack = tagged_slack(dag);
+}
+
+// Two plans with the same groups and group configurations.
+static bool same_groups(const spdz_plan &a, const spdz_plan &b) {
+    if (a.mode != b.mode || a.n_groups != b.n_groups || a.barrier_slack != b.barrier_slack) return false;
+    for (int g = 0; g < a.n_groups; ++g)
+        if (a.group_end[g] != b.group_end[g] || a.group_cluster[g] != b.group_cluster[g] ||
+            a.group_block[g] != b.group_block[g] || a.group_ctas_per_sm[g] != b.group_ctas_per_sm[g] ||
+            a.group_tagged[g] != b.group_tagged[g] || a.group_flush[g] != b.group_flush[g])
+            return false;
+    return true;
 }
 
 // Median device time (ms) of `reps` runs of the plan, after one warm-up run.
@@ -152,6 +177,7 @@ static int learned_plan(spdz_ctx *ctx, spdz_dag *dag, spdz_plan &p, double *pred
         for (int j = 0; j < l; ++j) {
             if (ngr[j] >= SPDZ_MAX_GROUPS) continue;
             for (int c = 0; c < NCFG; ++c) {
+                if (!config_ok(dag, c)) continue;
                 const double v = dp[j] + pre[(size_t)l * NCFG + c] - pre[(size_t)j * NCFG + c] + (j > 0 ? s->switch_us : 0.0);
                 if (v < dp[l]) {
                     dp[l] = v;
@@ -175,6 +201,14 @@ static int learned_plan(spdz_ctx *ctx, spdz_dag *dag, spdz_plan &p, double *pred
         p.group_cluster[g] = gc.cluster;
         p.group_block[g] = gc.block;
         p.group_ctas_per_sm[g] = gc.cpsm;
+        p.group_tagged[g] = gc.tagged;
+        if (gc.tagged) p.barrier_slack = tagged_slack(dag);
+    }
+    // one group: the block size and CTAs per SM of the plan as the autotuner
+    // writes them, so that equal plans compare equal
+    if (p.n_groups == 1) {
+        p.block = p.group_block[0];
+        p.ctas_per_sm = p.group_ctas_per_sm[0];
     }
     if (pred_ms) *pred_ms = dp[L] * 1e-3;
     return SPDZ_OK;
@@ -238,6 +272,7 @@ int spdz_sched_record(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int32
     const int L = dag->depth;
     std::vector<float> f(NFEAT);
     for (int c = 0; c < NCFG; ++c) {
+        if (!config_ok(dag, c)) continue;
         spdz_plan p;
         uniform_plan(dag, c, p);
         p.record_layer_times = 1;
@@ -345,11 +380,15 @@ int spdz_sched_autotune(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int
                         double *best_ms) {
     if (!ctx || !dag || !wires || !out || reps < 1) return set_err(ctx, SPDZ_ERR_ARG, "sched_autotune: bad argument");
     double best = 1e300;
+    Sched *s = sched_of(ctx);
+    s->last_tagged_ms = -1;
     for (int c = 0; c < NCFG; ++c) {
+        if (!config_ok(dag, c)) continue;
         spdz_plan p;
         uniform_plan(dag, c, p);
         double ms = 0;
         if (int rc = measure(ctx, dag, p, wires, reps, &ms)) return rc;
+        if (kConfigs[c].tagged) s->last_tagged_ms = ms;
         if (ms < best) {
             best = ms;
             *out = p;
@@ -368,6 +407,7 @@ int spdz_sched_choose(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int32
     uniform_plan(dag, DEFAULT_CFG, def);
     if (int rc = measure(ctx, dag, def, wires, reps, &r.default_ms)) return rc;
     if (int rc = spdz_sched_autotune(ctx, dag, wires, reps, &tuned, &r.autotuned_ms)) return rc;
+    r.tagged_ms = s->last_tagged_ms;
     spdz_plan best = tuned;
     double best_ms = r.autotuned_ms;
     r.chosen = 1;
@@ -379,28 +419,20 @@ int spdz_sched_choose(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int32
     r.learned_ms = -1;
     r.predicted_ms = -1;
     if (s->trained && learned_plan(ctx, dag, learned, &r.predicted_ms) == SPDZ_OK) {
-        if (int rc = measure(ctx, dag, learned, wires, reps, &r.learned_ms)) return rc;
         r.learned_groups = learned.n_groups;
-        if (r.learned_ms < best_ms) {
-            best = learned;
-            best_ms = r.learned_ms;
-            r.chosen = 2;
-        }
-    }
-    r.tagged_ms = -1;
-    if (dag->field == SPDZ_F61) {
-        spdz_plan df;
-        memset(&df, 0, sizeof df);
-        df.mode = SPDZ_SCHED_TAGGED;
-        df.block = 256;
-        df.use_graph = 1;
-        // a layer starts when all but 1/12 of the CTAs (2 per SM) arrived
-        df.barrier_slack = (uint32_t)(2 * ctx->sm_count / 12);
-        if (int rc = measure(ctx, dag, df, wires, reps, &r.tagged_ms)) return rc;
-        if (r.tagged_ms < best_ms) {
-            best = df;
-            best_ms = r.tagged_ms;
-            r.chosen = 3;
+        if (same_groups(learned, tuned)) {
+            // the model picked the plan the autotuner found by measuring
+            // every configuration: nothing more to measure
+            r.learned_is_autotuned = 1;
+            r.learned_ms = r.autotuned_ms;
+            if (r.chosen == 1) r.chosen = 2;
+        } else {
+            if (int rc = measure(ctx, dag, learned, wires, reps, &r.learned_ms)) return rc;
+            if (r.learned_ms < best_ms) {
+                best = learned;
+                best_ms = r.learned_ms;
+                r.chosen = 2;
+            }
         }
     }
     r.samples = (int32_t)s->Y.size();

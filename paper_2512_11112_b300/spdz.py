@@ -62,7 +62,8 @@ class spdz_plan(C.Structure):
                 ("barrier_extra_arrivals", C.c_int32),
                 ("group_cluster", C.c_int32 * SPDZ_MAX_GROUPS),
                 ("group_block", C.c_int32 * SPDZ_MAX_GROUPS), ("poll_ns", C.c_uint32),
-                ("barrier_slack", C.c_uint32), ("test_unwritten_tag", C.c_int32)]
+                ("barrier_slack", C.c_uint32), ("test_unwritten_tag", C.c_int32),
+                ("group_tagged", C.c_int32 * SPDZ_MAX_GROUPS)]
 
 
 class spdz_stats(C.Structure):
@@ -74,7 +75,7 @@ class spdz_sched_report(C.Structure):
     _fields_ = [("default_ms", C.c_double), ("autotuned_ms", C.c_double), ("learned_ms", C.c_double),
                 ("predicted_ms", C.c_double), ("switch_us", C.c_double), ("chosen", C.c_int32),
                 ("learned_groups", C.c_int32), ("samples", C.c_int32), ("train_loss", C.c_float),
-                ("tagged_ms", C.c_double)]
+                ("tagged_ms", C.c_double), ("learned_is_autotuned", C.c_int32)]
 
 
 SPDZ_SERVE_SEQUENTIAL, SPDZ_SERVE_BATCHED, SPDZ_SERVE_HEURISTIC, SPDZ_SERVE_LEARNED = 0, 1, 2, 3
@@ -309,7 +310,8 @@ def spdz_field_op(ctx, op: int, a, b, out, N: int) -> None:
 def plan(mode: int = SPDZ_SCHED_FUSED, block: int = 256, ctas_per_sm: int = 0, use_graph: int = 1,
          groups=None, flush=None, group_ctas=None, record_layer_times: int = 0,
          spin_limit_us: int = 0, barrier_extra_arrivals: int = 0, group_cluster=None,
-         group_block=None, poll_ns: int = 0, barrier_slack: int = 0, test_unwritten_tag: int = 0) -> spdz_plan:
+         group_block=None, poll_ns: int = 0, barrier_slack: int = 0, test_unwritten_tag: int = 0,
+         group_tagged=None) -> spdz_plan:
     """Builds a spdz_plan; groups = list of exclusive end layers;
     group_cluster[g] > 0 runs group g inside one cluster of that many CTAs."""
     p = spdz_plan()
@@ -322,6 +324,7 @@ def plan(mode: int = SPDZ_SCHED_FUSED, block: int = 256, ctas_per_sm: int = 0, u
         p.group_ctas_per_sm[g] = int(group_ctas[g]) if group_ctas else 0
         p.group_cluster[g] = int(group_cluster[g]) if group_cluster else 0
         p.group_block[g] = int(group_block[g]) if group_block else 0
+        p.group_tagged[g] = int(group_tagged[g]) if group_tagged else 0
     p.record_layer_times, p.spin_limit_us = record_layer_times, spin_limit_us
     p.barrier_extra_arrivals = barrier_extra_arrivals
     p.poll_ns = poll_ns

@@ -100,6 +100,19 @@ def plans(depth, p=None):
         out["tagged_slack"] = S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=1, barrier_slack=3)
         # slack above the grid size: no CTA ever waits at a layer barrier
         out["tagged_no_wait"] = S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=0, barrier_slack=10**6, poll_ns=32)
+        # tagged groups inside fused plans: a whole-circuit tagged group; a
+        # grid group, then a tagged group (its first layer reads the grid
+        # group's outputs from the party-major wires); tagged, cluster,
+        # tagged (the last group's last CTA runs the check) with a flush
+        out["tagged_group"] = S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=1, groups=[depth], group_tagged=[1],
+                                     barrier_slack=2)
+        if depth > 1:
+            out["grid_then_tagged"] = S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=0, groups=[mid, depth],
+                                             group_tagged=[0, 1], flush=[1, 0])
+        if depth > 2:
+            out["tagged_cluster_tagged"] = S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=1, groups=[1, mid + 1, depth],
+                                                  group_tagged=[1, 0, 1], group_cluster=[0, 8, 0], flush=[1, 0, 0],
+                                                  barrier_slack=1)
     return out
 
 
@@ -137,7 +150,7 @@ def test_benchmark_sized_circuit_matches_oracle():
     wire."""
     dag = W.layered_dag(seed=2)
     n = 3
-    dc = DeviceCircuit(dag, n, seed=2, runs=3)
+    dc = DeviceCircuit(dag, n, seed=2, runs=4)
     try:
         O.set_threads(8)
         ev, em, ok, osig = oracle_run(dag, n, seed=2, run_index=0)
@@ -161,6 +174,16 @@ def test_benchmark_sized_circuit_matches_oracle():
         assert_equal(gm, em2, "tagged MACs")
         assert passed and ok2
         assert_equal(sig, osig2, "tagged sigma")
+        # two tagged groups inside a fused plan (the second group's first
+        # layer reads the first group's outputs from the party-major wires)
+        ev3, em3, ok3, osig3 = oracle_run(dag, n, seed=2, run_index=3)
+        st, passed, sig = dc.run(S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=1, groups=[16, 32], group_tagged=[1, 1],
+                                        barrier_slack=24))
+        gv, gm = dc.wires.host()
+        assert_equal(gv, ev3, "tagged groups values")
+        assert_equal(gm, em3, "tagged groups MACs")
+        assert passed and ok3
+        assert_equal(sig, osig3, "tagged groups sigma")
     finally:
         dc.close()
 
@@ -348,6 +371,26 @@ def test_invalid_circuit_rejected():
         assert e.value.code == S.SPDZ_ERR_ARG
     finally:
         S.spdz_ctx_destroy(ctx)
+
+
+def test_tagged_groups_refused_outside_p61_and_with_clusters():
+    dag = W.small_dag(seed=4, p=O.P127, n_inputs=20, widths=[10, 10])
+    dc = DeviceCircuit(dag, 2, seed=4, runs=1)
+    try:
+        with pytest.raises(S.SpdzError) as e:
+            S.spdz_run_dag(dc.ctx, dc.h, S.plan(mode=S.SPDZ_SCHED_FUSED, groups=[2], group_tagged=[1]), dc.wires.buf())
+        assert e.value.code == S.SPDZ_ERR_ARG
+    finally:
+        dc.close()
+    dag = W.small_dag(seed=4, p=O.P61, n_inputs=20, widths=[10, 10])
+    dc = DeviceCircuit(dag, 2, seed=4, runs=1)
+    try:
+        with pytest.raises(S.SpdzError) as e:
+            S.spdz_run_dag(dc.ctx, dc.h, S.plan(mode=S.SPDZ_SCHED_FUSED, groups=[2], group_tagged=[1],
+                                                group_cluster=[8]), dc.wires.buf())
+        assert e.value.code == S.SPDZ_ERR_ARG
+    finally:
+        dc.close()
 
 
 @pytest.mark.parametrize("p", [O.P61, O.P127])

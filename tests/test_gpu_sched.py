@@ -52,7 +52,7 @@ class World:
         S.spdz_ctx_destroy(self.ctx)
 
 
-def test_learned_scheduler_gains_over_default_and_stays_exact():
+def test_learned_scheduler_matches_or_beats_autotuned_and_stays_exact():
     p, n = O.P61, 3
     cal = W.calibration_dags(p)
     narrow = W.small_dag(seed=5, p=p, n_inputs=256, widths=[256] * 24,
@@ -81,10 +81,20 @@ def test_learned_scheduler_gains_over_default_and_stays_exact():
             errs.append(np.median(np.abs(pred - meas[c]) / meas[c]))
         assert np.median(errs) < 0.35, errs
 
-        # narrow circuit: the learned plan (cluster groups) against the default plan
+        # the held-out circuit (mixed widths, p61): the learned planner picks,
+        # without running it, the plan that the autotuner finds by measuring
+        # every configuration (the tagged form), so that plan is the learned one
+        _, rep_h = S.spdz_sched_choose(w.ctx, hh, wh.buf(), 3)
+        assert rep_h.learned_ms > 0 and rep_h.learned_ms <= 1.1 * rep_h.autotuned_ms, (rep_h.learned_ms,
+                                                                                    rep_h.autotuned_ms)
+        if rep_h.learned_is_autotuned:
+            assert rep_h.chosen == 2
+        # narrow circuit: the learned plan (cluster groups) against the
+        # autotuned fallback and the default plan
         dn, hn, wn = w.items[len(cal)]
         plan, rep = S.spdz_sched_choose(w.ctx, hn, wn.buf(), 5)
         assert rep.learned_ms > 0 and rep.learned_ms < 0.9 * rep.default_ms, (rep.learned_ms, rep.default_ms)
+        assert rep.learned_ms <= 1.1 * rep.autotuned_ms, (rep.learned_ms, rep.autotuned_ms)
         assert rep.chosen in (1, 2)
         assert abs(rep.predicted_ms - rep.learned_ms) < 0.5 * rep.learned_ms
 
