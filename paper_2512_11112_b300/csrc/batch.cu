@@ -285,82 +285,85 @@ __global__ void __launch_bounds__(256, (mul_min_blocks<F, NP, V>())) k_mul(MulAr
 // Inner products: one warp per product t; lane l takes terms l, l+32, ...;
 // the per-party sums of the term products (value and MAC) are reduced
 // across the warp and stored by lane 0.  N = number of products.
-// Two CTAs per SM: latency of the lanes' term loads is hidden by more
-// resident warps (p127 then keeps its sums in 128 registers with a few
-// spilled, and is faster than with one CTA and no spill).
 template <class F, int NP>
-__global__ void __launch_bounds__(256, 2) k_innerprod(MulArgs<F> a) {
+__global__ void __launch_bounds__(256) k_innerprod(MulArgs<F> a) {
     using T = typename F::T;
     const uint64_t key = a.ds->key;
-    if constexpr (std::is_same_v<F, F127>) {
-        // the term products' shares are summed unreduced across a lane's
-        // terms and reduced once per product before the warp sum
-        u128v alpha[NP], acc[NP + 1];
-        W127 wacc[NP + 1];
+    T alpha[NP], acc[NP + 1];
 #pragma unroll
-        for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
-        const int lane = threadIdx.x & 31;
-        const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
-        for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < a.N; t += wstride) {
-            W127 sums[2 * NP];
-            for (int64_t k = lane; k < a.len; k += 32) {
-                u128v z[NP], gz[NP], eps, dlt;
-                beaver_core127<NP>(a, t * a.len + k, key, alpha, wacc, z, gz, eps, dlt, sums);
-            }
-            u128v sz[NP], sg[NP];
+    for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
+#pragma unroll
+    for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < a.N; t += wstride) {
+        T sz[NP], sg[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) sz[i] = sg[i] = F::zero();
+        for (int64_t k = lane; k < a.len; k += 32) {
+            const int64_t e = t * a.len + k;
+            T z[NP][1], gz[NP][1], eps[1], dlt[1];
+            beaver_core<F, NP, 1>(a, e, e, key, alpha, acc, z, gz, eps, dlt);
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
-                sz[i] = warp_sum<F>(sums[i].reduce());
-                sg[i] = warp_sum<F>(sums[NP + i].reduce());
-            }
-            if (lane == 0) {
-#pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    F::st(a.zv + i * a.zs + t, sz[i]);
-                    F::st(a.zm + i * a.zs + t, sg[i]);
-                }
+                sz[i] = F::add(sz[i], z[i][0]);
+                sg[i] = F::add(sg[i], gz[i][0]);
             }
         }
 #pragma unroll
-        for (int k = 0; k < NP + 1; ++k) acc[k] = wacc[k].reduce();
-        block_accumulate<F, NP + 1>(acc, a.ds->acc);
-    } else {
-        T alpha[NP], acc[NP + 1];
-#pragma unroll
-        for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
-#pragma unroll
-        for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
-        const int lane = threadIdx.x & 31;
-        const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
-        for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < a.N; t += wstride) {
-            T sz[NP], sg[NP];
-#pragma unroll
-            for (int i = 0; i < NP; ++i) sz[i] = sg[i] = F::zero();
-            for (int64_t k = lane; k < a.len; k += 32) {
-                const int64_t e = t * a.len + k;
-                T z[NP][1], gz[NP][1], eps[1], dlt[1];
-                beaver_core<F, NP, 1>(a, e, e, key, alpha, acc, z, gz, eps, dlt);
-#pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    sz[i] = F::add(sz[i], z[i][0]);
-                    sg[i] = F::add(sg[i], gz[i][0]);
-                }
-            }
+        for (int i = 0; i < NP; ++i) {
+            sz[i] = warp_sum<F>(sz[i]);
+            sg[i] = warp_sum<F>(sg[i]);
+        }
+        if (lane == 0) {
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
-                sz[i] = warp_sum<F>(sz[i]);
-                sg[i] = warp_sum<F>(sg[i]);
-            }
-            if (lane == 0) {
-#pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    F::st(a.zv + i * a.zs + t, sz[i]);
-                    F::st(a.zm + i * a.zs + t, sg[i]);
-                }
+                F::st(a.zv + i * a.zs + t, sz[i]);
+                F::st(a.zm + i * a.zs + t, sg[i]);
             }
         }
-        block_accumulate<F, NP + 1>(acc, a.ds->acc);
     }
+    block_accumulate<F, NP + 1>(acc, a.ds->acc);
+}
+
+// p127 inner products: the term products' shares are summed unreduced
+// across a lane's terms and reduced once per product before the warp sum.
+// Two CTAs per SM: latency of the lanes' term loads is hidden by more
+// resident warps (the sums then live in 128 registers with a few spilled,
+// faster than one CTA and no spill).
+template <int NP>
+__global__ void __launch_bounds__(256, 2) k_innerprod127(MulArgs<F127> a) {
+    using F = F127;
+    const uint64_t key = a.ds->key;
+    u128v alpha[NP], acc[NP + 1];
+    W127 wacc[NP + 1];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < a.N; t += wstride) {
+        W127 sums[2 * NP];
+        for (int64_t k = lane; k < a.len; k += 32) {
+            u128v z[NP], gz[NP], eps, dlt;
+            beaver_core127<NP>(a, t * a.len + k, key, alpha, wacc, z, gz, eps, dlt, sums);
+        }
+        u128v sz[NP], sg[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            sz[i] = warp_sum<F>(sums[i].reduce());
+            sg[i] = warp_sum<F>(sums[NP + i].reduce());
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                F::st(a.zv + i * a.zs + t, sz[i]);
+                F::st(a.zm + i * a.zs + t, sg[i]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NP + 1; ++k) acc[k] = wacc[k].reduce();
+    block_accumulate<F, NP + 1>(acc, a.ds->acc);
 }
 
 // ----------------------------------------------------------------- open
@@ -449,6 +452,17 @@ template <class F> static bool host_canonical(const void *k) {
     }
 }
 
+
+template <class F, int NP>
+static void launch_innerprod(spdz_ctx *ctx, const MulArgs<F> &a, int64_t count) {
+    if constexpr (std::is_same_v<F, F127>) {
+        auto kern = k_innerprod127<NP>;
+        kern<<<grid_for(ctx, (const void *)kern, 256, 0, count * 32), 256, 0, ctx->stream>>>(a);
+    } else {
+        auto kern = k_innerprod<F, NP>;
+        kern<<<grid_for(ctx, (const void *)kern, 256, 0, count * 32), 256, 0, ctx->stream>>>(a);
+    }
+}
 
 template <class F, int NP>
 static void launch_linear(spdz_ctx *ctx, const LinArgs<F> &a, bool v2) {
@@ -597,10 +611,7 @@ int spdz_innerprod_batch(spdz_ctx *ctx, const spdz_buf *x, const spdz_buf *y, co
         fill_mul_args<F>(ctx, a, x, y, z, t0);
         a.N = count;
         a.len = len;
-        SPDZ_NP_SWITCH(ctx->n, {
-            auto kern = k_innerprod<F, NP>;
-            kern<<<grid_for(ctx, (const void *)kern, 256, 0, count * 32), 256, 0, ctx->stream>>>(a);
-        });
+        SPDZ_NP_SWITCH(ctx->n, launch_innerprod<F, NP>(ctx, a, count));
     });
     if ((rc = check_launch(ctx, "innerprod"))) return rc;
     ctx->opened += 2 * T;
