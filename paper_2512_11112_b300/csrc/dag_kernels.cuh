@@ -4,6 +4,7 @@
 // gate's layer-independent operands, the bounded device-wide barrier and
 // the per-layer, fused and cluster kernels.
 #pragma once
+#include <cstddef>
 #include "beaver.cuh"
 #include "check.cuh"
 #include "dag.cuh"
@@ -145,14 +146,29 @@ __device__ __forceinline__ void gate_exec(const DagArgs<F> &a, const LayerRow &L
 // own shared-memory slots (structure of arrays across the block, so the
 // accesses are conflict-free) with cp.async; nothing is shared between
 // threads, so only the thread's own wait is needed before use.
+// L2 eviction priorities: data read once (triples, records, constants, the
+// party-major output rows) goes first; the tagged copy, whose wires later
+// layers gather from anywhere in the run, goes last.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
 __device__ __forceinline__ void cp_async(void *smem, const void *gmem, int bytes) {
     const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    const uint64_t pol = l2_evict_first();
     if (bytes == 16)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+        asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "l"(pol) : "memory");
     else if (bytes == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+        asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;" ::"r"(s), "l"(gmem), "l"(pol) : "memory");
     else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+        asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" ::"r"(s), "l"(gmem), "l"(pol) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
@@ -261,17 +277,24 @@ __device__ __forceinline__ void grid_arrive_relaxed(DevState *ds) {
     if (threadIdx.x == 0) asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(&ds->bar_count) : "memory");
 }
 // Wait: thread 0 polls until `target` arrivals (bounded by spin_ns, as in
-// grid_barrier), then the CTA goes on together.
+// grid_barrier), then the CTA goes on together.  The arrival count and the
+// abort flag are adjacent words, read by one 8-byte load per poll (one L2
+// round trip, not two in a row); the time bound is read every 16th poll.
+// (Four polls in flight at once, 30 ns apart, were slower: 139 -> 144 us
+// per run of the benchmark circuit.)
 __device__ __forceinline__ bool grid_wait_relaxed(DevState *ds, unsigned int target, uint64_t spin_ns) {
+    static_assert(offsetof(DevState, bar_abort) == offsetof(DevState, bar_count) + 4, "count, abort adjacent");
+    static_assert(offsetof(DevState, bar_count) % 8 == 0, "count 8-byte aligned");
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         int ok = 1;
         const unsigned long long t0 = gtimer();
-        while (true) {
-            const unsigned int v = ld_relaxed_u32(&ds->bar_count);
+        for (unsigned int it = 1;; ++it) {
+            unsigned int v, ab;
+            asm volatile("ld.relaxed.gpu.global.v2.u32 {%0, %1}, [%2];" : "=r"(v), "=r"(ab) : "l"(&ds->bar_count) : "memory");
             if ((int)(v - target) >= 0) break;
-            if (ld_relaxed_u32(&ds->bar_abort)) { ok = 0; break; }
-            if (gtimer() - t0 > spin_ns) {
+            if (ab) { ok = 0; break; }
+            if ((it & 15) == 0 && gtimer() - t0 > spin_ns) {
                 atomicOr(&ds->err_flags, ERR_TIMEOUT);
                 atomicExch(&ds->bar_abort, 1u);
                 ok = 0;
@@ -432,10 +455,16 @@ template <class F, int NP> constexpr size_t fused_smem(int block) {
 constexpr int DF_TAG_SHIFT = 61;
 
 __device__ __forceinline__ void df_st2(uint64_t *p, uint64_t a, uint64_t b) {
-    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+    asm volatile("st.relaxed.gpu.global.L2::cache_hint.v2.u64 [%0], {%1, %2}, %3;" ::"l"(p), "l"(a), "l"(b),
+                 "l"(l2_evict_last()) : "memory");
 }
 __device__ __forceinline__ void df_ld2(const uint64_t *p, uint64_t &a, uint64_t &b) {
-    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;" : "=l"(a), "=l"(b) : "l"(p),
+                 "l"(l2_evict_last()) : "memory");
+}
+// A party-major output share, read by nobody during a tagged run.
+__device__ __forceinline__ void st_first(uint64_t *p, uint64_t v) {
+    asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(l2_evict_first()) : "memory");
 }
 
 // Issues the loads of the operand record of wire w (its first use waits).
@@ -576,8 +605,8 @@ __device__ __forceinline__ bool df_gate(const DagArgs<F61> &a, const LayerRow &L
     const uint32_t out = rec.z;
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-        F::st(a.wv + i * a.ws + out, z[i]);
-        F::st(a.wm + i * a.ws + out, gz[i]);
+        st_first(a.wv + i * a.ws + out, z[i]);
+        st_first(a.wm + i * a.ws + out, gz[i]);
     }
     df_store<NP>(a.mir, out, tag, z, gz);
     return true;
