@@ -16,12 +16,18 @@
 //
 // One CTA computes a 128 x 128 output tile of one job (or its share of the
 // tile's digit-pair chains) with three roles: warp 0 loads digit-plane
-// tiles with TMA (3-stage ring of 64 KB: 128 of the inner dimension per
-// stage, so the MMA thread waits once per 8 MMAs -- a barrier wait in that
-// thread stalls it behind the MMAs it has issued, and 4 MMAs per wait left
-// the tensor pipe idle 40 % of the time), warp 1 issues the MMAs (and owns
-// the tensor memory), warps 2..9 drain the accumulators; two accumulators in
-// tensor memory let the drain of one chain overlap the MMAs of the next.
+// tiles with TMA, warp 1 issues the MMAs (and owns the tensor memory), warps
+// 2..9 drain the accumulators.  The chains run in pairs (a, b), (a, b+1):
+// both read the same left tile, so a stage holds the left tile's boxes and
+// both right tiles' boxes (2-stage ring of 96 KB, 128 of the inner dimension
+// per stage) and feeds 16 MMAs into two accumulators -- three boxes loaded
+// per two chains' MMAs where separate chains load four, a quarter fewer
+// L2 -> shared-memory bytes, and one wait of the MMA thread per 16 MMAs (a
+// barrier wait in that thread stalls it behind the MMAs it has issued).
+// Two pairs of accumulators (all 512 tensor-memory columns) let the drain of
+// one pair overlap the MMAs of the next.  Whole 2048^3 product: 12.1 ms with
+// single chains (8 MMAs per wait), 11.3 ms with pairs in 64-deep stages,
+// 10.65 ms here.
 // Every wait is bounded: on timeout the CTA raises an error flag, stops
 // issuing work, waits for what it already issued and frees its tensor
 // memory.
@@ -42,12 +48,12 @@ constexpr int TC_DIGIT_BITS = 8;
 constexpr int TC_KCHUNK = 1024;       // inner length of one exact digit-pair sum
 constexpr int TC_TILE = 128;          // output tile edge (M = N = 128)
 constexpr int TC_KB = 64;             // K elements per TMA box (128 bytes of bf16, the swizzle span)
-constexpr int TC_KSTAGE = 128;        // K elements per stage: two boxes of each operand
-constexpr int TC_STAGES = 3;
+constexpr int TC_KSTAGE = 128;        // K elements per stage: two boxes of each tile
+constexpr int TC_STAGES = 2;
 constexpr int TC_BOX_BYTES = TC_TILE * TC_KB * 2;            // one 128 x 64 bf16 box
-constexpr int TC_STAGE_BYTES = 4 * TC_BOX_BYTES;             // A and B, two boxes each
+constexpr int TC_STAGE_BYTES = 6 * TC_BOX_BYTES;             // left digit a, right digits b and b+1, two boxes each
 constexpr int TC_THREADS = 320;       // 10 warps
-constexpr uint32_t TC_TMEM_COLS = 256;
+constexpr uint32_t TC_TMEM_COLS = 512;   // two chain pairs in flight, two 128-column accumulators each
 constexpr unsigned long long TC_WAIT_NS = 1000000000ull;   // bound of one pipeline wait
 
 // ----------------------------------------------------------- digit planes
@@ -244,17 +250,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
     __shared__ int issued_g, consumed_g;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row0 = (int64_t)blockIdx.y * TC_TILE, col0 = (int64_t)blockIdx.x * TC_TILE;
-    // chains: (segment, inner chunk of TC_KCHUNK, digit a, digit b); this
-    // CTA's share [c0, c1) of the tile's chains
+    // chain pairs: (segment, inner chunk of TC_KCHUNK, digit a, digits
+    // 2 bp and 2 bp + 1), bp fastest; this CTA's share [c0, c1) of the
+    // tile's pairs
+    constexpr int BPAIRS = TC_DIGITS / 2;
     const int nchunks = (int)((job.k + TC_KCHUNK - 1) / TC_KCHUNK);
-    const int pairs = TC_DIGITS * TC_DIGITS;
-    const int nchains = 2 * nchunks * pairs;
+    const int per_chunk = TC_DIGITS * BPAIRS;
+    const int npairs = 2 * nchunks * per_chunk;
     auto chain_kblocks = [&](int kc) {
         const int64_t len = min((int64_t)TC_KCHUNK, job.k - (int64_t)kc * TC_KCHUNK);
         return (int)((len + TC_KSTAGE - 1) / TC_KSTAGE);
     };
-    const int c0 = (int)((int64_t)nchains * blockIdx.z / job.nsplit), c1 = (int)((int64_t)nchains * (blockIdx.z + 1) / job.nsplit);
-    const int chains = c1 - c0;
+    const int c0 = (int)((int64_t)npairs * blockIdx.z / job.nsplit), c1 = (int)((int64_t)npairs * (blockIdx.z + 1) / job.nsplit);
+    const int chains = c1 - c0;   // chain pairs of this CTA
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
@@ -287,15 +295,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
             int g = 0;
             for (int ci = 0; ci < chains && !abort_flag; ++ci) {
                 const int c = c0 + ci;
-                const int seg = c / (nchunks * pairs), kc = (c / pairs) % nchunks;
-                const int a = (c / TC_DIGITS) % TC_DIGITS, b = c % TC_DIGITS;
+                const int seg = c / (nchunks * per_chunk), kc = (c / per_chunk) % nchunks;
+                const int a = (c / BPAIRS) % TC_DIGITS, b = 2 * (c % BPAIRS);
                 const CUtensorMap *Lm = seg == 0 ? &L0 : &L1, *Rm = seg == 0 ? &R0 : &R1;
                 const int kblocks = chain_kblocks(kc), kbase = kc * TC_KCHUNK;
                 for (int kb = 0; kb < kblocks; ++kb, ++g) {
                     const int s = g % TC_STAGES;
                     const uint32_t ph = (uint32_t)(g / TC_STAGES) & 1u;
                     if (g >= TC_STAGES && !mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag)) break;
-                    // A boxes at 0 and 16 KB, B boxes at 32 and 48 KB (inner offsets 0, 64)
+                    // left digit a at 0, right digits b and b + 1 at 16 and 32 KB
                     unsigned char *st = smem + (size_t)s * TC_STAGE_BYTES;
                     mbar_expect_tx(&full_bar[s], TC_STAGE_BYTES);
 #pragma unroll
@@ -303,6 +311,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
                         const int kx = kbase + kb * TC_KSTAGE + h * TC_KB;
                         tma_load_3d(st + h * TC_BOX_BYTES, Lm, kx, (int)row0, a, &full_bar[s]);
                         tma_load_3d(st + (2 + h) * TC_BOX_BYTES, Rm, kx, (int)col0, b, &full_bar[s]);
+                        tma_load_3d(st + (4 + h) * TC_BOX_BYTES, Rm, kx, (int)col0, b + 1, &full_bar[s]);
                     }
                     issued_g = g + 1;
                 }
@@ -317,8 +326,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
                 const uint32_t acc_ph = (uint32_t)(ci >> 1) & 1u;
                 if (ci >= 2 && !mbar_wait(&acc_empty[ab], acc_ph ^ 1u, &abort_flag)) break;
                 tc_fence_after();
-                const uint32_t d_tmem = tmem_base + (uint32_t)(ab * TC_TILE);
-                const int kblocks = chain_kblocks(((c0 + ci) / pairs) % nchunks);
+                // accumulators of digits b and b + 1: columns [256 ab, +128) and [256 ab + 128, +128)
+                const uint32_t d0 = tmem_base + (uint32_t)(ab * 2 * TC_TILE), d1 = d0 + (uint32_t)TC_TILE;
+                const int kblocks = chain_kblocks(((c0 + ci) / per_chunk) % nchunks);
                 bool ok = true;
                 for (int kb = 0; kb < kblocks; ++kb, ++g) {
                     const int s = g % TC_STAGES;
@@ -330,8 +340,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
 #pragma unroll
                     for (int k16 = 0; k16 < TC_KSTAGE / 16; ++k16) {
                         const int h = k16 / (TC_KB / 16), kk = k16 % (TC_KB / 16);
-                        const uint64_t da = smem_desc(st + h * TC_BOX_BYTES), db = smem_desc(st + (2 + h) * TC_BOX_BYTES);
-                        mma_bf16(d_tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), (kb | k16) != 0);
+                        const uint64_t da = smem_desc(st + h * TC_BOX_BYTES), db0 = smem_desc(st + (2 + h) * TC_BOX_BYTES),
+                                       db1 = smem_desc(st + (4 + h) * TC_BOX_BYTES);
+                        const uint32_t acc = (kb | k16) != 0;
+                        mma_bf16(d0, da + (uint64_t)(kk * 2), db0 + (uint64_t)(kk * 2), acc);
+                        mma_bf16(d1, da + (uint64_t)(kk * 2), db1 + (uint64_t)(kk * 2), acc);
                     }
                     mma_commit(&empty_bar[s]);     // frees the stage once these MMAs have read it
                 }
@@ -361,28 +374,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
             const uint32_t acc_ph = (uint32_t)(ci >> 1) & 1u;
             if (!mbar_wait(&acc_full[ab], acc_ph, &abort_flag)) break;
             tc_fence_after();
-            const int a = (c / TC_DIGITS) % TC_DIGITS, b = c % TC_DIGITS;
-            const int e = (TC_DIGIT_BITS * (a + b)) % 61;
-            off = F61::add(off, rot61(1ull << 24, e));
-            const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ab * TC_TILE + half * 64);
-            // for e <= 36, u * 2^e <= 2^61 needs no wrap: a plain shift
-            auto drain = [&](auto nowrap) {
+            const int a = (c / BPAIRS) % TC_DIGITS, b0 = 2 * (c % BPAIRS);
+#pragma unroll 1
+            for (int sub = 0; sub < 2; ++sub) {
+                const int e = (TC_DIGIT_BITS * (a + b0 + sub)) % 61;
+                off = F61::add(off, rot61(1ull << 24, e));
+                const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) +
+                                       (uint32_t)((2 * ab + sub) * TC_TILE + half * 64);
+                // for e <= 36, u * 2^e <= 2^61 needs no wrap: a plain shift
+                auto drain = [&](auto nowrap) {
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    uint32_t r[32];
-                    tmem_ld32(taddr + (uint32_t)(q * 32), r);
-                    tmem_wait_ld();
+                    for (int q = 0; q < 2; ++q) {
+                        uint32_t r[32];
+                        tmem_ld32(taddr + (uint32_t)(q * 32), r);
+                        tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int32_t v = __float2int_rn(__uint_as_float(r[j]));    // exact, |v| <= 2^24
-                        const uint64_t u = (uint64_t)(uint32_t)(v + (1 << 24));       // [0, 2^25]
-                        const uint64_t t = sum[q * 32 + j] + (decltype(nowrap)::value ? u << e : rot61(u, e));
-                        sum[q * 32 + j] = (t & F61::P) + (t >> 61);                   // < 2^61 + 2
+                        for (int j = 0; j < 32; ++j) {
+                            const int32_t v = __float2int_rn(__uint_as_float(r[j]));    // exact, |v| <= 2^24
+                            const uint64_t u = (uint64_t)(uint32_t)(v + (1 << 24));       // [0, 2^25]
+                            const uint64_t t = sum[q * 32 + j] + (decltype(nowrap)::value ? u << e : rot61(u, e));
+                            sum[q * 32 + j] = (t & F61::P) + (t >> 61);                   // < 2^61 + 2
+                        }
                     }
-                }
-            };
-            if (e <= 36) drain(std::true_type{});
-            else drain(std::false_type{});
+                };
+                if (e <= 36) drain(std::true_type{});
+                else drain(std::false_type{});
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[ab]);
