@@ -1212,6 +1212,25 @@ def run_profile(args):
         S.spdz_ctx_destroy(ctx)
     elif args.profile == "beaver127":
         beaver_roofline(torch, S, SH, peaks()[0], N=2**24, calls=args.steps, field=S.SPDZ_F127)
+    elif args.profile == "innerprod61":
+        # p61, 3 parties: 4096 inner products of length 1024 (2^22 terms,
+        # 1 GB of shares and triples read per call), `steps` times
+        n, f, P, L = N_PARTIES, S.SPDZ_F61, 4096, 1024
+        N = P * L
+        ctx = S.spdz_ctx_create(n, f, torch.cuda.current_stream().cuda_stream)
+        ash = SH.zeros(f, n)
+        S.spdz_deal_alpha(ctx, 3, ash)
+        x, y = (SH.alloc(f, n, N) for _ in range(2))
+        S.spdz_deal_shared(ctx, 3, S.SPDZ_KIND_INPUT, 0, 0, N, ash, None, x.buf())
+        S.spdz_deal_shared(ctx, 3, S.SPDZ_KIND_INPUT, 1, 0, N, ash, None, y.buf())
+        zi = SH.alloc(f, n, P)
+        tri = [SH.alloc(f, n, N) for _ in range(3)]
+        for rep in range(args.steps):
+            S.spdz_deal_triples(ctx, 3, rep * N, N, ash, *[t.buf() for t in tri])
+            S.spdz_load_preproc(ctx, ash, *[t.buf() for t in tri], N)
+            S.spdz_innerprod_batch(ctx, x.buf(), y.buf(), zi.buf(), P, L)
+            assert S.spdz_mac_check(ctx)
+        S.spdz_ctx_destroy(ctx)
     elif args.profile == "heavy_small":
         # p127, 3 parties: 2^21 Beaver products, then 2048 inner products of
         # length 1024 (2^21 terms), `steps` times; about 1.8 GB on the device
@@ -1249,7 +1268,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="circuit workload only (skip the other configurations attached to the line)")
     ap.add_argument("--extras-requests", type=int, default=1500, help="serving requests of the attached run")
-    ap.add_argument("--profile", default=None, choices=["dag", "tagged", "beaver", "beaver127", "heavy_small", "matmul", "linear"],
+    ap.add_argument("--profile", default=None, choices=["dag", "tagged", "beaver", "beaver127", "heavy_small", "innerprod61", "matmul", "linear"],
                     help="small run of one kernel for an ncu capture (prints nothing)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

@@ -6,6 +6,7 @@
 // Layout: party-major rows (party i's shares at ptr + i*stride); for p61 a
 // thread moves two consecutive elements with one 128-bit access when every
 // row is 16-byte aligned, for p127 one element per 128-bit access.
+#include <atomic>
 #include <type_traits>
 
 #include "common.cuh"
@@ -150,11 +151,14 @@ __device__ __forceinline__ void beaver_core(const MulArgs<F> &a, int64_t e, int6
 // terms go into exact three-word sums that stay unreduced across every
 // element a thread handles (acc[0] = A, acc[1+i] = S_i); z and gamma(z) are
 // one exact sum each, reduced once.  With sums != nullptr the outputs are not
-// reduced either: they are added to sums[i] / sums[NP + i] (inner products).
+// reduced either: they are added to sums[i] / sums[NP + i] (inner products),
+// without the eps delta terms (party 0's value, alpha_i eps delta in every
+// MAC share), whose sum goes to *sde for one product per party at the end.
 template <int NP>
 __device__ __forceinline__ void beaver_core127(const MulArgs<F127> &a, int64_t e, uint64_t key,
                                                const u128v (&alpha)[NP], W127 (&acc)[NP + 1], u128v (&z)[NP],
-                                               u128v (&gz)[NP], u128v &eps, u128v &dlt, W127 *sums) {
+                                               u128v (&gz)[NP], u128v &eps, u128v &dlt, W127 *sums,
+                                               W127 *sde = nullptr) {
     using F = F127;
     u128v av[NP], bv[NP];
     eps = dlt = F::zero();
@@ -188,13 +192,18 @@ __device__ __forceinline__ void beaver_core127(const MulArgs<F127> &a, int64_t e
         vld<F, 1, true>(a.am + i * a.as + e, ga);
         vld<F, 1, true>(a.bm + i * a.bs + e, gb);
         vld<F, 1, true>(a.cm + i * a.cs + e, gc);
-        W127 v = W127::prod(eps, bv[i]), m = W127::prod(eps, gb[0]), m2 = W127::prod(alpha[i], de);
+        W127 v = W127::prod(eps, bv[i]), m = W127::prod(eps, gb[0]);
         v.add(W127::prod(dlt, av[i]));
         v.add(c[0]);
-        if (i == 0) v.add(de);
+        if (!sums && i == 0) v.add(de);
         m.add(W127::prod(dlt, ga[0]));
-        m2.add(gc[0]);
-        m.add(m2);
+        if (sums) {
+            m.add(gc[0]);
+        } else {
+            W127 m2 = W127::prod(alpha[i], de);
+            m2.add(gc[0]);
+            m.add(m2);
+        }
         W127 q = W127::prod(re, F::sub(gx[0], ga[0]));
         q.add(W127::prod(rd, F::sub(gy[0], gb[0])));
         acc[1 + i].add(q);
@@ -206,6 +215,7 @@ __device__ __forceinline__ void beaver_core127(const MulArgs<F127> &a, int64_t e
             gz[i] = m.reduce();
         }
     }
+    if (sums) sde->add(de);
 }
 
 template <int NP>
@@ -326,6 +336,121 @@ __global__ void __launch_bounds__(256) k_innerprod(MulArgs<F> a) {
     block_accumulate<F, NP + 1>(acc, a.ds->acc);
 }
 
+// Inner products, p61 and p = 2^32-5: the term's 10 NP words (value and MAC
+// rows of x, y, a, b, c of every party) are copied with cp.async into a
+// thread-private slot of a two-stage shared-memory buffer, the next term's
+// copies issued before the current term's arithmetic, so each thread keeps a
+// term of loads in flight while it computes (the register form issues a
+// term's loads only after the last term's arithmetic: the 128-register
+// budget has no room for two terms; deeper rings measured no faster).  Slots
+// are [stage][word][thread]: a warp's accesses to one word are consecutive,
+// conflict-free.  The MAC shares' alpha_i (eps delta) terms are summed as
+// alpha_i (sum of eps delta) once per product, as the field allows: three
+// fewer products per term at n = 3, the same sums.
+constexpr int IP_BLOCK = 128;
+
+template <class F, int NP> constexpr size_t ip_stage_bytes() {
+    return (size_t)2 * 10 * NP * sizeof(typename F::T) * IP_BLOCK;
+}
+
+__device__ __forceinline__ void cp_async_word(void *smem, const void *gmem, int bytes) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+template <class F, int NP>
+__device__ __forceinline__ void ip_issue(const MulArgs<F> &a, typename F::T *slot, int64_t e) {
+    using T = typename F::T;
+    const T *rows[10] = {a.xv, a.xm, a.yv, a.ym, a.av, a.am, a.bv, a.bm, a.cv, a.cm};
+    const int64_t strides[10] = {a.xs, a.xs, a.ys, a.ys, a.as, a.as, a.bs, a.bs, a.cs, a.cs};
+#pragma unroll
+    for (int i = 0; i < NP; ++i)
+#pragma unroll
+        for (int w = 0; w < 10; ++w)
+            cp_async_word(slot + (i * 10 + w) * IP_BLOCK, rows[w] + i * strides[w] + e, (int)sizeof(T));
+}
+
+template <class F, int NP>
+__global__ void __launch_bounds__(IP_BLOCK) k_innerprod_staged(MulArgs<F> a) {
+    using T = typename F::T;
+    static_assert(ip_stage_bytes<F, NP>() <= 227 * 1024, "buffer exceeds shared memory");
+    extern __shared__ __align__(16) unsigned char ip_smem[];
+    T *const stage0 = reinterpret_cast<T *>(ip_smem) + threadIdx.x;
+    constexpr int W = 10 * NP * IP_BLOCK;   // elements of one stage
+    const uint64_t key = a.ds->key;
+    T alpha[NP], acc[NP + 1];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
+#pragma unroll
+    for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = ((int64_t)gridDim.x * IP_BLOCK) >> 5;
+    const int64_t nit = (a.len + 31) >> 5;
+    int64_t t = (blockIdx.x * (int64_t)IP_BLOCK + threadIdx.x) >> 5;
+    if (t < a.N && lane < a.len) ip_issue<F, NP>(a, stage0, t * a.len + lane);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    int s = 0;
+    for (; t < a.N; t += wstride) {
+        T sz[NP], sg[NP], sde = F::zero();
+#pragma unroll
+        for (int i = 0; i < NP; ++i) sz[i] = sg[i] = F::zero();
+        for (int64_t it = 0; it < nit; ++it) {
+            const int64_t k = it * 32 + lane;
+            // this thread's next term: later in the product, else the first
+            // of the warp's next product
+            const int64_t tn = it + 1 < nit ? t : t + wstride, kn = it + 1 < nit ? k + 32 : lane;
+            if (tn < a.N && kn < a.len) ip_issue<F, NP>(a, stage0 + (s ^ 1) * W, tn * a.len + kn);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+            if (k < a.len) {
+                const T *q = stage0 + s * W;
+                auto word = [&](int i, int w) { return q[(i * 10 + w) * IP_BLOCK]; };
+                T eps = F::zero(), dlt = F::zero();
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    eps = F::add(eps, F::sub(word(i, 0), word(i, 4)));
+                    dlt = F::add(dlt, F::sub(word(i, 2), word(i, 6)));
+                }
+                const T de = F::mul(eps, dlt);
+                sde = F::add(sde, de);
+                const uint64_t j = a.base + 2 * (uint64_t)(t * a.len + k);
+                const T re = Draw<F>::at(key, j), rd = Draw<F>::at(key, j + 1);
+                acc[0] = Fma<F>::f2(acc[0], re, eps, rd, dlt);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    const T av = word(i, 4), am = word(i, 5), bv = word(i, 6), bm = word(i, 7);
+                    sz[i] = Fma<F>::f2(F::add(sz[i], word(i, 8)), eps, bv, dlt, av);
+                    sg[i] = Fma<F>::f2(F::add(sg[i], word(i, 9)), eps, bm, dlt, am);
+                    acc[1 + i] = Fma<F>::f2(acc[1 + i], re, F::sub(word(i, 1), am), rd, F::sub(word(i, 3), bm));
+                }
+            }
+            s ^= 1;
+        }
+        // party 0's value share takes the sum of eps delta, every MAC share
+        // alpha_i times it
+        sz[0] = F::add(sz[0], sde);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) sg[i] = F::add(sg[i], F::mul(alpha[i], sde));
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            sz[i] = warp_sum<F>(sz[i]);
+            sg[i] = warp_sum<F>(sg[i]);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                F::st(a.zv + i * a.zs + t, sz[i]);
+                F::st(a.zm + i * a.zs + t, sg[i]);
+            }
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    block_accumulate<F, NP + 1>(acc, a.ds->acc);
+}
+
 // p127 inner products: the term products' shares are summed unreduced
 // across a lane's terms and reduced once per product before the warp sum.
 // Two CTAs per SM: latency of the lanes' term loads is hidden by more
@@ -342,11 +467,15 @@ __global__ void __launch_bounds__(256, 2) k_innerprod127(MulArgs<F127> a) {
     const int lane = threadIdx.x & 31;
     const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < a.N; t += wstride) {
-        W127 sums[2 * NP];
+        W127 sums[2 * NP], sde;
         for (int64_t k = lane; k < a.len; k += 32) {
             u128v z[NP], gz[NP], eps, dlt;
-            beaver_core127<NP>(a, t * a.len + k, key, alpha, wacc, z, gz, eps, dlt, sums);
+            beaver_core127<NP>(a, t * a.len + k, key, alpha, wacc, z, gz, eps, dlt, sums, &sde);
         }
+        const u128v de = sde.reduce();
+        sums[0].add(de);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) sums[NP + i].add(W127::prod(alpha[i], de));
         u128v sz[NP], sg[NP];
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
@@ -453,14 +582,26 @@ template <class F> static bool host_canonical(const void *k) {
 }
 
 
+// The staged kernel's ring is above the default 48 KB of dynamic shared
+// memory: raise the kernel's limit once per device.
+template <class F, int NP> static void ip_smem_attr(spdz_ctx *ctx, const void *kern, size_t smem) {
+    static std::atomic<uint64_t> done{0};
+    const uint64_t bit = 1ull << (ctx->device & 63);
+    if (done.load(std::memory_order_acquire) & bit) return;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    done.fetch_or(bit, std::memory_order_acq_rel);
+}
+
 template <class F, int NP>
 static void launch_innerprod(spdz_ctx *ctx, const MulArgs<F> &a, int64_t count) {
     if constexpr (std::is_same_v<F, F127>) {
         auto kern = k_innerprod127<NP>;
         kern<<<grid_for(ctx, (const void *)kern, 256, 0, count * 32), 256, 0, ctx->stream>>>(a);
     } else {
-        auto kern = k_innerprod<F, NP>;
-        kern<<<grid_for(ctx, (const void *)kern, 256, 0, count * 32), 256, 0, ctx->stream>>>(a);
+        auto kern = k_innerprod_staged<F, NP>;
+        constexpr size_t smem = ip_stage_bytes<F, NP>();
+        ip_smem_attr<F, NP>(ctx, (const void *)kern, smem);
+        kern<<<grid_for(ctx, (const void *)kern, IP_BLOCK, smem, count * 32), IP_BLOCK, smem, ctx->stream>>>(a);
     }
 }
 

@@ -265,13 +265,42 @@ def test_innerprod_matches_oracle(p, P, L):
         S.spdz_ctx_destroy(ctx)
 
 
-def test_innerprod_full_size_sampled():
+@pytest.mark.parametrize("p,n,P,L", [(O.P61, 2, 300, 65), (O.P61, 5, 41, 97), (O.P61, 8, 23, 40),
+                                     (O.P32, 4, 77, 129), (O.P61, 3, 5000, 33), (O.P32, 2, 4100, 31)])
+def test_innerprod_party_counts_and_wrapping(p, n, P, L):
+    """Inner products for other party counts (the staged kernel's buffer
+    grows with n: at n = 8 one CTA per SM) and with more products than the
+    grid has warps, so each warp's next-term copies cross into its next
+    product; lengths that leave lanes idle in the last step."""
+    seed, chk = 12, 3
+    ctx = ctx_for(n, p)
+    try:
+        dw = DeviceWorld(ctx, p, n, seed, P * L, P * L)
+        S.spdz_set_check_seed(ctx, chk)
+        z = SH.alloc(dw.field, n, P)
+        S.spdz_innerprod_batch(ctx, dw.inputs[0].buf(), dw.inputs[1].buf(), z.buf(), P, L)
+        sig = O.zeros(p, n)
+        assert S.spdz_mac_check(ctx, sig)
+        ow = OracleWorld(p, n, seed, P * L, P * L)
+        (xv, xm, _), (yv, ym, _) = ow.inputs
+        zv, zm, _, _, log = O.innerprod(p, P, L, xv, xm, yv, ym, ow.tri, ow.alpha_sh)
+        _, osig, _, _ = O.mac_check(p, [log], ow.alpha_sh, chk, 0)
+        gv, gm = z.host()
+        assert_equal(gv, zv, "ip val")
+        assert_equal(gm, zm, "ip mac")
+        assert_equal(sig, osig, "sigma")
+    finally:
+        S.spdz_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("p", [O.P127, O.P61])
+def test_innerprod_full_size_sampled(p):
     """The inner-product workload at its full size (16,384 products of
-    length 1024, 3 parties, p = 2^127-1) in one call: sampled products (the
-    first, the last and random ones) against the oracle over each product's
-    own 1024 dealt terms; the check over all 2^25 opened values passes and
-    its sigma sums to zero."""
-    p, n, P, L, seed, chk = O.P127, 3, 16384, 1024, 23, 6
+    length 1024, 3 parties, p = 2^127-1 and 2^61-1) in one call: sampled
+    products (the first, the last and random ones) against the oracle over
+    each product's own 1024 dealt terms; the check over all 2^24 products'
+    opened values passes and its sigma sums to zero."""
+    n, P, L, seed, chk = 3, 16384, 1024, 23, 6
     ctx = ctx_for(n, p)
     try:
         dw = DeviceWorld(ctx, p, n, seed, P * L, P * L)
