@@ -346,7 +346,8 @@ __global__ void __launch_bounds__(256) k_innerprod(MulArgs<F> a) {
 // are [stage][word][thread]: a warp's accesses to one word are consecutive,
 // conflict-free.  The MAC shares' alpha_i (eps delta) terms are summed as
 // alpha_i (sum of eps delta) once per product, as the field allows: three
-// fewer products per term at n = 3, the same sums.
+// fewer products per term at n = 3, the same sums; every sum is kept exact
+// and reduced once (IpSum).
 constexpr int IP_BLOCK = 128;
 
 template <class F, int NP> constexpr size_t ip_stage_bytes() {
@@ -373,19 +374,42 @@ __device__ __forceinline__ void ip_issue(const MulArgs<F> &a, typename F::T *slo
             cp_async_word(slot + (i * 10 + w) * IP_BLOCK, rows[w] + i * strides[w] + e, (int)sizeof(T));
 }
 
+// Exact sums of the inner products' term products, reduced once per product
+// (the term sums) or once per thread (the check sums): p61 in three words
+// (S61); p = 2^32-5 as 128-bit sums of 64-bit products, with 2^64 == 25.
+// lsub(a, b) is a value congruent to a - b that mac accepts.
+template <class F> struct IpSum;
+template <> struct IpSum<F61> {
+    S61 s;
+    __device__ __forceinline__ void add(uint64_t c) { s.add(c); }
+    __device__ __forceinline__ void mac(uint64_t a, uint64_t b) { s.mac(a, b); }
+    __device__ __forceinline__ uint64_t get() const { return s.reduce(); }
+    __device__ __forceinline__ static uint64_t lsub(uint64_t a, uint64_t b) { return a + F61::P - b; }
+};
+template <> struct IpSum<F32> {
+    uint64_t lo = 0, hi = 0;   // hi counts 2^64 carries: below 2^59 for any input that fits memory
+    __device__ __forceinline__ void add64(uint64_t v) {
+        asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(lo), "+l"(hi) : "l"(v));
+    }
+    __device__ __forceinline__ void add(uint32_t c) { add64(c); }
+    __device__ __forceinline__ void mac(uint32_t a, uint32_t b) { add64((uint64_t)a * b); }
+    __device__ __forceinline__ uint32_t get() const { return F32::add(F32::reduce64(lo), F32::reduce64(25 * hi)); }
+    __device__ __forceinline__ static uint32_t lsub(uint32_t a, uint32_t b) { return F32::sub(a, b); }
+};
+
 template <class F, int NP>
 __global__ void __launch_bounds__(IP_BLOCK) k_innerprod_staged(MulArgs<F> a) {
     using T = typename F::T;
+    using Sum = IpSum<F>;
     static_assert(ip_stage_bytes<F, NP>() <= 227 * 1024, "buffer exceeds shared memory");
     extern __shared__ __align__(16) unsigned char ip_smem[];
     T *const stage0 = reinterpret_cast<T *>(ip_smem) + threadIdx.x;
     constexpr int W = 10 * NP * IP_BLOCK;   // elements of one stage
     const uint64_t key = a.ds->key;
-    T alpha[NP], acc[NP + 1];
+    T alpha[NP];
+    Sum acc[NP + 1];
 #pragma unroll
     for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
-#pragma unroll
-    for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
     const int lane = threadIdx.x & 31;
     const int64_t wstride = ((int64_t)gridDim.x * IP_BLOCK) >> 5;
     const int64_t nit = (a.len + 31) >> 5;
@@ -394,9 +418,7 @@ __global__ void __launch_bounds__(IP_BLOCK) k_innerprod_staged(MulArgs<F> a) {
     asm volatile("cp.async.commit_group;" ::: "memory");
     int s = 0;
     for (; t < a.N; t += wstride) {
-        T sz[NP], sg[NP], sde = F::zero();
-#pragma unroll
-        for (int i = 0; i < NP; ++i) sz[i] = sg[i] = F::zero();
+        Sum sz[NP], sg[NP], sde;
         for (int64_t it = 0; it < nit; ++it) {
             const int64_t k = it * 32 + lane;
             // this thread's next term: later in the product, else the first
@@ -414,41 +436,54 @@ __global__ void __launch_bounds__(IP_BLOCK) k_innerprod_staged(MulArgs<F> a) {
                     eps = F::add(eps, F::sub(word(i, 0), word(i, 4)));
                     dlt = F::add(dlt, F::sub(word(i, 2), word(i, 6)));
                 }
-                const T de = F::mul(eps, dlt);
-                sde = F::add(sde, de);
+                sde.mac(eps, dlt);
                 const uint64_t j = a.base + 2 * (uint64_t)(t * a.len + k);
                 const T re = Draw<F>::at(key, j), rd = Draw<F>::at(key, j + 1);
-                acc[0] = Fma<F>::f2(acc[0], re, eps, rd, dlt);
+                acc[0].mac(re, eps);
+                acc[0].mac(rd, dlt);
 #pragma unroll
                 for (int i = 0; i < NP; ++i) {
-                    const T av = word(i, 4), am = word(i, 5), bv = word(i, 6), bm = word(i, 7);
-                    sz[i] = Fma<F>::f2(F::add(sz[i], word(i, 8)), eps, bv, dlt, av);
-                    sg[i] = Fma<F>::f2(F::add(sg[i], word(i, 9)), eps, bm, dlt, am);
-                    acc[1 + i] = Fma<F>::f2(acc[1 + i], re, F::sub(word(i, 1), am), rd, F::sub(word(i, 3), bm));
+                    const T am = word(i, 5), bm = word(i, 7);
+                    sz[i].add(word(i, 8));
+                    sz[i].mac(eps, word(i, 6));
+                    sz[i].mac(dlt, word(i, 4));
+                    sg[i].add(word(i, 9));
+                    sg[i].mac(eps, bm);
+                    sg[i].mac(dlt, am);
+                    acc[1 + i].mac(re, Sum::lsub(word(i, 1), am));
+                    acc[1 + i].mac(rd, Sum::lsub(word(i, 3), bm));
                 }
             }
             s ^= 1;
         }
         // party 0's value share takes the sum of eps delta, every MAC share
         // alpha_i times it
-        sz[0] = F::add(sz[0], sde);
-#pragma unroll
-        for (int i = 0; i < NP; ++i) sg[i] = F::add(sg[i], F::mul(alpha[i], sde));
+        const T de = sde.get();
+        T vz[NP], vg[NP];
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
-            sz[i] = warp_sum<F>(sz[i]);
-            sg[i] = warp_sum<F>(sg[i]);
+            vz[i] = sz[i].get();
+            vg[i] = F::add(sg[i].get(), F::mul(alpha[i], de));
+        }
+        vz[0] = F::add(vz[0], de);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            vz[i] = warp_sum<F>(vz[i]);
+            vg[i] = warp_sum<F>(vg[i]);
         }
         if (lane == 0) {
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
-                F::st(a.zv + i * a.zs + t, sz[i]);
-                F::st(a.zm + i * a.zs + t, sg[i]);
+                F::st(a.zv + i * a.zs + t, vz[i]);
+                F::st(a.zm + i * a.zs + t, vg[i]);
             }
         }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
-    block_accumulate<F, NP + 1>(acc, a.ds->acc);
+    T vacc[NP + 1];
+#pragma unroll
+    for (int k = 0; k < NP + 1; ++k) vacc[k] = acc[k].get();
+    block_accumulate<F, NP + 1>(vacc, a.ds->acc);
 }
 
 // p127 inner products: the term products' shares are summed unreduced

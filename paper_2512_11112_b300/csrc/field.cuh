@@ -105,6 +105,29 @@ struct W61 {
     }
 };
 
+// An exact sum of many p61 products, reduced once: three 64-bit words hold
+// up to 2^64 products of operands below 2^64.  With 2^61 == 1 (mod p),
+// w1 2^64 == 8 w1 and w2 2^128 == 64 w2, each split at bit 61.
+struct S61 {
+    uint64_t w0 = 0, w1 = 0, w2 = 0;
+    __device__ __forceinline__ void add(uint64_t a) {
+        asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, 0;\n\taddc.u64 %2, %2, 0;"
+            : "+l"(w0), "+l"(w1), "+l"(w2) : "l"(a));
+    }
+    __device__ __forceinline__ void mac(uint64_t a, uint64_t b) {
+        const uint64_t pl = a * b, ph = __umul64hi(a, b);
+        asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, 0;"
+            : "+l"(w0), "+l"(w1), "+l"(w2) : "l"(pl), "l"(ph));
+    }
+    __device__ __forceinline__ uint64_t reduce() const {
+        // six pieces, each below 2^61: the sum is below 2^64
+        uint64_t s = (w0 & F61::P) + (w0 >> 61) + ((w1 << 3) & F61::P) + (w1 >> 58) + ((w2 << 6) & F61::P) +
+                     (w2 >> 55);
+        s = (s & F61::P) + (s >> 61);
+        return s >= F61::P ? s - F61::P : s;
+    }
+};
+
 // c + a1 b1 + a2 b2 (+ a3 b3) mod p with one reduction where the field allows
 // it: p61 sums the 122-bit products exactly in 128 bits (below 2^124);
 // p = 2^32-5 folds each 64-bit product to 5 hi + lo (below 2^35) and sums in
