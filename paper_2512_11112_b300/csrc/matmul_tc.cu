@@ -71,50 +71,61 @@ __device__ __forceinline__ void balanced_digits(uint64_t x, float (&d)[TC_DIGITS
     d[TC_DIGITS - 1] = (float)t;
 }
 
-// Row-major rows x cols matrix -> planes [9][rows][colsp] (bf16), columns
-// cols .. colsp-1 zero (colsp: cols rounded up for 16-byte TMA strides).
+// Row-major rows x cols matrix -> planes [TC_DIGITS][rows][colsp] (bf16),
+// columns cols .. colsp-1 zero (colsp: cols rounded up to a multiple of 8 for
+// 16-byte TMA strides).  A block walks whole rows, a thread four consecutive
+// columns: one 8-byte store of four digits per plane, no index division.
 __global__ void k_digits_rowmajor(const uint64_t *x, int64_t rows, int64_t cols, int64_t ld, int64_t colsp,
                                   __nv_bfloat16 *planes) {
     const int64_t total = rows * colsp;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = e / colsp, c = e % colsp;
-        float d[TC_DIGITS];
-        if (c < cols) {
-            balanced_digits(x[r * ld + c], d);
-        } else {
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const uint64_t *xr = x + r * ld;
+        for (int64_t c0 = 4 * (int64_t)threadIdx.x; c0 < colsp; c0 += 4 * (int64_t)blockDim.x) {
+            float d[4][TC_DIGITS];
 #pragma unroll
-            for (int j = 0; j < TC_DIGITS; ++j) d[j] = 0.f;
+            for (int u = 0; u < 4; ++u) {
+                if (c0 + u < cols) {
+                    balanced_digits(xr[c0 + u], d[u]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < TC_DIGITS; ++j) d[u][j] = 0.f;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < TC_DIGITS; ++j) {
+                const __nv_bfloat162 lo = __floats2bfloat162_rn(d[0][j], d[1][j]), hi = __floats2bfloat162_rn(d[2][j], d[3][j]);
+                uint2 w;
+                w.x = *reinterpret_cast<const uint32_t *>(&lo);
+                w.y = *reinterpret_cast<const uint32_t *>(&hi);
+                *reinterpret_cast<uint2 *>(planes + j * total + r * colsp + c0) = w;
+            }
         }
-#pragma unroll
-        for (int j = 0; j < TC_DIGITS; ++j) planes[j * total + e] = __float2bfloat16_rn(d[j]);
     }
 }
 
-// Row-major rows x cols matrix -> transposed planes [9][cols][rowsp]
-// (bf16), columns rows .. rowsp-1 of each output row zero, through 32 x 32
-// shared-memory tiles.
+// Row-major rows x cols matrix -> transposed planes [TC_DIGITS][cols][rowsp]
+// (bf16), columns rows .. rowsp-1 of each output row zero (rowsp: a multiple
+// of 8), through 64 x 32 shared-memory tiles: a thread writes two
+// consecutive output columns (4-byte stores, 128 bytes per warp and plane).
 __global__ void k_digits_transposed(const uint64_t *x, int64_t rows, int64_t cols, int64_t ld, int64_t rowsp,
                                     __nv_bfloat16 *planes) {
-    __shared__ uint64_t tile[32][33];
-    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
-    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    __shared__ uint64_t tile[64][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 64, c0 = (int64_t)blockIdx.x * 32;
+    for (int i = threadIdx.y; i < 64; i += blockDim.y) {
         const int64_t r = r0 + i, c = c0 + threadIdx.x;
         tile[i][threadIdx.x] = (r < rows && c < cols) ? x[r * ld + c] : 0;
     }
     __syncthreads();
     const int64_t total = cols * rowsp;
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-        const int64_t c = c0 + i, r = r0 + threadIdx.x;   // output row c, column r
+        const int64_t c = c0 + i, r = r0 + 2 * threadIdx.x;   // output row c, columns r and r + 1
         if (c < cols && r < rowsp) {
-            float d[TC_DIGITS];
-            if (r < rows) {
-                balanced_digits(tile[threadIdx.x][i], d);
-            } else {
+            float d0[TC_DIGITS], d1[TC_DIGITS];
+            balanced_digits(tile[2 * threadIdx.x][i], d0);       // rows past the matrix read 0: all-zero digits
+            balanced_digits(tile[2 * threadIdx.x + 1][i], d1);
 #pragma unroll
-                for (int j = 0; j < TC_DIGITS; ++j) d[j] = 0.f;
-            }
-#pragma unroll
-            for (int j = 0; j < TC_DIGITS; ++j) planes[j * total + c * rowsp + r] = __float2bfloat16_rn(d[j]);
+            for (int j = 0; j < TC_DIGITS; ++j)
+                *reinterpret_cast<__nv_bfloat162 *>(planes + j * total + c * rowsp + r) = __floats2bfloat162_rn(d0[j], d1[j]);
         }
     }
 }
@@ -445,15 +456,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
     }
 }
 
-// out = add + sum of the nsplit partial tiles, mod p (elementwise).
+// out = add + sum of the nsplit partial tiles, mod p (elementwise).  A block
+// walks whole rows (no index division); the partials are read once.
 __global__ void k_tc_combine(const uint64_t *part, int nsplit, int64_t m, int64_t n, const uint64_t *add, uint64_t *out,
                              int64_t ldo) {
-    const int64_t total = m * n, stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-        const int64_t r = i / n, c = i - r * n;
-        uint64_t v = add ? add[r * ldo + c] : 0;
-        for (int q = 0; q < nsplit; ++q) v = F61::add(v, __ldcs(reinterpret_cast<const unsigned long long *>(part) + q * total + i));
-        out[r * ldo + c] = v;
+    const int64_t total = m * n;
+    for (int64_t r = blockIdx.x; r < m; r += gridDim.x) {
+        const unsigned long long *pr = reinterpret_cast<const unsigned long long *>(part) + r * n;
+#pragma unroll 4
+        for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+            uint64_t v = add ? add[r * ldo + c] : 0;
+            for (int q = 0; q < nsplit; ++q) v = F61::add(v, __ldcs(pr + q * total + c));
+            out[r * ldo + c] = v;
+        }
     }
 }
 
@@ -544,7 +559,7 @@ int matmul_tensor(spdz_ctx *ctx, const uint64_t *E, const uint64_t *Fm, const ui
             k_digits_rowmajor<<<gb, 256, 0, ctx->stream>>>((const uint64_t *)(w == 0 ? A->val : A->mac) + (int64_t)i * A->stride,
                                                            m, k, k, kp, (__nv_bfloat16 *)((unsigned char *)dA + plane_l * (w * NPn + i)));
     // the transposed kernel covers output columns 0 .. kp-1 (padding included)
-    dim3 tg((unsigned)((n + 31) / 32), (unsigned)((kp + 31) / 32)), tb(32, 8);
+    dim3 tg((unsigned)((n + 31) / 32), (unsigned)((kp + 63) / 64)), tb(32, 8);
     k_digits_transposed<<<tg, tb, 0, ctx->stream>>>(Fm, k, n, n, kp, dF);
     for (int j = 0; j < 2 * NPn; ++j)
         k_digits_transposed<<<tg, tb, 0, ctx->stream>>>(Rfold + (int64_t)j * k * n, k, n, n, kp,
