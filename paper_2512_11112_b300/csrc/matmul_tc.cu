@@ -18,16 +18,17 @@
 // tile's digit-pair chains) with three roles: warp 0 loads digit-plane
 // tiles with TMA, warp 1 issues the MMAs (and owns the tensor memory), warps
 // 2..9 drain the accumulators.  The chains run in pairs (a, b), (a, b+1):
-// both read the same left tile, so a stage holds the left tile's boxes and
-// both right tiles' boxes (2-stage ring of 96 KB, 128 of the inner dimension
-// per stage) and feeds 16 MMAs into two accumulators -- three boxes loaded
-// per two chains' MMAs where separate chains load four, a quarter fewer
-// L2 -> shared-memory bytes, and one wait of the MMA thread per 16 MMAs (a
-// barrier wait in that thread stalls it behind the MMAs it has issued).
-// Two pairs of accumulators (all 512 tensor-memory columns) let the drain of
-// one pair overlap the MMAs of the next.  Whole 2048^3 product: 12.1 ms with
-// single chains (8 MMAs per wait), 11.3 ms with pairs in 64-deep stages,
-// 10.65 ms here.
+// both read the same left tile, so a stage holds the left tile's box and
+// both right tiles' boxes side by side -- three boxes loaded per two chains'
+// MMAs where separate chains load four, a quarter fewer L2 -> shared-memory
+// bytes -- and the two right boxes form one 256-row operand: one M = 128,
+// N = 256 MMA per 16 of the inner dimension writes both chains'
+// accumulators.  A 4-stage ring of 48 KB (64 of the inner dimension per
+// stage, 4 MMAs per wait) keeps three stages of loads in flight.  Two pairs
+// of accumulators (all 512 tensor-memory columns) let the drain of one pair
+// overlap the MMAs of the next.  Whole 2048^3 product: 12.1 ms with single
+// chains, 10.65 ms with pairs as two N = 128 MMAs in a 2-stage ring of
+// 96 KB, 9.5 ms here.
 // Every wait is bounded: on timeout the CTA raises an error flag, stops
 // issuing work, waits for what it already issued and frees its tensor
 // memory.
@@ -48,10 +49,13 @@ constexpr int TC_DIGIT_BITS = 8;
 constexpr int TC_KCHUNK = 1024;       // inner length of one exact digit-pair sum
 constexpr int TC_TILE = 128;          // output tile edge (M = N = 128)
 constexpr int TC_KB = 64;             // K elements per TMA box (128 bytes of bf16, the swizzle span)
-constexpr int TC_KSTAGE = 128;        // K elements per stage: two boxes of each tile
-constexpr int TC_STAGES = 2;
+constexpr int TC_KSTAGE = 64;         // K elements per stage: TC_NH boxes of each tile
+constexpr int TC_STAGES = 4;
+constexpr int TC_NH = TC_KSTAGE / TC_KB;                      // 64-element halves of a stage
 constexpr int TC_BOX_BYTES = TC_TILE * TC_KB * 2;            // one 128 x 64 bf16 box
-constexpr int TC_STAGE_BYTES = 6 * TC_BOX_BYTES;             // left digit a, right digits b and b+1, two boxes each
+// A stage: the left digit a's boxes (halves 0 .. TC_NH-1), then per half the
+// right digits b and b+1 side by side, one 256-row operand of one MMA
+constexpr int TC_STAGE_BYTES = 3 * TC_NH * TC_BOX_BYTES;
 constexpr int TC_THREADS = 320;       // 10 warps
 constexpr uint32_t TC_TMEM_COLS = 512;   // two chain pairs in flight, two 128-column accumulators each
 constexpr unsigned long long TC_WAIT_NS = 1000000000ull;   // bound of one pipeline wait
@@ -199,9 +203,12 @@ __device__ __forceinline__ uint64_t smem_desc(const void *p) {
     return d;
 }
 
-// bf16 x bf16 -> f32, A and B K-major, M = N = 128.
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_TILE >> 3) << 17) |
+// bf16 x bf16 -> f32, A and B K-major, M = 128, N = 256: the two right
+// digits b and b+1 of a chain pair as one 256-row operand, their
+// accumulators side by side in tensor memory (256 columns).
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * TC_TILE) >> 3) << 17) |
                               ((uint32_t)(TC_TILE >> 4) << 24);
+static_assert(2 * TC_TILE <= 256, "N of one MMA is at most 256");
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
@@ -314,15 +321,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
                     const int s = g % TC_STAGES;
                     const uint32_t ph = (uint32_t)(g / TC_STAGES) & 1u;
                     if (g >= TC_STAGES && !mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag)) break;
-                    // left digit a at 0, right digits b and b + 1 at 16 and 32 KB
+                    // left digit a's halves first; per half h the right
+                    // digits b and b + 1 in adjacent boxes
                     unsigned char *st = smem + (size_t)s * TC_STAGE_BYTES;
                     mbar_expect_tx(&full_bar[s], TC_STAGE_BYTES);
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
+                    for (int h = 0; h < TC_NH; ++h) {
                         const int kx = kbase + kb * TC_KSTAGE + h * TC_KB;
                         tma_load_3d(st + h * TC_BOX_BYTES, Lm, kx, (int)row0, a, &full_bar[s]);
-                        tma_load_3d(st + (2 + h) * TC_BOX_BYTES, Rm, kx, (int)col0, b, &full_bar[s]);
-                        tma_load_3d(st + (4 + h) * TC_BOX_BYTES, Rm, kx, (int)col0, b + 1, &full_bar[s]);
+                        tma_load_3d(st + (TC_NH + 2 * h) * TC_BOX_BYTES, Rm, kx, (int)col0, b, &full_bar[s]);
+                        tma_load_3d(st + (TC_NH + 2 * h + 1) * TC_BOX_BYTES, Rm, kx, (int)col0, b + 1, &full_bar[s]);
                     }
                     issued_g = g + 1;
                 }
@@ -337,8 +345,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
                 const uint32_t acc_ph = (uint32_t)(ci >> 1) & 1u;
                 if (ci >= 2 && !mbar_wait(&acc_empty[ab], acc_ph ^ 1u, &abort_flag)) break;
                 tc_fence_after();
-                // accumulators of digits b and b + 1: columns [256 ab, +128) and [256 ab + 128, +128)
-                const uint32_t d0 = tmem_base + (uint32_t)(ab * 2 * TC_TILE), d1 = d0 + (uint32_t)TC_TILE;
+                // accumulators of digits b and b + 1: columns [256 ab, +128) and [256 ab + 128, +128),
+                // written by one N = 256 MMA at d0
+                const uint32_t d0 = tmem_base + (uint32_t)(ab * 2 * TC_TILE);
                 const int kblocks = chain_kblocks(((c0 + ci) / per_chunk) % nchunks);
                 bool ok = true;
                 for (int kb = 0; kb < kblocks; ++kb, ++g) {
@@ -351,11 +360,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
 #pragma unroll
                     for (int k16 = 0; k16 < TC_KSTAGE / 16; ++k16) {
                         const int h = k16 / (TC_KB / 16), kk = k16 % (TC_KB / 16);
-                        const uint64_t da = smem_desc(st + h * TC_BOX_BYTES), db0 = smem_desc(st + (2 + h) * TC_BOX_BYTES),
-                                       db1 = smem_desc(st + (4 + h) * TC_BOX_BYTES);
+                        const uint64_t da = smem_desc(st + h * TC_BOX_BYTES),
+                                       db = smem_desc(st + (TC_NH + 2 * h) * TC_BOX_BYTES);
                         const uint32_t acc = (kb | k16) != 0;
-                        mma_bf16(d0, da + (uint64_t)(kk * 2), db0 + (uint64_t)(kk * 2), acc);
-                        mma_bf16(d1, da + (uint64_t)(kk * 2), db1 + (uint64_t)(kk * 2), acc);
+                        // one MMA for both chains: rows 0-127 of the right
+                        // operand are digit b (into d0), 128-255 digit b+1 (d1)
+                        mma_bf16(d0, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), acc);
                     }
                     mma_commit(&empty_bar[s]);     // frees the stage once these MMAs have read it
                 }
