@@ -76,6 +76,9 @@ def oracle_world(p, n, dout, din, R):
 
 @pytest.mark.parametrize("p,n,dout,din,R", [
     (O.P32, 2, 7, 5, 3), (O.P32, 3, 130, 67, 16), (O.P32, 2, 1, 1, 1), (O.P32, 2, 96, 1000, 32),
+    # the staged two-party row kernel: several rounds of rows per CTA (each
+    # thread's next-step copies cross into its next row), a ragged wide half
+    (O.P32, 2, 5000, 64, 7), (O.P32, 2, 300, 2052, 32),
     (O.P61, 2, 33, 100, 8), (O.P61, 3, 64, 64, 64), (O.P61, 4, 50, 257, 7), (O.P61, 2, 9, 300, 1000),
 ])
 def test_linear_layer_matches_oracle(p, n, dout, din, R):
