@@ -643,7 +643,8 @@ def serve_metrics(count, nshape=64, tight_budget_gb=4):
                 "all_checks_passed": all(r.passed == 1 for r in res),
                 "admission_wait_p99_ms": wait[min(len(wait) - 1, int(0.99 * (len(wait) - 1) + 0.5))] if wait else 0.0,
                 "host_s": {"admit": st.host_admit_s, "tick": st.host_tick_s, "complete": st.host_complete_s,
-                           "idle": st.host_idle_s, "ring_wait": st.host_ring_wait_s}}
+                           "idle": st.host_idle_s, "ring_wait": st.host_ring_wait_s},
+                "device_tick_s": st.device_tick_s, "device_ticks_timed": st.device_ticks_timed}
 
     modes = {"sequential": S.SPDZ_SERVE_SEQUENTIAL, "batched": S.SPDZ_SERVE_BATCHED,
              "heuristic": S.SPDZ_SERVE_HEURISTIC, "learned": S.SPDZ_SERVE_LEARNED}

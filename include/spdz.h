@@ -536,6 +536,10 @@ typedef struct {
     int32_t max_active;
     /* host time of the serving thread by phase (tracing) */
     double host_admit_s, host_tick_s, host_complete_s, host_idle_s, host_ring_wait_s;
+    /* device time of the ticks (events around each tick's launches), over
+       device_ticks_timed ticks */
+    double device_tick_s;
+    int64_t device_ticks_timed;
 } spdz_serve_stats;
 
 /* Creates a stopped server on the current device.  Errors: SPDZ_ERR_ARG,

@@ -59,8 +59,10 @@ struct ReqDev {
     DevState *ds;
 };
 
-struct Tile {
-    int32_t slot, layer, r0, r1;
+// One request's part of a tick: its layer's records [r0, r1) are tiles
+// tile0, tile0 + 1, ... of the tick, 256 records each (the last one short).
+struct TickReq {
+    int32_t slot, layer, r0, r1, tile0, pad;
 };
 
 template <class F>
@@ -81,22 +83,40 @@ __device__ __forceinline__ DagArgs<F> req_args(const ReqDev &R) {
     return a;
 }
 
-// One tick: every tile is <= blockDim.x gates of one layer of one request.
+// One tick: every tile is <= blockDim.x (256) gates of one layer of one
+// request.  The tick's requests (sorted by tile0) are copied into shared
+// memory when they fit (staged != 0), and a tile finds its request by a
+// binary search over tile0.
 template <class F, int NP>
-__global__ void __launch_bounds__(256) k_serve_tick(const ReqDev *reqs, const Tile *tiles, int ntiles) {
+__global__ void __launch_bounds__(256) k_serve_tick(const ReqDev *reqs, const TickReq *treq, int nreq, int ntiles,
+                                                    int staged) {
     using T = typename F::T;
+    extern __shared__ TickReq tq_smem[];
+    const TickReq *tq = treq;
+    if (staged) {
+        for (int j = threadIdx.x; j < nreq; j += blockDim.x) tq_smem[j] = treq[j];
+        __syncthreads();
+        tq = tq_smem;
+    }
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const Tile tl = tiles[t];
-        const DagArgs<F> a = req_args<F>(reqs[tl.slot]);
-        const LayerRow L = load_row(a.lay, tl.layer);
+        int lo = 0, hi = nreq - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tq[mid].tile0 <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const TickReq q = tq[lo];
+        const int32_t r0 = q.r0 + 256 * (t - q.tile0), r1 = min(q.r1, r0 + 256);
+        const DagArgs<F> a = req_args<F>(reqs[q.slot]);
+        const LayerRow L = load_row(a.lay, q.layer);
         const uint64_t key = a.ds->key;
         T alpha[NP], acc[NP + 1];
 #pragma unroll
         for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
 #pragma unroll
         for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
-        const int32_t r = tl.r0 + (int32_t)threadIdx.x;
-        if (r < tl.r1) {
+        const int32_t r = r0 + (int32_t)threadIdx.x;
+        if (r < r1) {
             const int cls = class_of(L, r);
             GateIn<F, NP> g;
             gate_load_direct<F, NP>(a, L, r, cls, 0, g);
@@ -377,11 +397,11 @@ struct spdz_server {
     ReqDev *h_reqs = nullptr;       // pinned mirror
     // tick buffers (ring of pinned host + device tile lists)
     static constexpr int RING = 4;
-    Tile *h_tiles[RING] = {}, *d_tiles[RING] = {};
-    int32_t *h_slots[RING] = {}, *d_slots[RING] = {};
+    // a tick's requests and finishing slots, pinned host and device, at most
+    // max_active requests of each field
+    void *h_tickbuf[RING] = {}, *d_tickbuf[RING] = {};
     cudaEvent_t ring_ev[RING] = {};       // end of the tick that used the slot
     cudaEvent_t ring_start[RING] = {};    // start of its kernels
-    int64_t tile_cap = 0;
     std::map<int64_t, std::unique_ptr<ServeCircuit>> circuits;   // registered, by id
     int64_t next_circuit = 0;
     double tick_us_ema = 0;                // measured duration of one tick (moving average)
@@ -402,6 +422,8 @@ struct spdz_server {
     std::vector<double> lat;
     int64_t st_requests = 0, st_gates = 0, st_ticks = 0, st_cluster = 0;
     double st_dealer_s = 0, st_last_done = 0;
+    double st_tick_dev_s = 0;              // device time of the ticks measured so far
+    int64_t st_tick_timed = 0;
     int st_max_active = 0;
     double h_admit = 0, h_tick = 0, h_done = 0, h_idle = 0, h_ringwait = 0;
 
@@ -679,68 +701,48 @@ void spdz_server::loop() {
                 if (cudaEventElapsedTime(&ms, ring_start[ring], ring_ev[ring]) == cudaSuccess && ms > 0) {
                     tick_us_ema = tick_us_ema == 0 ? ms * 1e3 : 0.9 * tick_us_ema + 0.1 * ms * 1e3;
                     tick_us_min = tick_us_min == 0 ? ms * 1e3 : std::min(tick_us_min, (double)ms * 1e3);
+                    st_tick_dev_s += ms * 1e-3;
+                    ++st_tick_timed;
                 }
+                ring_busy[ring] = 0;
             }
-            int64_t need = 0;
-            for (Live *L : ticking) {
-                const LayerRow &R = L->circ->h_lay[L->next];
-                need += (R.s[5] - R.s[0] + 255) / 256;
-            }
-            if (need > tile_cap) {
-                for (int k = 0; k < RING; ++k) {
-                    if (ring_busy[k]) cudaEventSynchronize(ring_ev[k]);
-                    if (h_tiles[k]) cudaFreeHost(h_tiles[k]);
-                    if (d_tiles[k]) cudaFree(d_tiles[k]);
-                    if (h_slots[k]) cudaFreeHost(h_slots[k]);
-                    if (d_slots[k]) cudaFree(d_slots[k]);
-                    h_tiles[k] = d_tiles[k] = nullptr;
-                    h_slots[k] = d_slots[k] = nullptr;
-                    const int64_t cap = std::max<int64_t>(need * 2, 4096);
-                    if (cudaMallocHost(&h_tiles[k], cap * sizeof(Tile)) != cudaSuccess ||
-                        cudaMalloc(&d_tiles[k], cap * sizeof(Tile)) != cudaSuccess ||
-                        cudaMallocHost(&h_slots[k], (size_t)max_active * sizeof(int32_t) * 2) != cudaSuccess ||
-                        cudaMalloc(&d_slots[k], (size_t)max_active * sizeof(int32_t) * 2) != cudaSuccess) {
-                        rc_fail = SPDZ_ERR_OOM;
-                        break;
-                    }
-                    tile_cap = cap;
-                    ring_busy[k] = 0;
-                }
-                if (rc_fail) break;
-            }
-            Tile *ht = h_tiles[ring];
-            int32_t *hs = h_slots[ring];
-            int nt[2] = {0, 0}, nf[2] = {0, 0};
-            // tiles of each field grouped: p61 first, then p127
-            for (int fld = 0; fld < 2; ++fld) {
-                const int base = fld == 0 ? 0 : nt[0];
-                int cnt = 0;
+            // the tick's requests by field (p61 first, then p127), each with
+            // its first tile index, then the slots of the requests finishing
+            // with this tick: one copy
+            TickReq *ht = reinterpret_cast<TickReq *>(h_tickbuf[ring]);
+            int nq[2] = {0, 0}, nt[2] = {0, 0}, nf[2] = {0, 0};
+            for (int fld = 0; fld < 2; ++fld)
                 for (Live *L : ticking) {
                     if (L->field != fld) continue;
                     const LayerRow &R = L->circ->h_lay[L->next];
-                    for (int32_t r = R.s[0]; r < R.s[5]; r += 256) ht[base + cnt++] = Tile{L->slot, L->next, r, std::min(R.s[5], r + 256)};
+                    ht[nq[0] * fld + nq[fld]++] = TickReq{L->slot, L->next, R.s[0], R.s[5], nt[fld], 0};
+                    nt[fld] += (R.s[5] - R.s[0] + 255) / 256;
                 }
-                nt[fld] = cnt;
-            }
-            // requests finishing with this tick (their last layer)
+            const int nreq = nq[0] + nq[1];
+            int32_t *hs = reinterpret_cast<int32_t *>(ht + nreq);
             for (int fld = 0; fld < 2; ++fld)
                 for (Live *L : ticking)
-                    if (L->field == fld && L->next + 1 == L->depth) hs[(fld == 0 ? 0 : max_active) + nf[fld]++] = L->slot;
-            const int ntot = nt[0] + nt[1];
-            cudaMemcpyAsync(d_tiles[ring], ht, (size_t)ntot * sizeof(Tile), cudaMemcpyHostToDevice, tick_stream);
-            cudaMemcpyAsync(d_slots[ring], hs, (size_t)max_active * 2 * sizeof(int32_t), cudaMemcpyHostToDevice, tick_stream);
+                    if (L->field == fld && L->next + 1 == L->depth) hs[nf[0] * fld + nf[fld]++] = L->slot;
+            const size_t tick_bytes = (size_t)nreq * sizeof(TickReq) + (size_t)(nf[0] + nf[1]) * sizeof(int32_t);
+            cudaMemcpyAsync(d_tickbuf[ring], ht, tick_bytes, cudaMemcpyHostToDevice, tick_stream);
+            const TickReq *dq = reinterpret_cast<const TickReq *>(d_tickbuf[ring]);
+            const int32_t *dslots = reinterpret_cast<const int32_t *>(dq + nreq);
             // the tick must see every request's descriptor and dealt state
             for (Live *L : ticking)
                 if (L->next == 0) cudaStreamWaitEvent(tick_stream, L->dealt, 0);
             cudaEventRecord(ring_start[ring], tick_stream);
             for (int fld = 0; fld < 2; ++fld) {
                 if (nt[fld] == 0) continue;
-                const Tile *dt = d_tiles[ring] + (fld == 0 ? 0 : nt[0]);
+                const TickReq *dqf = dq + (fld == 0 ? 0 : nq[0]);
                 const int grid = (int)std::min<int64_t>(nt[fld], (int64_t)8 * sm_count);
-                SPDZ_FIELD_SWITCH(fld, SPDZ_NP_SWITCH(n_, k_serve_tick<F, NP><<<grid, 256, 0, tick_stream>>>(d_reqs, dt, nt[fld])));
+                const size_t qb = (size_t)nq[fld] * sizeof(TickReq);
+                const int staged = qb <= 48 * 1024;
+                const size_t smem = staged ? qb : 0;
+                SPDZ_FIELD_SWITCH(fld, SPDZ_NP_SWITCH(n_, k_serve_tick<F, NP><<<grid, 256, smem, tick_stream>>>(
+                                                           d_reqs, dqf, nq[fld], nt[fld], staged)));
                 if (nf[fld] > 0)
                     SPDZ_FIELD_SWITCH(fld, SPDZ_NP_SWITCH(n_, k_serve_check<F, NP><<<(nf[fld] + 63) / 64, 64, 0, tick_stream>>>(
-                                                               d_reqs, d_slots[ring] + (fld == 0 ? 0 : max_active), nf[fld])));
+                                                               d_reqs, dslots + (fld == 0 ? 0 : nf[0]), nf[fld])));
             }
             cudaEventRecord(ring_ev[ring], tick_stream);
             ring_busy[ring] = 1;
@@ -835,6 +837,14 @@ void spdz_server::loop() {
     cudaStreamSynchronize(deal_stream);
     cudaStreamSynchronize(up_stream);
     for (auto st : side) cudaStreamSynchronize(st);
+    // the ticks still in the ring
+    for (int k = 0; k < RING; ++k) {
+        float ms = 0;
+        if (ring_busy[k] && cudaEventElapsedTime(&ms, ring_start[k], ring_ev[k]) == cudaSuccess && ms > 0) {
+            st_tick_dev_s += ms * 1e-3;
+            ++st_tick_timed;
+        }
+    }
 }
 
 extern "C" {
@@ -873,9 +883,14 @@ int spdz_serve_create(spdz_server **out, int n_parties, uint64_t budget_bytes, i
     cudaStreamCreateWithFlags(&s->up_stream, cudaStreamNonBlocking);
     s->side.resize(16);
     for (auto &st : s->side) cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    const size_t tick_cap = (size_t)2 * s->max_active * (sizeof(TickReq) + sizeof(int32_t));
     for (int k = 0; k < spdz_server::RING; ++k) {
         cudaEventCreate(&s->ring_ev[k]);
         cudaEventCreate(&s->ring_start[k]);
+        if (cudaMallocHost(&s->h_tickbuf[k], tick_cap) != cudaSuccess || cudaMalloc(&s->d_tickbuf[k], tick_cap) != cudaSuccess) {
+            spdz_serve_destroy(s);
+            return SPDZ_ERR_OOM;
+        }
     }
     *out = s;
     return SPDZ_OK;
@@ -944,6 +959,8 @@ int spdz_serve_start(spdz_server *s) {
     s->st_dealer_s = s->st_last_done = 0;
     s->st_max_active = 0;
     s->h_admit = s->h_tick = s->h_done = s->h_idle = s->h_ringwait = 0;
+    s->st_tick_dev_s = 0;
+    s->st_tick_timed = 0;
     s->cluster_backlog_us = 0;
     s->arena.reset_peak();
     for (auto &kv : s->circuits) kv.second->users = 0;
@@ -1038,6 +1055,8 @@ int spdz_serve_stop(spdz_server *s, spdz_serve_stats *stats) {
         stats->host_complete_s = s->h_done;
         stats->host_idle_s = s->h_idle;
         stats->host_ring_wait_s = s->h_ringwait;
+        stats->device_tick_s = s->st_tick_dev_s;
+        stats->device_ticks_timed = s->st_tick_timed;
     }
     return s->worker_rc;
 }
@@ -1056,10 +1075,8 @@ int spdz_serve_destroy(spdz_server *s) {
     if (s->d_reqs) cudaFree(s->d_reqs);
     if (s->h_reqs) cudaFreeHost(s->h_reqs);
     for (int k = 0; k < spdz_server::RING; ++k) {
-        if (s->h_tiles[k]) cudaFreeHost(s->h_tiles[k]);
-        if (s->d_tiles[k]) cudaFree(s->d_tiles[k]);
-        if (s->h_slots[k]) cudaFreeHost(s->h_slots[k]);
-        if (s->d_slots[k]) cudaFree(s->d_slots[k]);
+        if (s->h_tickbuf[k]) cudaFreeHost(s->h_tickbuf[k]);
+        if (s->d_tickbuf[k]) cudaFree(s->d_tickbuf[k]);
         if (s->ring_ev[k]) cudaEventDestroy(s->ring_ev[k]);
         if (s->ring_start[k]) cudaEventDestroy(s->ring_start[k]);
     }
