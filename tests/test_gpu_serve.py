@@ -79,6 +79,25 @@ def test_served_results_equal_oracle_alone_and_in_the_mix():
         assert_equal(outs[0][0], expect[k][0], f"request {k} alone")
 
 
+def test_wide_layers_equal_oracle():
+    """Layers of 70k-440k gates (up to 1,720 tiles of one request in a tick,
+    each tile finding its request on the device): two wide requests (p61 and
+    p127) in the mix with small ones, every wire equals the oracle's and
+    every check passes."""
+    wide = [W.Request(rid=0, arrival_s=0.0, p=O.P61, gates=600000, depth=3, seed=41),
+            W.Request(rid=1, arrival_s=0.0, p=O.P127, gates=300000, depth=2, seed=42)]
+    trace = [(r, W.request_dag(r)) for r in wide] + small_trace(count=4, seed=43)
+    assert max(int(np.max(np.diff(d.layer_offsets))) for _, d in trace[:2]) > 65536
+    expect = [oracle_wires(r, d) for r, d in trace]
+    for mode, kw in ((S.SPDZ_SERVE_BATCHED, {}), (S.SPDZ_SERVE_HEURISTIC, {"cluster_width": 1024})):
+        outs, res, st = serve(trace, mode, **kw)
+        assert st.requests == len(trace)
+        for k, ((ov, om), (ev, em)) in enumerate(zip(outs, expect)):
+            assert res[k].passed == 1, (mode, k)
+            assert_equal(ov, ev, f"mode {mode} request {k} values")
+            assert_equal(om, em, f"mode {mode} request {k} MACs")
+
+
 def test_admission_respects_the_memory_budget():
     trace = small_trace(count=12, seed=8, rate=1e6)     # all arrive at once
     per = []
