@@ -98,6 +98,15 @@ __global__ void __launch_bounds__(256) k_serve_tick(const ReqDev *reqs, const Ti
         __syncthreads();
         tq = tq_smem;
     }
+    // A CTA's tiles (gridDim apart) mostly belong to one request: its check
+    // sums are kept in registers and added to the request's accumulators
+    // when the CTA moves to another request and at the end, not once per
+    // tile.  The request of a tile is the same for every thread of the CTA.
+    int cur = -1;
+    DevState *cur_ds = nullptr;
+    T acc[NP + 1];
+#pragma unroll
+    for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         int lo = 0, hi = nreq - 1;
         while (lo < hi) {
@@ -106,15 +115,22 @@ __global__ void __launch_bounds__(256) k_serve_tick(const ReqDev *reqs, const Ti
             else hi = mid - 1;
         }
         const TickReq q = tq[lo];
-        const int32_t r0 = q.r0 + 256 * (t - q.tile0), r1 = min(q.r1, r0 + 256);
         const DagArgs<F> a = req_args<F>(reqs[q.slot]);
+        if (lo != cur) {
+            if (cur >= 0) {
+                block_accumulate<F, NP + 1>(acc, cur_ds->acc);
+#pragma unroll
+                for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
+            }
+            cur = lo;
+            cur_ds = a.ds;
+        }
+        const int32_t r0 = q.r0 + 256 * (t - q.tile0), r1 = min(q.r1, r0 + 256);
         const LayerRow L = load_row(a.lay, q.layer);
         const uint64_t key = a.ds->key;
-        T alpha[NP], acc[NP + 1];
+        T alpha[NP];
 #pragma unroll
         for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
-#pragma unroll
-        for (int k = 0; k < NP + 1; ++k) acc[k] = F::zero();
         const int32_t r = r0 + (int32_t)threadIdx.x;
         if (r < r1) {
             const int cls = class_of(L, r);
@@ -122,8 +138,8 @@ __global__ void __launch_bounds__(256) k_serve_tick(const ReqDev *reqs, const Ti
             gate_load_direct<F, NP>(a, L, r, cls, 0, g);
             gate_exec<F, NP>(a, L, r, cls, g.rec, g.k, TriRegs<F, NP>{g}, key, alpha, acc);
         }
-        block_accumulate<F, NP + 1>(acc, a.ds->acc);
     }
+    if (cur >= 0) block_accumulate<F, NP + 1>(acc, cur_ds->acc);
 }
 
 // Final MAC check of one request (after its cluster launch).
