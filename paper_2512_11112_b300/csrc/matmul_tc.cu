@@ -77,31 +77,33 @@ __device__ __forceinline__ void balanced_digits(uint64_t x, float (&d)[TC_DIGITS
 
 // Row-major rows x cols matrix -> planes [TC_DIGITS][rows][colsp] (bf16),
 // columns cols .. colsp-1 zero (colsp: cols rounded up to a multiple of 8 for
-// 16-byte TMA strides).  A block walks whole rows, a thread four consecutive
-// columns: one 8-byte store of four digits per plane, no index division.
+// 16-byte TMA strides).  A block takes chunks of 2048 columns of one row (one
+// index division per chunk), a thread eight consecutive columns: eight loads
+// in flight and one 16-byte store of eight digits per plane.
+constexpr int64_t TC_DCHUNK = 2048;
 __global__ void k_digits_rowmajor(const uint64_t *x, int64_t rows, int64_t cols, int64_t ld, int64_t colsp,
                                   __nv_bfloat16 *planes) {
     const int64_t total = rows * colsp;
-    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int64_t nch = (colsp + TC_DCHUNK - 1) / TC_DCHUNK;
+    for (int64_t c = blockIdx.x; c < rows * nch; c += gridDim.x) {
+        const int64_t r = c / nch, k0 = (c - r * nch) * TC_DCHUNK, k1 = min(colsp, k0 + TC_DCHUNK);
         const uint64_t *xr = x + r * ld;
-        for (int64_t c0 = 4 * (int64_t)threadIdx.x; c0 < colsp; c0 += 4 * (int64_t)blockDim.x) {
-            float d[4][TC_DIGITS];
+        for (int64_t c0 = k0 + 8 * (int64_t)threadIdx.x; c0 < k1; c0 += 8 * (int64_t)blockDim.x) {
+            uint64_t v[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (c0 + u < cols) {
-                    balanced_digits(xr[c0 + u], d[u]);
-                } else {
+            for (int u = 0; u < 8; ++u) v[u] = c0 + u < cols ? xr[c0 + u] : 0;
+            float d[8][TC_DIGITS];
 #pragma unroll
-                    for (int j = 0; j < TC_DIGITS; ++j) d[u][j] = 0.f;
-                }
-            }
+            for (int u = 0; u < 8; ++u) balanced_digits(v[u], d[u]);   // 0 gives all-zero digits
 #pragma unroll
             for (int j = 0; j < TC_DIGITS; ++j) {
-                const __nv_bfloat162 lo = __floats2bfloat162_rn(d[0][j], d[1][j]), hi = __floats2bfloat162_rn(d[2][j], d[3][j]);
-                uint2 w;
-                w.x = *reinterpret_cast<const uint32_t *>(&lo);
-                w.y = *reinterpret_cast<const uint32_t *>(&hi);
-                *reinterpret_cast<uint2 *>(planes + j * total + r * colsp + c0) = w;
+                uint4 w;
+                __nv_bfloat162 h;
+                h = __floats2bfloat162_rn(d[0][j], d[1][j]); w.x = *reinterpret_cast<const uint32_t *>(&h);
+                h = __floats2bfloat162_rn(d[2][j], d[3][j]); w.y = *reinterpret_cast<const uint32_t *>(&h);
+                h = __floats2bfloat162_rn(d[4][j], d[5][j]); w.z = *reinterpret_cast<const uint32_t *>(&h);
+                h = __floats2bfloat162_rn(d[6][j], d[7][j]); w.w = *reinterpret_cast<const uint32_t *>(&h);
+                *reinterpret_cast<uint4 *>(planes + j * total + r * colsp + c0) = w;
             }
         }
     }
@@ -563,10 +565,11 @@ int matmul_tensor(spdz_ctx *ctx, const uint64_t *E, const uint64_t *Fm, const ui
     uint64_t *dP = (uint64_t *)((((uintptr_t)((unsigned char *)dR + plane_r * 2 * NPn)) + 255) & ~(uintptr_t)255);
     cudaMemsetAsync(err, 0, sizeof(int), ctx->stream);
     const int gb = 4 * ctx->sm_count;
-    k_digits_rowmajor<<<gb, 256, 0, ctx->stream>>>(E, m, k, k, kp, dE);
+    const int gd = (int)std::min<int64_t>(m * ((kp + TC_DCHUNK - 1) / TC_DCHUNK), 8 * (int64_t)ctx->sm_count);
+    k_digits_rowmajor<<<gd, 256, 0, ctx->stream>>>(E, m, k, k, kp, dE);
     for (int w = 0; w < 2; ++w)
         for (int i = 0; i < NPn; ++i)
-            k_digits_rowmajor<<<gb, 256, 0, ctx->stream>>>((const uint64_t *)(w == 0 ? A->val : A->mac) + (int64_t)i * A->stride,
+            k_digits_rowmajor<<<gd, 256, 0, ctx->stream>>>((const uint64_t *)(w == 0 ? A->val : A->mac) + (int64_t)i * A->stride,
                                                            m, k, k, kp, (__nv_bfloat16 *)((unsigned char *)dA + plane_l * (w * NPn + i)));
     // the transposed kernel covers output columns 0 .. kp-1 (padding included)
     dim3 tg((unsigned)((n + 31) / 32), (unsigned)((kp + 63) / 64)), tb(32, 8);
