@@ -408,6 +408,10 @@ int spdz_sched_choose(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int32
     if (int rc = measure(ctx, dag, def, wires, reps, &r.default_ms)) return rc;
     if (int rc = spdz_sched_autotune(ctx, dag, wires, reps, &tuned, &r.autotuned_ms)) return rc;
     r.tagged_ms = s->last_tagged_ms;
+    // The winner's selection time is the least of several noisy medians,
+    // biased low: its time is measured again, so that the default, the
+    // autotuned and the learned plan are compared on fresh measurements alike.
+    if (int rc = measure(ctx, dag, tuned, wires, reps, &r.autotuned_ms)) return rc;
     spdz_plan best = tuned;
     double best_ms = r.autotuned_ms;
     r.chosen = 1;
