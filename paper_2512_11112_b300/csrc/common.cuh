@@ -168,12 +168,16 @@ __device__ __forceinline__ void block_accumulate(typename F::T (&v)[K], unsigned
     }
     __syncthreads();
     if (warp == 0) {
+        // lane k adds sum k: the K atomic round trips overlap instead of
+        // following each other in one lane
+        T mine = F::zero();
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             T s = lane < nwarps ? red[lane][k] : F::zero();
             s = warp_sum<F>(s);
-            if (lane == 0 && !F::is_zero(s)) acc_add(acc[k], s);
+            if (lane == k) mine = s;
         }
+        if (lane < K && !F::is_zero(mine)) acc_add(acc[lane], mine);
     }
     __syncthreads();
 }

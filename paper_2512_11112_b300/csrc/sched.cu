@@ -190,6 +190,25 @@ static int learned_plan(spdz_ctx *ctx, spdz_dag *dag, spdz_plan &p, double *pred
     std::vector<std::pair<int, int>> groups;   // (end, cfg)
     for (int l = L; l > 0; l = from[l]) groups.push_back({l, cfg[l]});
     std::reverse(groups.begin(), groups.end());
+    // Several groups only when their predicted gain over the best single
+    // group exceeds the model's error (the square root of its ln-space
+    // training loss, at least 10 %): the switches between kernel kinds cost
+    // more than the measured switch cost of one kind, and a predicted gain
+    // inside the error is not one.
+    {
+        int best_c = -1;
+        double best_uni = 1e300;
+        for (int c = 0; c < NCFG; ++c)
+            if (config_ok(dag, c) && pre[(size_t)L * NCFG + c] < best_uni) {
+                best_uni = pre[(size_t)L * NCFG + c];
+                best_c = c;
+            }
+        const double margin = std::max(0.10, std::sqrt(std::max(0.0, (double)s->train_loss)));
+        if (groups.size() > 1 && best_c >= 0 && dp[L] > best_uni * (1.0 - margin)) {
+            groups.assign(1, {L, best_c});
+            dp[L] = best_uni;
+        }
+    }
     memset(&p, 0, sizeof p);
     p.mode = SPDZ_SCHED_FUSED;
     p.block = 256;
