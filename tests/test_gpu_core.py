@@ -357,6 +357,36 @@ def test_tampered_share_fails_check_like_oracle(p):
         S.spdz_ctx_destroy(ctx)
 
 
+@pytest.mark.parametrize("p", [O.P61, O.P127, O.P32])
+def test_degenerate_sizes(p):
+    """Empty calls: a batch, an open and a linear gate of 0 elements do
+    nothing and consume no triples; inner products of length 0 are empty
+    sums, every share and MAC share 0; the check afterwards passes."""
+    n = 3
+    ctx = ctx_for(n, p)
+    try:
+        dw = DeviceWorld(ctx, p, n, 2, 64, 64)
+        x, y = dw.inputs
+        z = SH.alloc(dw.field, n, 8)
+        left = S.spdz_triples_left(ctx)
+        S.spdz_mul_batch(ctx, x.buf(), y.buf(), z.buf(), 0)
+        S.spdz_innerprod_batch(ctx, x.buf(), y.buf(), z.buf(), 0, 16)
+        S.spdz_linear(ctx, S.SPDZ_OP_ADD, x.buf(), y.buf(), None, z.buf(), 0)
+        out = torch.zeros(16, dtype=torch.int64, device="cuda")
+        S.spdz_open(ctx, x.buf(), out, 0)
+        assert S.spdz_triples_left(ctx) == left
+        # 8 inner products of length 0: fill the outputs with nonzero words first
+        z.val.fill_(1)
+        z.mac.fill_(1)
+        S.spdz_innerprod_batch(ctx, x.buf(), y.buf(), z.buf(), 8, 0)
+        gv, gm = z.host()
+        assert not np.any(O.to_ints(p, gv)) and not np.any(O.to_ints(p, gm))
+        assert S.spdz_triples_left(ctx) == left
+        assert S.spdz_mac_check(ctx)
+    finally:
+        S.spdz_ctx_destroy(ctx)
+
+
 def test_errors_are_status_codes():
     p, n = O.P61, 2
     ctx = ctx_for(n, p)
