@@ -62,7 +62,8 @@ def oracle_inputs(n, m, k, nn):
 
 
 @pytest.mark.parametrize("path", [0, 1])
-@pytest.mark.parametrize("n,m,k,nn", [(3, 64, 64, 64), (3, 100, 37, 50), (2, 5, 130, 7), (4, 33, 65, 129)])
+@pytest.mark.parametrize("n,m,k,nn", [(3, 64, 64, 64), (3, 100, 37, 50), (2, 5, 130, 7), (4, 33, 65, 129),
+                                     (2, 1, 1, 1), (3, 1, 300, 1), (2, 257, 1, 3)])
 def test_small_products_match_oracle(path, n, m, k, nn):
     if path == 1 and not _tensor_path_available():
         pytest.skip("tensor path not built")
