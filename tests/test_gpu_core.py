@@ -266,7 +266,8 @@ def test_innerprod_matches_oracle(p, P, L):
 
 
 @pytest.mark.parametrize("p,n,P,L", [(O.P61, 2, 300, 65), (O.P61, 5, 41, 97), (O.P61, 8, 23, 40),
-                                     (O.P32, 4, 77, 129), (O.P61, 3, 5000, 33), (O.P32, 2, 4100, 31)])
+                                     (O.P32, 4, 77, 129), (O.P61, 3, 5000, 33), (O.P32, 2, 4100, 31),
+                                     (O.P61, 3, 3000, 1), (O.P127, 3, 50, 1)])
 def test_innerprod_party_counts_and_wrapping(p, n, P, L):
     """Inner products for other party counts (the staged kernel's buffer
     grows with n: at n = 8 one CTA per SM) and with more products than the
