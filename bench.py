@@ -298,7 +298,7 @@ def beaver_roofline(torch, S, SH, hbm_peak, N=2**24, calls=4, field=None):
         ms = statistics.median(ts)
         bpm = 12 * N_PARTIES * {S.SPDZ_F61: 8, S.SPDZ_F127: 16, S.SPDZ_F32: 4}[field]
         gbs = bpm * N / (ms * 1e-3) / 1e9
-        kname = {S.SPDZ_F61: "k_mul<F61,3,2>", S.SPDZ_F127: "k_mul<F127,3,1>", S.SPDZ_F32: "k_mul<F32,3,4>"}[field]
+        kname = {S.SPDZ_F61: "k_mul<F61,3,2>", S.SPDZ_F127: "k_mul127_staged<3>", S.SPDZ_F32: "k_mul<F32,3,4>"}[field]
         return {"kernel": f"{kname} (spdz_mul_batch)", "N": N, "bytes_per_mult": bpm,
                 "ms": round(ms, 4), "mults_per_s": N / (ms * 1e-3), "achieved_gbs": round(gbs, 1),
                 "peak_gbs": hbm_peak, "frac": round(gbs / hbm_peak, 4),
@@ -943,8 +943,8 @@ def heavy_metrics(args, ipk=None):
     mul_ms, ip_ms = statistics.median(res["mul"]), statistics.median(res["ip"])
     pipes = read_pipes()
     roof = {}
-    for name, kern, ms, units, per in (("mul", "k_mul<F127,3,1>", mul_ms, N, 576),
-                                       ("innerprod", "k_innerprod<F127,3>", ip_ms, P * L, 480)):
+    for name, kern, ms, units, per in (("mul", "k_mul127_staged<3>", mul_ms, N, 576),
+                                       ("innerprod", "k_innerprod127_staged<3>", ip_ms, P * L, 480)):
         t_hbm = per * units / (hbm * 1e9)
         d = {"kernel": kern, "unit_bytes": per, "achieved_gbs": round(per * units / (ms * 1e-3) / 1e9, 1),
              "hbm_peak_gbs": hbm, "hbm_frac": round(t_hbm / (ms * 1e-3), 4), "hbm_bound_ms": round(t_hbm * 1e3, 4)}

@@ -147,35 +147,60 @@ __device__ __forceinline__ void beaver_core(const MulArgs<F> &a, int64_t e, int6
     }
 }
 
-// p127 form of one Beaver product at element e.  The opened values' check
-// terms go into exact three-word sums that stay unreduced across every
-// element a thread handles (acc[0] = A, acc[1+i] = S_i); z and gamma(z) are
-// one exact sum each, reduced once.  With sums != nullptr the outputs are not
-// reduced either: they are added to sums[i] / sums[NP + i] (inner products),
-// without the eps delta terms (party 0's value, alpha_i eps delta in every
-// MAC share), whose sum goes to *sde for one product per party at the end.
-template <int NP>
-__device__ __forceinline__ void beaver_core127(const MulArgs<F127> &a, int64_t e, uint64_t key,
-                                               const u128v (&alpha)[NP], W127 (&acc)[NP + 1], u128v (&z)[NP],
-                                               u128v (&gz)[NP], u128v &eps, u128v &dlt, W127 *sums,
-                                               W127 *sde = nullptr) {
+// The operands of one p127 Beaver product at element e, read from the
+// party-major rows (triple rows with the evict-first hint: read once).
+// The hooks (before the value shares are read, after they are, before and
+// after party i's other shares are read) do nothing here.
+struct Src127Rows {
+    const MulArgs<F127> &a;
+    int64_t e;
+    template <bool S> __device__ __forceinline__ static u128v g(const u128v *p) {
+        u128v t[1];
+        vld<F127, 1, S>(p, t);
+        return t[0];
+    }
+    __device__ __forceinline__ u128v x(int i) const { return g<false>(a.xv + i * a.xs + e); }
+    __device__ __forceinline__ u128v y(int i) const { return g<false>(a.yv + i * a.ys + e); }
+    __device__ __forceinline__ u128v av(int i) const { return g<true>(a.av + i * a.as + e); }
+    __device__ __forceinline__ u128v bv(int i) const { return g<true>(a.bv + i * a.bs + e); }
+    __device__ __forceinline__ u128v c(int i) const { return g<true>(a.cv + i * a.cs + e); }
+    __device__ __forceinline__ u128v gx(int i) const { return g<false>(a.xm + i * a.xs + e); }
+    __device__ __forceinline__ u128v gy(int i) const { return g<false>(a.ym + i * a.ys + e); }
+    __device__ __forceinline__ u128v ga(int i) const { return g<true>(a.am + i * a.as + e); }
+    __device__ __forceinline__ u128v gb(int i) const { return g<true>(a.bm + i * a.bs + e); }
+    __device__ __forceinline__ u128v gc(int i) const { return g<true>(a.cm + i * a.cs + e); }
+    __device__ __forceinline__ void begin() const {}
+    __device__ __forceinline__ void opened() const {}
+    __device__ __forceinline__ void ready(int) const {}
+    __device__ __forceinline__ void consumed(int) const {}
+};
+
+// p127 form of one Beaver product at element e, its operands from src.  The
+// opened values' check terms go into exact three-word sums that stay
+// unreduced across every element a thread handles (acc[0] = A, acc[1+i] =
+// S_i); z and gamma(z) are one exact sum each, reduced once.  With sums !=
+// nullptr the outputs are not reduced either: they are added to sums[i] /
+// sums[NP + i] (inner products), without the eps delta terms (party 0's
+// value, alpha_i eps delta in every MAC share), whose sum goes to *sde for
+// one product per party at the end.
+template <int NP, class SRC>
+__device__ __forceinline__ void beaver_core127(const SRC &src, uint64_t j, uint64_t key, const u128v (&alpha)[NP],
+                                               W127 (&acc)[NP + 1], u128v (&z)[NP], u128v (&gz)[NP], u128v &eps,
+                                               u128v &dlt, W127 *sums, W127 *sde = nullptr) {
     using F = F127;
     u128v av[NP], bv[NP];
     eps = dlt = F::zero();
+    src.begin();
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-        u128v x[1], y[1], ta[1], tb[1];
-        vld<F, 1, false>(a.xv + i * a.xs + e, x);
-        vld<F, 1, false>(a.yv + i * a.ys + e, y);
-        vld<F, 1, true>(a.av + i * a.as + e, ta);
-        vld<F, 1, true>(a.bv + i * a.bs + e, tb);
-        av[i] = ta[0];
-        bv[i] = tb[0];
-        eps = F::add(eps, F::sub(x[0], av[i]));
-        dlt = F::add(dlt, F::sub(y[0], bv[i]));
+        const u128v x = src.x(i), y = src.y(i);
+        av[i] = src.av(i);
+        bv[i] = src.bv(i);
+        eps = F::add(eps, F::sub(x, av[i]));
+        dlt = F::add(dlt, F::sub(y, bv[i]));
     }
+    src.opened();
     const u128v de = W127::prod(eps, dlt).reduce();
-    const uint64_t j = a.base + 2 * (uint64_t)e;
     const u128v re = Draw<F>::at(key, j), rd = Draw<F>::at(key, j + 1);
     {
         // each product formed on its own; one three-word add into a sum
@@ -185,27 +210,23 @@ __device__ __forceinline__ void beaver_core127(const MulArgs<F127> &a, int64_t e
     }
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-        u128v c[1], gx[1], gy[1], ga[1], gb[1], gc[1];
-        vld<F, 1, true>(a.cv + i * a.cs + e, c);
-        vld<F, 1, false>(a.xm + i * a.xs + e, gx);
-        vld<F, 1, false>(a.ym + i * a.ys + e, gy);
-        vld<F, 1, true>(a.am + i * a.as + e, ga);
-        vld<F, 1, true>(a.bm + i * a.bs + e, gb);
-        vld<F, 1, true>(a.cm + i * a.cs + e, gc);
-        W127 v = W127::prod(eps, bv[i]), m = W127::prod(eps, gb[0]);
+        src.ready(i);
+        const u128v c = src.c(i), gx = src.gx(i), gy = src.gy(i), ga = src.ga(i), gb = src.gb(i), gc = src.gc(i);
+        src.consumed(i);
+        W127 v = W127::prod(eps, bv[i]), m = W127::prod(eps, gb);
         v.add(W127::prod(dlt, av[i]));
-        v.add(c[0]);
+        v.add(c);
         if (!sums && i == 0) v.add(de);
-        m.add(W127::prod(dlt, ga[0]));
+        m.add(W127::prod(dlt, ga));
         if (sums) {
-            m.add(gc[0]);
+            m.add(gc);
         } else {
             W127 m2 = W127::prod(alpha[i], de);
-            m2.add(gc[0]);
+            m2.add(gc);
             m.add(m2);
         }
-        W127 q = W127::prod(re, F::sub(gx[0], ga[0]));
-        q.add(W127::prod(rd, F::sub(gy[0], gb[0])));
+        W127 q = W127::prod(re, F::sub(gx, ga));
+        q.add(W127::prod(rd, F::sub(gy, gb)));
         acc[1 + i].add(q);
         if (sums) {
             sums[i].add(v);
@@ -223,7 +244,7 @@ __device__ __forceinline__ void mul_elem127(const MulArgs<F127> &a, int64_t e, u
                                             W127 (&acc)[NP + 1]) {
     using F = F127;
     u128v z[NP], gz[NP], eps, dlt;
-    beaver_core127<NP>(a, e, key, alpha, acc, z, gz, eps, dlt, nullptr);
+    beaver_core127<NP>(Src127Rows{a, e}, a.base + 2 * (uint64_t)e, key, alpha, acc, z, gz, eps, dlt, nullptr);
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         F::st(a.zv + i * a.zs + e, z[i]);
@@ -290,6 +311,143 @@ __global__ void __launch_bounds__(256, (mul_min_blocks<F, NP, V>())) k_mul(MulAr
         for (int64_t e = ng * V + tid; e < a.N; e += stride) mul_elems<F, NP, 1>(a, e, key, alpha, acc);
         block_accumulate<F, NP + 1>(acc, a.ds->acc);
     }
+}
+
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_groups() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// ------------------------------------------------ p127 Beaver batch, staged
+// A p127 product is long integer arithmetic (about 2,400 instructions at
+// n = 3).  Read straight from the rows, all of a product's loads are held in
+// registers (233 of them: one CTA of 8 warps per SM) and each warp waits for
+// them before it computes.  Here each thread streams its products' operands
+// through private shared-memory slots with cp.async, one product ahead: the
+// x, y, a, b value shares of every party are read from their slots when the
+// party sums are formed, and the copies of the next product's value shares
+// are issued at once; party i's c share and five MAC shares are read from
+// their slots just before party i's combine, and the copies of the next
+// product's are issued at once.  Every copy is in flight for about one
+// product's arithmetic, and no more than one party's shares are live in
+// registers, so 12 warps fit an SM.  Slot k of thread t is at k * B127S + t:
+// a warp's 16-byte accesses of one slot cover 512 consecutive bytes.  Each
+// thread reads only its own slots, after its own cp.async waits: no block
+// barrier.  Per product 1 + NP copy groups are committed, in order: the
+// value shares, then party 0's .. party NP-1's other shares; a read waits
+// until at most NP groups (the ones committed after the one it needs) are
+// pending.
+constexpr int B127S = 384;
+template <int NP, int BLK> constexpr size_t p127s_smem() { return (size_t)10 * NP * sizeof(u128v) * BLK; }
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+template <int N> __device__ __forceinline__ void cp_async_wait_pending() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Copies of product e's value shares (slots 4i .. 4i+3: x, y, a, b of party i).
+template <int NP, int BLK>
+__device__ __forceinline__ void p127s_issue_values(const MulArgs<F127> &a, u128v *sm, int64_t e) {
+    u128v *p = sm + threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        cp_async16(p + (4 * i + 0) * BLK, a.xv + i * a.xs + e);
+        cp_async16(p + (4 * i + 1) * BLK, a.yv + i * a.ys + e);
+        cp_async16(p + (4 * i + 2) * BLK, a.av + i * a.as + e);
+        cp_async16(p + (4 * i + 3) * BLK, a.bv + i * a.bs + e);
+    }
+}
+// Copies of party i's c share and MAC shares of product e (slots 4 NP + 6i ..
+// 4 NP + 6i + 5: c, gamma(x), gamma(y), gamma(a), gamma(b), gamma(c)).
+template <int NP, int BLK>
+__device__ __forceinline__ void p127s_issue_party(const MulArgs<F127> &a, u128v *sm, int64_t e, int i) {
+    u128v *p = sm + (size_t)(4 * NP + 6 * i) * BLK + threadIdx.x;
+    cp_async16(p + 0 * BLK, a.cv + i * a.cs + e);
+    cp_async16(p + 1 * BLK, a.xm + i * a.xs + e);
+    cp_async16(p + 2 * BLK, a.ym + i * a.ys + e);
+    cp_async16(p + 3 * BLK, a.am + i * a.as + e);
+    cp_async16(p + 4 * BLK, a.bm + i * a.bs + e);
+    cp_async16(p + 5 * BLK, a.cm + i * a.cs + e);
+}
+
+// Operands of the current product from this thread's slots; the hooks wait
+// for a set of slots before it is read and refill it (with element en, if
+// en is valid) once it has been read.
+template <int NP, int BLK> struct Src127Staged {
+    const MulArgs<F127> &a;
+    u128v *sm;
+    int64_t en;
+    bool more;          // en is an element to copy
+    __device__ __forceinline__ u128v s(int k) const {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(sm + (size_t)k * BLK + threadIdx.x);
+        return {v.x, v.y};
+    }
+    __device__ __forceinline__ u128v x(int i) const { return s(4 * i + 0); }
+    __device__ __forceinline__ u128v y(int i) const { return s(4 * i + 1); }
+    __device__ __forceinline__ u128v av(int i) const { return s(4 * i + 2); }
+    __device__ __forceinline__ u128v bv(int i) const { return s(4 * i + 3); }
+    __device__ __forceinline__ u128v c(int i) const { return s(4 * NP + 6 * i + 0); }
+    __device__ __forceinline__ u128v gx(int i) const { return s(4 * NP + 6 * i + 1); }
+    __device__ __forceinline__ u128v gy(int i) const { return s(4 * NP + 6 * i + 2); }
+    __device__ __forceinline__ u128v ga(int i) const { return s(4 * NP + 6 * i + 3); }
+    __device__ __forceinline__ u128v gb(int i) const { return s(4 * NP + 6 * i + 4); }
+    __device__ __forceinline__ u128v gc(int i) const { return s(4 * NP + 6 * i + 5); }
+    __device__ __forceinline__ void begin() const { cp_async_wait_pending<NP>(); }
+    __device__ __forceinline__ void opened() const {
+        if (more) p127s_issue_values<NP, BLK>(a, sm, en);
+        cp_async_commit_group();
+    }
+    __device__ __forceinline__ void ready(int) const { cp_async_wait_pending<NP>(); }
+    __device__ __forceinline__ void consumed(int i) const {
+        if (more) p127s_issue_party<NP, BLK>(a, sm, en, i);
+        cp_async_commit_group();
+    }
+};
+
+// The first element's copies of a thread (if it has one), in the groups' order.
+template <int NP, int BLK>
+__device__ __forceinline__ void p127s_prologue(const MulArgs<F127> &a, u128v *sm, int64_t e, bool valid) {
+    if (valid) p127s_issue_values<NP, BLK>(a, sm, e);
+    cp_async_commit_group();
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        if (valid) p127s_issue_party<NP, BLK>(a, sm, e, i);
+        cp_async_commit_group();
+    }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(B127S, 1) k_mul127_staged(MulArgs<F127> a) {
+    using F = F127;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    u128v *sm = reinterpret_cast<u128v *>(smem_raw);
+    const uint64_t key = a.ds->key;
+    u128v alpha[NP], acc[NP + 1];
+    W127 wacc[NP + 1];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
+    const int64_t stride = (int64_t)gridDim.x * B127S;
+    int64_t e = blockIdx.x * (int64_t)B127S + threadIdx.x;
+    p127s_prologue<NP, B127S>(a, sm, e, e < a.N);
+    for (; e < a.N; e += stride) {
+        u128v z[NP], gz[NP], eps, dlt;
+        beaver_core127<NP>(Src127Staged<NP, B127S>{a, sm, e + stride, e + stride < a.N}, a.base + 2 * (uint64_t)e,
+                           key, alpha, wacc, z, gz, eps, dlt, nullptr);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            F::st(a.zv + i * a.zs + e, z[i]);
+            F::st(a.zm + i * a.zs + e, gz[i]);
+        }
+        if (a.opened) {
+            F::st(a.opened + 2 * e, eps);
+            F::st(a.opened + 2 * e + 1, dlt);
+        }
+    }
+    cp_async_wait_all_groups();
+#pragma unroll
+    for (int k = 0; k < NP + 1; ++k) acc[k] = wacc[k].reduce();
+    block_accumulate<F, NP + 1>(acc, a.ds->acc);
 }
 
 // Inner products: one warp per product t; lane l takes terms l, l+32, ...;
@@ -491,6 +649,62 @@ __global__ void __launch_bounds__(IP_BLOCK) k_innerprod_staged(MulArgs<F> a) {
 // Two CTAs per SM: latency of the lanes' term loads is hidden by more
 // resident warps (the sums then live in 128 registers with a few spilled,
 // faster than one CTA and no spill).
+// p127 inner products with their terms streamed through shared memory as in
+// k_mul127_staged: one warp per product, lane l takes terms l, l + 32, ...;
+// a lane's next term (in this product, else the first of the warp's next
+// product) is copied while it computes the current one.
+constexpr int B127IP = 384;
+
+template <int NP>
+__global__ void __launch_bounds__(B127IP, 1) k_innerprod127_staged(MulArgs<F127> a) {
+    using F = F127;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    u128v *sm = reinterpret_cast<u128v *>(smem_raw);
+    const uint64_t key = a.ds->key;
+    u128v alpha[NP], acc[NP + 1];
+    W127 wacc[NP + 1];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = ((int64_t)gridDim.x * B127IP) >> 5;
+    const int64_t t0 = (blockIdx.x * (int64_t)B127IP + threadIdx.x) >> 5;
+    p127s_prologue<NP, B127IP>(a, sm, t0 * a.len + lane, t0 < a.N && lane < a.len);
+    for (int64_t t = t0; t < a.N; t += wstride) {
+        W127 sums[2 * NP], sde;
+        for (int64_t k = lane; k < a.len; k += 32) {
+            // the lane's next term
+            const bool same = k + 32 < a.len;
+            const int64_t tn = same ? t : t + wstride, kn = same ? k + 32 : lane;
+            const bool more = tn < a.N && kn < a.len;
+            u128v z[NP], gz[NP], eps, dlt;
+            const int64_t e = t * a.len + k;
+            beaver_core127<NP>(Src127Staged<NP, B127IP>{a, sm, tn * a.len + kn, more}, a.base + 2 * (uint64_t)e, key,
+                               alpha, wacc, z, gz, eps, dlt, sums, &sde);
+        }
+        const u128v de = sde.reduce();
+        sums[0].add(de);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) sums[NP + i].add(W127::prod(alpha[i], de));
+        u128v sz[NP], sg[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            sz[i] = warp_sum<F>(sums[i].reduce());
+            sg[i] = warp_sum<F>(sums[NP + i].reduce());
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                F::st(a.zv + i * a.zs + t, sz[i]);
+                F::st(a.zm + i * a.zs + t, sg[i]);
+            }
+        }
+    }
+    cp_async_wait_all_groups();
+#pragma unroll
+    for (int k = 0; k < NP + 1; ++k) acc[k] = wacc[k].reduce();
+    block_accumulate<F, NP + 1>(acc, a.ds->acc);
+}
+
 template <int NP>
 __global__ void __launch_bounds__(256, 2) k_innerprod127(MulArgs<F127> a) {
     using F = F127;
@@ -505,7 +719,9 @@ __global__ void __launch_bounds__(256, 2) k_innerprod127(MulArgs<F127> a) {
         W127 sums[2 * NP], sde;
         for (int64_t k = lane; k < a.len; k += 32) {
             u128v z[NP], gz[NP], eps, dlt;
-            beaver_core127<NP>(a, t * a.len + k, key, alpha, wacc, z, gz, eps, dlt, sums, &sde);
+            const int64_t e = t * a.len + k;
+            beaver_core127<NP>(Src127Rows{a, e}, a.base + 2 * (uint64_t)e, key, alpha, wacc, z, gz, eps, dlt, sums,
+                               &sde);
         }
         const u128v de = sde.reduce();
         sums[0].add(de);
@@ -627,9 +843,26 @@ template <class F, int NP> static void ip_smem_attr(spdz_ctx *ctx, const void *k
     done.fetch_or(bit, std::memory_order_acq_rel);
 }
 
+// The staged p127 kernels' slots are above the default 48 KB of dynamic
+// shared memory: raise a kernel's limit once per device (KIND: 0 the batch,
+// 1 the inner products).
+template <int NP, int KIND> static void p127s_smem_attr(spdz_ctx *ctx, const void *kern, size_t smem) {
+    static std::atomic<uint64_t> done{0};
+    const uint64_t bit = 1ull << (ctx->device & 63);
+    if (done.load(std::memory_order_acquire) & bit) return;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    done.fetch_or(bit, std::memory_order_acq_rel);
+}
+
 template <class F, int NP>
 static void launch_innerprod(spdz_ctx *ctx, const MulArgs<F> &a, int64_t count) {
-    if constexpr (std::is_same_v<F, F127>) {
+    if constexpr (std::is_same_v<F, F127> && NP <= 3) {
+        // terms staged through shared memory (up to 180 KB per CTA)
+        auto kern = k_innerprod127_staged<NP>;
+        constexpr size_t smem = p127s_smem<NP, B127IP>();
+        p127s_smem_attr<NP, 1>(ctx, (const void *)kern, smem);
+        kern<<<grid_for(ctx, (const void *)kern, B127IP, smem, count * 32), B127IP, smem, ctx->stream>>>(a);
+    } else if constexpr (std::is_same_v<F, F127>) {
         auto kern = k_innerprod127<NP>;
         kern<<<grid_for(ctx, (const void *)kern, 256, 0, count * 32), 256, 0, ctx->stream>>>(a);
     } else {
@@ -673,6 +906,14 @@ static void launch_mul(spdz_ctx *ctx, const MulArgs<F> &a, bool v2) {
             kern<<<grid_for(ctx, (const void *)kern, 256, 0, (a.N + 3) / 4), 256, 0, ctx->stream>>>(a);
             return;
         }
+    }
+    if constexpr (std::is_same_v<F, F127> && NP <= 3) {
+        // operands staged through shared memory (up to 192 KB per CTA)
+        auto kern = k_mul127_staged<NP>;
+        constexpr size_t smem = p127s_smem<NP, B127S>();
+        p127s_smem_attr<NP, 0>(ctx, (const void *)kern, smem);
+        kern<<<grid_for(ctx, (const void *)kern, B127S, smem, a.N), B127S, smem, ctx->stream>>>(a);
+        return;
     }
     auto kern = k_mul<F, NP, 1>;
     kern<<<grid_for(ctx, (const void *)kern, 256, 0, a.N), 256, 0, ctx->stream>>>(a);

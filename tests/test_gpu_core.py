@@ -84,6 +84,8 @@ MUL_CASES = [
     (O.P61, 4, 5003, 0),
     (O.P127, 3, 4099, 0),
     (O.P127, 2, 3, 0),
+    (O.P127, 2, 70001, 0),    # more products than the staged p127 grid has threads
+    (O.P127, 4, 1000, 0),     # more parties than the staged p127 kernel's slots hold
     (O.P32, 3, 4097, 0),      # p = 2^32-5, the prime of the paper's evaluation
     (O.P32, 2, 777, 1),
 ]
@@ -267,12 +269,15 @@ def test_innerprod_matches_oracle(p, P, L):
 
 @pytest.mark.parametrize("p,n,P,L", [(O.P61, 2, 300, 65), (O.P61, 5, 41, 97), (O.P61, 8, 23, 40),
                                      (O.P32, 4, 77, 129), (O.P61, 3, 5000, 33), (O.P32, 2, 4100, 31),
-                                     (O.P61, 3, 3000, 1), (O.P127, 3, 50, 1)])
+                                     (O.P61, 3, 3000, 1), (O.P127, 3, 50, 1), (O.P127, 2, 300, 65),
+                                     (O.P127, 3, 2000, 33), (O.P127, 4, 23, 40)])
 def test_innerprod_party_counts_and_wrapping(p, n, P, L):
     """Inner products for other party counts (the staged kernel's buffer
     grows with n: at n = 8 one CTA per SM) and with more products than the
     grid has warps, so each warp's next-term copies cross into its next
-    product; lengths that leave lanes idle in the last step."""
+    product; lengths that leave lanes idle in the last step.  For p127 the
+    staged kernel takes n = 2 and 3 (2000 products wrap its 1776 warps) and
+    the register kernel n = 4."""
     seed, chk = 12, 3
     ctx = ctx_for(n, p)
     try:
