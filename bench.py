@@ -376,6 +376,77 @@ def cpu_baseline(dag, seed, reps=3):
                             "sample": f"one full evaluation by the oracle's gate-order loop, {t_one:.3f} s"}}
 
 
+def config_cpu_baselines():
+    """The CPU oracle as it stands on bounded samples of the other
+    configurations, on every host core (each sample a few seconds at most; the
+    rate is the sample's units over its time, in the configuration's unit).
+    Only the online computation is timed, not the oracle's dealing."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    out = {}
+
+    def world(p, n, seed, N, T):
+        alpha, ash = O.deal_alpha(p, n, seed)
+        x = O.deal_shared(p, n, seed, O.K_INPUT, 0, 0, N, alpha)
+        y = O.deal_shared(p, n, seed, O.K_INPUT, 1, 0, N, alpha)
+        return ash, x, y, O.deal_triples(p, n, seed, 0, T, alpha)
+
+    def timed(fn):
+        t0 = time.perf_counter()
+        fn()
+        return time.perf_counter() - t0
+
+    # c1: 2^16 products at n = 2, p61, with their MAC check
+    N = 2**16
+    ash, x, y, tri = world(O.P61, 2, 1, N, N)
+
+    def c1():
+        *_, log = O.mul(O.P61, x[0], x[1], y[0], y[1], tri, ash)
+        O.mac_check(O.P61, [log], ash, 1, 0)
+    dt = timed(c1)
+    out["c1_batch_n2_p61"] = {"value": N / dt, "unit": "Beaver mults/s (with the MAC check)", "cores": cores,
+                              "kind": "oracle", "sample": f"the full 2^16-product batch and its check, {dt:.3f} s"}
+    # c3: p127, n = 3: 2^16 of the 2^24 products, 64 of the 16,384 inner products
+    N, P, L = 2**16, 64, 1024
+    ash, x, y, tri = world(O.P127, 3, 3, max(N, P * L), max(N, P * L))
+    dm = timed(lambda: O.mul(O.P127, x[0][:, :N].copy(), x[1][:, :N].copy(), y[0][:, :N].copy(),
+                             y[1][:, :N].copy(), tri, ash))
+    di = timed(lambda: O.innerprod(O.P127, P, L, x[0], x[1], y[0], y[1], tri, ash))
+    out["c3_heavy_p127"] = {"value": N / dm, "unit": "Beaver mults/s", "cores": cores, "kind": "oracle",
+                            "innerprod_terms_per_s": P * L / di,
+                            "sample": f"2^16 of the 2^24 products ({dm:.3f} s) and 64 of the 16,384 inner products "
+                                      f"of length 1024 ({di:.3f} s)"}
+    # c4: a 256^3 secret-shared matrix product (n = 3, p61) instead of 2048^3
+    M = 256
+    p, n = O.P61, 3
+    alpha, ash = O.deal_alpha(p, n, 4)
+    X = O.deal_shared(p, n, 4, O.K_INPUT, 0, 0, M * M, alpha)[:2]
+    Y = O.deal_shared(p, n, 4, O.K_INPUT, 1, 0, M * M, alpha)[:2]
+    mtri = O.deal_matrix_triple(p, n, 4, 0, M, M, M, alpha)
+    rows, cols = np.repeat(np.arange(M), M), np.tile(np.arange(M), M)
+
+    def c4():
+        E, F, _, _ = O.mat_open(p, M, M, M, X, Y, mtri)
+        O.mat_entries(p, M, M, M, E, F, mtri, ash, rows, cols)
+    dt = timed(c4)
+    out["c4_matmul_2048"] = {"value": 12 * M**3 / dt, "unit": "modular MACs/s", "cores": cores, "kind": "oracle",
+                             "sample": f"the whole product at 256^3 instead of 2048^3, {dt:.3f} s"}
+    # the LinearLayer: 256 of the 8192 output rows (n = 2, p = 2^32-5, 32-row tiles)
+    p, n, dout, din, R = O.P32, 2, 256, 8192, 32
+    alpha, ash = O.deal_alpha(p, n, 6)
+    Wm = O.deal_shared(p, n, 6, O.K_INPUT, 0, 0, dout * din, alpha)[:2]
+    xv = O.deal_shared(p, n, 6, O.K_INPUT, 1, 0, din, alpha)[:2]
+    bv = O.deal_shared(p, n, 6, O.K_INPUT, 2, 0, dout, alpha)[:2]
+    ltri = O.deal_matvec_triples(p, n, 6, 0, dout, din, R, alpha)
+    dt = timed(lambda: O.linear_layer(p, dout, din, R, Wm, xv, bv, ltri, ash))
+    out["linear_layer_8192"] = {"value": dt * (8192 / dout) * 1e3, "unit": "ms per 8192 x 8192 layer (projected)",
+                                "cores": cores, "kind": "oracle",
+                                "sample": f"256 of the 8192 output rows ({dt:.3f} s), scaled by 32"}
+    O.set_threads(1)
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     torch.cuda.set_device(local_rank)
@@ -443,6 +514,13 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.empty_cache()
     extras = all_configs(args) if world == 1 and not args.no_extras else None
     cpu = cpu_baseline(dag, seed=2) if not args.no_cpu_baseline else None
+    if extras is not None and not args.no_cpu_baseline:
+        try:
+            for key, cb in config_cpu_baselines().items():
+                if key in extras and "error" not in extras[key]:
+                    extras[key]["cpu_baseline"] = cb
+        except Exception as e:   # noqa: BLE001
+            extras["cpu_baseline_error"] = repr(e)[:300]
     line = {
         "metric": METRIC,
         "value": value,
