@@ -322,6 +322,17 @@ int spdz_check_result(spdz_ctx *ctx, int *passed, void *sigma_host);
 /* Per-layer device times (microseconds, [depth]) of the last run that had
  * record_layer_times set. */
 int spdz_dag_layer_times(const spdz_dag *dag, float *us_out);
+/* Kernel timing of a circuit's runs (a measurement aid beside the run-time
+ * figures of Sec. IV-B).  With on != 0 every later run of dag records CUDA
+ * events on its stream right after its begin kernel and right after its last
+ * circuit kernel (its check kernel included when the plan has one; a tagged
+ * run checks inside its circuit kernel), also inside a captured graph: a
+ * graph captured with the other setting is captured again at the next run.
+ * spdz_dag_kernel_ms waits for the last such run and writes the time between
+ * the two events (milliseconds) to *ms.  SPDZ_ERR_STATE when timing was never
+ * enabled, SPDZ_ERR_CUDA when no timed run has completed. */
+int spdz_dag_time_kernels(spdz_dag *dag, int32_t on);
+int spdz_dag_kernel_ms(spdz_dag *dag, float *ms);
 /* Layer-shape summary used by schedulers: for each layer l, counts[l*5 + c]
  * is the number of gates of class c (MUL, ADD, SUB, CMUL, CADD). */
 int spdz_dag_layer_counts(const spdz_dag *dag, int32_t *counts_out);

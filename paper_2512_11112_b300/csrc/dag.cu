@@ -116,6 +116,16 @@ static int launch_tagged(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, Da
     }
 }
 
+// Records a timing event on s: while s is being captured, as an external
+// record (an event node of the graph, recorded at every replay); otherwise
+// as a plain record.
+static void record_timing_event(cudaEvent_t ev, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+    else cudaEventRecord(ev, s);
+}
+
 // Enqueues every kernel of one run on stream s (begin, layers, checks).
 // Returns the number of launches, or -status.
 template <class F, int NP>
@@ -124,6 +134,7 @@ static int enqueue_run(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, cons
     int launches = 0;
     k_run_begin<<<1, 1, 0, s>>>(ctx->ds, tri_base, df_tag);
     ++launches;
+    if (dag->time_kernels) record_timing_event(dag->kev0, s);
     const int block = plan.block > 0 ? plan.block : 256;
     DagArgs<F> a = base_args<F>(ctx, dag, w);
     a.spin_ns = (uint64_t)(plan.spin_limit_us ? plan.spin_limit_us : 200000u) * 1000ull;
@@ -282,6 +293,7 @@ static int enqueue_run(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, cons
             return -rc;
         }
     }
+    if (dag->time_kernels) record_timing_event(dag->kev1, s);
     ctx->stream = saved;
     return launches;
 }
@@ -423,6 +435,8 @@ int spdz_dag_destroy(spdz_dag *g) {
     if (g->gexec) cudaGraphExecDestroy(g->gexec);
     if (g->graph) cudaGraphDestroy(g->graph);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    if (g->kev0) cudaEventDestroy(g->kev0);
+    if (g->kev1) cudaEventDestroy(g->kev1);
     if (g->d_rec) cudaFree(g->d_rec);
     if (g->d_lay) cudaFree(g->d_lay);
     if (g->d_kc) cudaFree(g->d_kc);
@@ -431,6 +445,24 @@ int spdz_dag_destroy(spdz_dag *g) {
     if (g->ev1) cudaEventDestroy(g->ev1);
     for (auto &e : g->lev) cudaEventDestroy(e);
     delete g;
+    return SPDZ_OK;
+}
+
+int spdz_dag_time_kernels(spdz_dag *dag, int32_t on) {
+    if (!dag) return SPDZ_ERR_ARG;
+    if (on && !dag->kev0) {
+        if (cudaEventCreate(&dag->kev0) != cudaSuccess || cudaEventCreate(&dag->kev1) != cudaSuccess)
+            return set_err(dag->ctx, SPDZ_ERR_CUDA, "dag_time_kernels: event creation failed");
+    }
+    dag->time_kernels = on != 0;
+    return SPDZ_OK;
+}
+
+int spdz_dag_kernel_ms(spdz_dag *dag, float *ms) {
+    if (!dag || !ms) return SPDZ_ERR_ARG;
+    if (!dag->kev0) return set_err(dag->ctx, SPDZ_ERR_STATE, "dag_kernel_ms: kernel timing was never enabled");
+    if (cudaEventSynchronize(dag->kev1) != cudaSuccess || cudaEventElapsedTime(ms, dag->kev0, dag->kev1) != cudaSuccess)
+        return set_err(dag->ctx, SPDZ_ERR_CUDA, "dag_kernel_ms: no timed run has completed");
     return SPDZ_OK;
 }
 
@@ -478,7 +510,8 @@ int spdz_run_dag(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan *plan_in, const s
     int launches = 0;
     if (plan.use_graph && !layer_events) {
         const bool reuse = dag->gexec && same_plan(dag->gplan, plan) && dag->gwires.val == wires->val &&
-                           dag->gwires.mac == wires->mac && dag->gwires.stride == wires->stride;
+                           dag->gwires.mac == wires->mac && dag->gwires.stride == wires->stride &&
+                           dag->gtimed == dag->time_kernels;
         if (!reuse) {
             if (dag->gexec) { cudaGraphExecDestroy(dag->gexec); dag->gexec = nullptr; }
             if (dag->graph) { cudaGraphDestroy(dag->graph); dag->graph = nullptr; }
@@ -508,6 +541,7 @@ int spdz_run_dag(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan *plan_in, const s
             dag->gplan = plan;
             dag->gwires = *wires;
             dag->glaunches = n;
+            dag->gtimed = dag->time_kernels;
         }
         DevState *ds = ctx->ds;
         uint64_t tb = tri_base;

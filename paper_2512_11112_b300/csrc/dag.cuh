@@ -39,9 +39,13 @@ struct spdz_dag {
     spdz_plan gplan{};
     spdz_buf gwires{};
     int glaunches = 0;
+    bool gtimed = false;                  // the captured run records kev0 / kev1
     cudaStream_t cap_stream = nullptr;
     // timing
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> lev;
     std::vector<float> layer_us;
+    // spdz_dag_time_kernels: events around the run's circuit kernels
+    bool time_kernels = false;
+    cudaEvent_t kev0 = nullptr, kev1 = nullptr;
 };

@@ -132,6 +132,8 @@ _SIGS = {
     "spdz_run_dag": [_vp, _vp, C.POINTER(spdz_plan), _bufp, C.POINTER(spdz_stats)],
     "spdz_check_result": [_vp, C.POINTER(_int), _vp],
     "spdz_dag_layer_times": [_vp, _vp],
+    "spdz_dag_time_kernels": [_vp, C.c_int32],
+    "spdz_dag_kernel_ms": [_vp, C.POINTER(C.c_float)],
     "spdz_dag_layer_counts": [_vp, _vp],
     "spdz_mul_check_noalloc": [_int, _int, _vp, _bufp, _bufp, _bufp, _bufp, _bufp, _vp, _bufp, _i64, _u64,
                                _u64, _vp],
@@ -387,6 +389,20 @@ def spdz_dag_layer_times(dag, depth: int) -> np.ndarray:
     if rc != SPDZ_OK:
         raise SpdzError(rc, "layer times")
     return out
+
+
+def spdz_dag_time_kernels(dag, on: bool) -> None:
+    rc = lib.spdz_dag_time_kernels(dag, 1 if on else 0)
+    if rc != SPDZ_OK:
+        raise SpdzError(rc, "dag kernel timing")
+
+
+def spdz_dag_kernel_ms(dag) -> float:
+    ms = C.c_float(0.0)
+    rc = lib.spdz_dag_kernel_ms(dag, C.byref(ms))
+    if rc != SPDZ_OK:
+        raise SpdzError(rc, "dag kernel time")
+    return float(ms.value)
 
 
 def spdz_dag_layer_counts(dag, depth: int) -> np.ndarray:

@@ -300,6 +300,37 @@ def test_layer_times_recorded():
         dc.close()
 
 
+def test_kernel_times_recorded():
+    """spdz_dag_time_kernels: events around a run's circuit kernels, in a
+    captured graph and without one, for the tagged and the fused plan; the
+    kernel time lies inside the run's device time, and timing changes no
+    result (a run after it, captured again without the events, equals the
+    oracle)."""
+    dag = W.layered_dag(seed=4, total_gates=2**15, depth=16, wmin=256, wmax=8192, n_inputs=2048)
+    n = 3
+    dc = DeviceCircuit(dag, n, seed=4, runs=5)
+    try:
+        with pytest.raises(S.SpdzError) as e:
+            S.spdz_dag_kernel_ms(dc.h)
+        assert e.value.code == S.SPDZ_ERR_STATE
+        S.spdz_dag_time_kernels(dc.h, True)
+        for plan in (S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=1), S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=0),
+                     S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=1), S.plan(mode=S.SPDZ_SCHED_FUSED, use_graph=0)):
+            st, passed, _ = dc.run(plan)
+            k = S.spdz_dag_kernel_ms(dc.h)
+            assert passed and 0 < k <= st.device_ms, (k, st.device_ms)
+        S.spdz_dag_time_kernels(dc.h, False)
+        st, passed, sig = dc.run(S.plan(mode=S.SPDZ_SCHED_TAGGED, use_graph=1))
+        ev, em, ok, osig = oracle_run(dag, n, seed=4, run_index=4)
+        gv, gm = dc.wires.host()
+        assert passed and ok
+        assert_equal(gv, ev, "run after kernel timing")
+        assert_equal(gm, em, "run after kernel timing, macs")
+        assert_equal(sig, osig, "run after kernel timing, sigma")
+    finally:
+        dc.close()
+
+
 def test_barrier_timeout_is_a_status_not_a_hang():
     """Every barrier waits for one arrival that never comes; the bounded wait
     runs out, the run reports SPDZ_ERR_TIMEOUT, and the context stays usable."""
