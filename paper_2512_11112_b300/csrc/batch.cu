@@ -650,31 +650,43 @@ __global__ void __launch_bounds__(IP_BLOCK) k_innerprod_staged(MulArgs<F> a) {
 // resident warps (the sums then live in 128 registers with a few spilled,
 // faster than one CTA and no spill).
 // p127 inner products with their terms streamed through shared memory as in
-// k_mul127_staged: one warp per product, lane l takes terms l, l + 32, ...;
-// a lane's next term (in this product, else the first of the warp's next
-// product) is copied while it computes the current one.
+// k_mul127_staged.  Each product goes to a pair of warps of one CTA: lane l
+// of the pair's warp h takes terms 32 h + l, 32 h + l + 64, ...; a lane's
+// next term (in this product, else the first of the pair's next product) is
+// copied while it computes the current one.  At the end of a product the
+// second warp hands its sums to the first through shared memory (a named
+// barrier per pair).  With whole products per warp, 16,384 products over
+// the 1776 resident warps take 10 rounds for 9.2 rounds of work; with pairs,
+// 19 half-length rounds for 18.5.
 constexpr int B127IP = 384;
+constexpr int IP_PAIRS = B127IP / 64;
+
+__device__ __forceinline__ void pair_sync(int pair) {
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + pair) : "memory");
+}
 
 template <int NP>
 __global__ void __launch_bounds__(B127IP, 1) k_innerprod127_staged(MulArgs<F127> a) {
     using F = F127;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ u128v xch[IP_PAIRS][2 * NP];
     u128v *sm = reinterpret_cast<u128v *>(smem_raw);
     const uint64_t key = a.ds->key;
     u128v alpha[NP], acc[NP + 1];
     W127 wacc[NP + 1];
 #pragma unroll
     for (int i = 0; i < NP; ++i) alpha[i] = load_alpha<F>(a.ds, i);
-    const int lane = threadIdx.x & 31;
-    const int64_t wstride = ((int64_t)gridDim.x * B127IP) >> 5;
-    const int64_t t0 = (blockIdx.x * (int64_t)B127IP + threadIdx.x) >> 5;
-    p127s_prologue<NP, B127IP>(a, sm, t0 * a.len + lane, t0 < a.N && lane < a.len);
-    for (int64_t t = t0; t < a.N; t += wstride) {
+    const int lane = threadIdx.x & 31, half = (threadIdx.x >> 5) & 1, pair = threadIdx.x >> 6;
+    const int64_t pstride = (int64_t)gridDim.x * IP_PAIRS;
+    const int64_t t0 = (int64_t)blockIdx.x * IP_PAIRS + pair;
+    const int64_t k0 = 32 * half + lane;
+    p127s_prologue<NP, B127IP>(a, sm, t0 * a.len + k0, t0 < a.N && k0 < a.len);
+    for (int64_t t = t0; t < a.N; t += pstride) {
         W127 sums[2 * NP], sde;
-        for (int64_t k = lane; k < a.len; k += 32) {
+        for (int64_t k = k0; k < a.len; k += 64) {
             // the lane's next term
-            const bool same = k + 32 < a.len;
-            const int64_t tn = same ? t : t + wstride, kn = same ? k + 32 : lane;
+            const bool same = k + 64 < a.len;
+            const int64_t tn = same ? t : t + pstride, kn = same ? k + 64 : k0;
             const bool more = tn < a.N && kn < a.len;
             u128v z[NP], gz[NP], eps, dlt;
             const int64_t e = t * a.len + k;
@@ -691,13 +703,22 @@ __global__ void __launch_bounds__(B127IP, 1) k_innerprod127_staged(MulArgs<F127>
             sz[i] = warp_sum<F>(sums[i].reduce());
             sg[i] = warp_sum<F>(sums[NP + i].reduce());
         }
-        if (lane == 0) {
+        if (half && lane == 0) {
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
-                F::st(a.zv + i * a.zs + t, sz[i]);
-                F::st(a.zm + i * a.zs + t, sg[i]);
+                xch[pair][i] = sz[i];
+                xch[pair][NP + i] = sg[i];
             }
         }
+        pair_sync(pair);
+        if (!half && lane == 0) {
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                F::st(a.zv + i * a.zs + t, F::add(sz[i], xch[pair][i]));
+                F::st(a.zm + i * a.zs + t, F::add(sg[i], xch[pair][NP + i]));
+            }
+        }
+        pair_sync(pair);   // the pair's slot is free for its next product
     }
     cp_async_wait_all_groups();
 #pragma unroll
@@ -861,7 +882,7 @@ static void launch_innerprod(spdz_ctx *ctx, const MulArgs<F> &a, int64_t count) 
         auto kern = k_innerprod127_staged<NP>;
         constexpr size_t smem = p127s_smem<NP, B127IP>();
         p127s_smem_attr<NP, 1>(ctx, (const void *)kern, smem);
-        kern<<<grid_for(ctx, (const void *)kern, B127IP, smem, count * 32), B127IP, smem, ctx->stream>>>(a);
+        kern<<<grid_for(ctx, (const void *)kern, B127IP, smem, count * 64), B127IP, smem, ctx->stream>>>(a);
     } else if constexpr (std::is_same_v<F, F127>) {
         auto kern = k_innerprod127<NP>;
         kern<<<grid_for(ctx, (const void *)kern, 256, 0, count * 32), 256, 0, ctx->stream>>>(a);
