@@ -81,13 +81,24 @@ __device__ __forceinline__ void balanced_digits(uint64_t x, float (&d)[TC_DIGITS
 // index division per chunk), a thread eight consecutive columns: eight loads
 // in flight and one 16-byte store of eight digits per plane.
 constexpr int64_t TC_DCHUNK = 2048;
-__global__ void k_digits_rowmajor(const uint64_t *x, int64_t rows, int64_t cols, int64_t ld, int64_t colsp,
-                                  __nv_bfloat16 *planes) {
+// The matrices of one conversion launch (all of one shape): sources, and
+// the planes each one's digits go to.
+constexpr int TC_MAX_JOBS = 2 * SPDZ_MAX_PARTIES + 1;
+struct DigitJobs {
+    const uint64_t *x[TC_MAX_JOBS];
+    int64_t ld;
+    __nv_bfloat16 *planes[TC_MAX_JOBS];
+    int n;
+};
+
+__global__ void k_digits_rowmajor(DigitJobs jb, int64_t rows, int64_t cols, int64_t colsp) {
     const int64_t total = rows * colsp;
-    const int64_t nch = (colsp + TC_DCHUNK - 1) / TC_DCHUNK;
-    for (int64_t c = blockIdx.x; c < rows * nch; c += gridDim.x) {
-        const int64_t r = c / nch, k0 = (c - r * nch) * TC_DCHUNK, k1 = min(colsp, k0 + TC_DCHUNK);
-        const uint64_t *xr = x + r * ld;
+    const int64_t nch = (colsp + TC_DCHUNK - 1) / TC_DCHUNK, per = rows * nch;
+    for (int64_t c = blockIdx.x; c < per * jb.n; c += gridDim.x) {
+        const int64_t q = c / per, cr = c - q * per;
+        const int64_t r = cr / nch, k0 = (cr - r * nch) * TC_DCHUNK, k1 = min(colsp, k0 + TC_DCHUNK);
+        const uint64_t *xr = jb.x[q] + r * jb.ld;
+        __nv_bfloat16 *planes = jb.planes[q];
         for (int64_t c0 = k0 + 8 * (int64_t)threadIdx.x; c0 < k1; c0 += 8 * (int64_t)blockDim.x) {
             uint64_t v[8];
 #pragma unroll
@@ -113,13 +124,14 @@ __global__ void k_digits_rowmajor(const uint64_t *x, int64_t rows, int64_t cols,
 // (bf16), columns rows .. rowsp-1 of each output row zero (rowsp: a multiple
 // of 8), through 64 x 32 shared-memory tiles: a thread writes two
 // consecutive output columns (4-byte stores, 128 bytes per warp and plane).
-__global__ void k_digits_transposed(const uint64_t *x, int64_t rows, int64_t cols, int64_t ld, int64_t rowsp,
-                                    __nv_bfloat16 *planes) {
+__global__ void k_digits_transposed(DigitJobs jb, int64_t rows, int64_t cols, int64_t rowsp) {
     __shared__ uint64_t tile[64][33];
+    const uint64_t *x = jb.x[blockIdx.z];
+    __nv_bfloat16 *planes = jb.planes[blockIdx.z];
     const int64_t r0 = (int64_t)blockIdx.y * 64, c0 = (int64_t)blockIdx.x * 32;
     for (int i = threadIdx.y; i < 64; i += blockDim.y) {
         const int64_t r = r0 + i, c = c0 + threadIdx.x;
-        tile[i][threadIdx.x] = (r < rows && c < cols) ? x[r * ld + c] : 0;
+        tile[i][threadIdx.x] = (r < rows && c < cols) ? x[r * jb.ld + c] : 0;
     }
     __syncthreads();
     const int64_t total = cols * rowsp;
@@ -565,18 +577,30 @@ int matmul_tensor(spdz_ctx *ctx, const uint64_t *E, const uint64_t *Fm, const ui
     uint64_t *dP = (uint64_t *)((((uintptr_t)((unsigned char *)dR + plane_r * 2 * NPn)) + 255) & ~(uintptr_t)255);
     cudaMemsetAsync(err, 0, sizeof(int), ctx->stream);
     const int gb = 4 * ctx->sm_count;
-    const int gd = (int)std::min<int64_t>(m * ((kp + TC_DCHUNK - 1) / TC_DCHUNK), 8 * (int64_t)ctx->sm_count);
-    k_digits_rowmajor<<<gd, 256, 0, ctx->stream>>>(E, m, k, k, kp, dE);
+    // every left matrix (E, then A_i values and MACs) in one launch, every
+    // right matrix (F, then the folded B_i) in another
+    DigitJobs jl{}, jr{};
+    jl.n = jr.n = 1 + 2 * NPn;
+    jl.ld = k;
+    jr.ld = n;
+    jl.x[0] = E;
+    jl.planes[0] = dE;
+    jr.x[0] = Fm;
+    jr.planes[0] = dF;
     for (int w = 0; w < 2; ++w)
-        for (int i = 0; i < NPn; ++i)
-            k_digits_rowmajor<<<gd, 256, 0, ctx->stream>>>((const uint64_t *)(w == 0 ? A->val : A->mac) + (int64_t)i * A->stride,
-                                                           m, k, k, kp, (__nv_bfloat16 *)((unsigned char *)dA + plane_l * (w * NPn + i)));
+        for (int i = 0; i < NPn; ++i) {
+            jl.x[1 + w * NPn + i] = (const uint64_t *)(w == 0 ? A->val : A->mac) + (int64_t)i * A->stride;
+            jl.planes[1 + w * NPn + i] = (__nv_bfloat16 *)((unsigned char *)dA + plane_l * (w * NPn + i));
+        }
+    for (int j = 0; j < 2 * NPn; ++j) {
+        jr.x[1 + j] = Rfold + (int64_t)j * k * n;
+        jr.planes[1 + j] = (__nv_bfloat16 *)((unsigned char *)dR + plane_r * j);
+    }
+    const int gd = (int)std::min<int64_t>(jl.n * m * ((kp + TC_DCHUNK - 1) / TC_DCHUNK), 8 * (int64_t)ctx->sm_count);
+    k_digits_rowmajor<<<gd, 256, 0, ctx->stream>>>(jl, m, k, kp);
     // the transposed kernel covers output columns 0 .. kp-1 (padding included)
-    dim3 tg((unsigned)((n + 31) / 32), (unsigned)((kp + 63) / 64)), tb(32, 8);
-    k_digits_transposed<<<tg, tb, 0, ctx->stream>>>(Fm, k, n, n, kp, dF);
-    for (int j = 0; j < 2 * NPn; ++j)
-        k_digits_transposed<<<tg, tb, 0, ctx->stream>>>(Rfold + (int64_t)j * k * n, k, n, n, kp,
-                                                        (__nv_bfloat16 *)((unsigned char *)dR + plane_r * j));
+    dim3 tg((unsigned)((n + 31) / 32), (unsigned)((kp + 63) / 64), (unsigned)jr.n), tb(32, 8);
+    k_digits_transposed<<<tg, tb, 0, ctx->stream>>>(jr, k, n, kp);
     if (int rc = check_launch(ctx, "matmul tensor digits")) return rc;
     const size_t smem = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
     cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
