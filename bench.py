@@ -748,7 +748,7 @@ def serve_metrics(count, nshape=64, tight_budget_gb=4):
         wait = sorted(1e3 * (r.latency_s - r.online_s) for r in res)
         return {"p50_ms": st.p50_s * 1e3, "p99_ms": st.p99_s * 1e3, "mean_ms": st.mean_s * 1e3,
                 "gates_per_s": st.gates_per_s, "wall_s": st.wall_s, "ticks": st.ticks,
-                "cluster_requests": st.cluster_requests, "dealer_s": st.dealer_s,
+                "cluster_requests": st.cluster_requests, "grid_requests": st.grid_requests, "dealer_s": st.dealer_s,
                 "peak_gb": st.peak_bytes / 2**30, "max_active": st.max_active,
                 "all_checks_passed": all(r.passed == 1 for r in res),
                 "admission_wait_p99_ms": wait[min(len(wait) - 1, int(0.99 * (len(wait) - 1) + 0.5))] if wait else 0.0,
@@ -786,7 +786,8 @@ def serve_metrics(count, nshape=64, tight_budget_gb=4):
                         f"registered circuit shapes", "mean_gates": mean_gates, "arrival_rate_per_s": rate,
             "cost_model_loss": loss, "modes": out,
             "capacity_burst_200": {k: {"gates_per_s": v["gates_per_s"], "wall_s": v["wall_s"],
-                                       "cluster_requests": v["cluster_requests"]} for k, v in cap.items()},
+                                       "cluster_requests": v["cluster_requests"],
+                                       "grid_requests": v["grid_requests"]} for k, v in cap.items()},
             "learned_under_binding_budget": tight}
 
 

@@ -494,11 +494,14 @@ int spdz_sched_choose(spdz_ctx *ctx, spdz_dag *dag, const spdz_buf *wires, int32
  *     that arrive while others run join at the next tick;
  *   SPDZ_SERVE_HEURISTIC: as BATCHED, but a request whose widest layer has at
  *     most cluster_width gates runs all its layers in one cluster launch on a
- *     side stream, overlapping the ticks;
- *   SPDZ_SERVE_LEARNED: as HEURISTIC, but the cluster launch is chosen when
- *     the cost model of model_ctx (trained with spdz_sched_train) predicts it
- *     to finish first, counting the cluster launches already waiting for the
- *     side streams.
+ *     side stream, overlapping the ticks, and a request of at least 2^20
+ *     gates runs all its layers in one fused launch with device barriers
+ *     between layers (a cooperative launch on half the SMs' worth of CTAs)
+ *     on a side stream;
+ *   SPDZ_SERVE_LEARNED: as HEURISTIC, but the cluster or the grid launch is
+ *     chosen when the cost model of model_ctx (trained with
+ *     spdz_sched_train) predicts it to finish first, counting the launches of
+ *     that kind already waiting.
  * Every request is its own MAC-check epoch (key of epoch 0 under
  * check_seed); its result does not depend on the mode or on the other
  * requests.  While the server runs, model_ctx belongs to the server thread:
@@ -532,7 +535,7 @@ typedef struct {
     double latency_s;           /* arrival -> result available on the host */
     double online_s;            /* preprocessing dealt -> result */
     int32_t passed;             /* MAC-check verdict */
-    int32_t mode;               /* 0 ticks, 1 cluster launch */
+    int32_t mode;               /* 0 ticks, 1 cluster launch, 2 grid launch */
     int32_t status;             /* SPDZ_OK; SPDZ_ERR_MAC (check failed); SPDZ_ERR_OOM (can never
                                    fit the budget: refused); SPDZ_ERR_CUDA (session failed) */
     int32_t pad;
@@ -551,6 +554,7 @@ typedef struct {
        device_ticks_timed ticks */
     double device_tick_s;
     int64_t device_ticks_timed;
+    int64_t grid_requests;      /* requests run as one grid launch (mode 2) */
 } spdz_serve_stats;
 
 /* Creates a stopped server on the current device.  Errors: SPDZ_ERR_ARG,

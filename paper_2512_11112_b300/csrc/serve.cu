@@ -47,6 +47,10 @@ int sched_cluster_width();
 int sched_grid_config();
 double sched_switch_us(spdz_ctx *ctx);
 
+// CTAs of a request's grid launch: half the SMs' worth, so two such launches
+// (or one and the ticks) share the GPU.
+static int serve_grid_ctas(int sm_count) { return std::max(1, sm_count / 2); }
+
 // Device-side descriptor of one admitted request (pointers into the arena).
 struct ReqDev {
     const uint4 *rec;
@@ -170,6 +174,8 @@ __global__ void k_serve_init(DevState *ds, const typename F::T *alpha, int n, ui
     ds->partial_fail = 0;
     ds->err_flags = 0;
     ds->res_passed = 0;
+    ds->bar_count = 0;     // (a grid launch's layer barriers)
+    ds->bar_abort = 0;
     for (int i = 0; i < n; ++i) {
         const typename F::T a = F::ld(alpha + i);
         if constexpr (F::WORDS == 1) {
@@ -381,7 +387,9 @@ struct Live {
     ServeCircuit *circ = nullptr;
     std::unique_ptr<ServeCircuit> own;     // one-off circuit (inside the request's block)
     bool cluster = false;
+    bool grid = false;                     // all its layers in one fused launch on part of the grid
     double backlog_us = 0;                 // learned: predicted cluster time it added to the backlog
+    double grid_backlog_us = 0;            // learned: predicted grid-launch time it added
     cudaEvent_t deal0 = nullptr, dealt = nullptr, done = nullptr, up = nullptr;
     bool dealt_ok = false, launched_cluster = false;
     double t_runnable = 0;
@@ -422,7 +430,12 @@ struct spdz_server {
     int64_t next_circuit = 0;
     double tick_us_ema = 0;                // measured duration of one tick (moving average)
     double tick_us_min = 0;                // shortest tick measured: the fixed cost of a tick
+    double tick_us_per_gate = 0;           // ticks' device time per gate beyond the fixed cost (moving average)
+    int64_t ring_gates[RING] = {};         // gates of the tick that used the slot
     double cluster_backlog_us = 0;         // learned: predicted time of cluster launches not yet done
+    double grid_backlog_us = 0;            // learned: predicted time of grid launches not yet done
+    int64_t grid_gates = (int64_t)1 << 20; // heuristic: requests of at least this many gates take a grid launch
+    int64_t st_grid = 0;
     // the serving thread and what it shares with the callers
     std::thread worker;
     std::mutex mu;
@@ -474,6 +487,7 @@ void spdz_server::loop() {
     auto release_live = [&](Live *L) {
         if (L->off >= 0) s->arena.release((size_t)L->off, L->bytes);
         s->cluster_backlog_us = std::max(0.0, s->cluster_backlog_us - L->backlog_us);
+        s->grid_backlog_us = std::max(0.0, s->grid_backlog_us - L->grid_backlog_us);
         if (L->circ && !L->own) L->circ->users -= 1;
         if (L->deal0) cudaEventDestroy(L->deal0);
         if (L->dealt) cudaEventDestroy(L->dealt);
@@ -604,6 +618,7 @@ void spdz_server::loop() {
             // execution mode of the request
             if (mode == SPDZ_SERVE_HEURISTIC) {
                 L->cluster = L->wmax <= cluster_width;
+                L->grid = !L->cluster && L->gates >= grid_gates;
             } else if (mode == SPDZ_SERVE_LEARNED) {
                 // cluster launch when the whole circuit in one cluster is
                 // predicted to finish before its layers would by ticks, each
@@ -637,18 +652,42 @@ void spdz_server::loop() {
                 }
                 if (Cm.predicted) {
                     double tick_mode = 0;
-                    // each layer costs at least one tick's fixed cost (a long
-                    // tick is long because of other requests' wide layers)
+                    // a ticked layer costs at least the tick's fixed cost plus
+                    // its gates at the ticks' measured time per gate, and at
+                    // least its predicted time on the whole grid
                     const double floor_us = tick_us_min > 0 ? tick_us_min : tick_us_ema;
-                    for (double g : Cm.pred_grid_us) tick_mode += std::max(g, floor_us);
+                    for (int l = 0; l < L->depth; ++l) {
+                        const int32_t *c = &C.counts[(size_t)l * 5];
+                        const double gl = (double)c[0] + c[1] + c[2] + c[3] + c[4];
+                        tick_mode += std::max(Cm.pred_grid_us[(size_t)l], floor_us + gl * tick_us_per_gate);
+                    }
                     // a cluster launch first waits for the cluster launches
                     // already queued: their predicted time spread over the
                     // clusters the SMs hold at once
                     const double conc = std::max(1, sm_count / std::max(1, sched_cluster_width()));
-                    L->cluster = cluster_backlog_us / conc + Cm.pred_cluster_us < tick_mode;
+                    const double t_cluster = cluster_backlog_us / conc + Cm.pred_cluster_us;
+                    // a grid launch on GRID_CTAS CTAs: each layer at least
+                    // its predicted time on the whole grid and its bytes at
+                    // that share of DRAM bandwidth, after the grid launches
+                    // already waiting (two run at once)
+                    const double share = hbm_bytes_per_us * serve_grid_ctas(sm_count) / std::max(1, 2 * sm_count);
+                    const double w = field == SPDZ_F61 ? 8.0 : 16.0;
+                    double pred_grid = 0;
+                    for (int l = 0; l < L->depth; ++l) {
+                        const int32_t *c = &C.counts[(size_t)l * 5];
+                        const double bb = n_ * w * (12.0 * c[0] + 6.0 * (c[1] + c[2]) + 4.0 * (c[3] + c[4]));
+                        pred_grid += std::max(Cm.pred_grid_us[(size_t)l], bb / std::max(1.0, share));
+                    }
+                    const double t_grid = grid_backlog_us / 2 + pred_grid;
+                    L->cluster = t_cluster < tick_mode && t_cluster <= t_grid;
+                    L->grid = !L->cluster && t_grid < tick_mode;
                     if (L->cluster) {
                         L->backlog_us = Cm.pred_cluster_us;
                         cluster_backlog_us += L->backlog_us;
+                    }
+                    if (L->grid) {
+                        L->grid_backlog_us = pred_grid;
+                        grid_backlog_us += pred_grid;
                     }
                 }
             }
@@ -698,13 +737,43 @@ void spdz_server::loop() {
                 L->next = L->depth;
                 ++st_cluster;
                 if (cudaGetLastError() != cudaSuccess) rc_fail = SPDZ_ERR_CUDA;
+            } else if (L->grid) {
+                // all its layers in one fused launch with device barriers
+                // between layers, on a side stream; a cooperative launch, so
+                // that every CTA is resident at once
+                cudaStream_t st = side[(size_t)(L->slot % (int)side.size())];
+                cudaStreamWaitEvent(st, L->dealt, 0);
+                const ReqDev &H = h_reqs[L->slot];
+                SPDZ_FIELD_SWITCH(L->field, SPDZ_NP_SWITCH(n_, {
+                    DagArgs<F> a{};
+                    using TT = typename F::T;
+                    a.rec = H.rec; a.kc = (const TT *)H.kc; a.lay = H.lay;
+                    a.wv = (TT *)H.wv; a.wm = (TT *)H.wm; a.ws = H.ws;
+                    for (int k = 0; k < 6; ++k) { a.tp[k] = (const TT *)H.tp[k]; a.ts[k] = H.ts[k]; }
+                    a.ds = H.ds; a.l0 = 0; a.l1 = L->depth;
+                    a.bar_base = 0;
+                    a.spin_ns = 500000000ull;   // bound of one layer barrier wait
+                    const int blk = 256;
+                    const size_t smem = fused_smem<F, NP>(blk);
+                    auto gk = F::WORDS == 1 ? k_dag_fused<F, NP> : k_dag_fused_wide<F, NP>;
+                    if (smem > 48 * 1024) cudaFuncSetAttribute((const void *)gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    void *args[1] = {&a};
+                    cudaLaunchCooperativeKernel((const void *)gk, dim3(serve_grid_ctas(sm_count)), dim3(blk), args, smem, st);
+                    k_serve_check_one<F, NP><<<1, 32, 0, st>>>(H.ds);
+                }));
+                cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming);
+                cudaEventRecord(L->done, st);
+                L->launched_cluster = true;
+                L->next = L->depth;
+                ++st_grid;
+                if (cudaGetLastError() != cudaSuccess) rc_fail = SPDZ_ERR_CUDA;
             }
         }
         if (rc_fail) break;
         // one tick: next layer of every runnable ticking request
         std::vector<Live *> ticking;
         for (Live *L : admitted)
-            if (L->dealt_ok && !L->cluster && L->next < L->depth) ticking.push_back(L);
+            if (L->dealt_ok && !L->cluster && !L->grid && L->next < L->depth) ticking.push_back(L);
         const double tt = now();
         if (!ticking.empty()) {
             // wait for the ring slot to be free again
@@ -717,6 +786,10 @@ void spdz_server::loop() {
                 if (cudaEventElapsedTime(&ms, ring_start[ring], ring_ev[ring]) == cudaSuccess && ms > 0) {
                     tick_us_ema = tick_us_ema == 0 ? ms * 1e3 : 0.9 * tick_us_ema + 0.1 * ms * 1e3;
                     tick_us_min = tick_us_min == 0 ? ms * 1e3 : std::min(tick_us_min, (double)ms * 1e3);
+                    if (ring_gates[ring] > 0) {
+                        const double per = std::max(0.0, ms * 1e3 - tick_us_min) / (double)ring_gates[ring];
+                        tick_us_per_gate = tick_us_per_gate == 0 ? per : 0.9 * tick_us_per_gate + 0.1 * per;
+                    }
                     st_tick_dev_s += ms * 1e-3;
                     ++st_tick_timed;
                 }
@@ -762,6 +835,11 @@ void spdz_server::loop() {
             }
             cudaEventRecord(ring_ev[ring], tick_stream);
             ring_busy[ring] = 1;
+            ring_gates[ring] = 0;
+            for (Live *L : ticking) {
+                const LayerRow &R = L->circ->h_lay[L->next];
+                ring_gates[ring] += R.s[5] - R.s[0];
+            }
             for (Live *L : ticking) {
                 L->next += 1;
                 if (L->next == L->depth) {
@@ -793,7 +871,7 @@ void spdz_server::loop() {
                 res.latency_s = t - L->p.arrival;
                 res.online_s = t - L->t_runnable;
                 res.passed = (int32_t)passed;
-                res.mode = L->cluster ? 1 : 0;
+                res.mode = L->cluster ? 1 : L->grid ? 2 : 0;
                 res.status = passed ? SPDZ_OK : SPDZ_ERR_MAC;
                 res.req_id = L->p.id;
                 lat.push_back(res.latency_s);
@@ -971,13 +1049,14 @@ int spdz_serve_start(spdz_server *s) {
     s->stopping = false;
     s->t0 = std::chrono::steady_clock::now();
     s->lat.clear();
-    s->st_requests = s->st_gates = s->st_ticks = s->st_cluster = 0;
+    s->st_requests = s->st_gates = s->st_ticks = s->st_cluster = s->st_grid = 0;
     s->st_dealer_s = s->st_last_done = 0;
     s->st_max_active = 0;
     s->h_admit = s->h_tick = s->h_done = s->h_idle = s->h_ringwait = 0;
     s->st_tick_dev_s = 0;
     s->st_tick_timed = 0;
     s->cluster_backlog_us = 0;
+    s->grid_backlog_us = 0;
     s->arena.reset_peak();
     for (auto &kv : s->circuits) kv.second->users = 0;
     s->worker = std::thread([s] { s->loop(); });
@@ -1063,6 +1142,7 @@ int spdz_serve_stop(spdz_server *s, spdz_serve_stats *stats) {
         stats->mean_s = v.empty() ? 0 : m / (double)v.size();
         stats->ticks = s->st_ticks;
         stats->cluster_requests = s->st_cluster;
+        stats->grid_requests = s->st_grid;
         stats->dealer_s = s->st_dealer_s;
         stats->peak_bytes = (int64_t)s->arena.peak();
         stats->max_active = s->st_max_active;

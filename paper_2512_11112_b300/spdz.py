@@ -100,7 +100,7 @@ class spdz_serve_stats(C.Structure):
                 ("cluster_requests", C.c_int64), ("dealer_s", C.c_double), ("peak_bytes", C.c_int64),
                 ("max_active", C.c_int32), ("host_admit_s", C.c_double), ("host_tick_s", C.c_double),
                 ("host_complete_s", C.c_double), ("host_idle_s", C.c_double), ("host_ring_wait_s", C.c_double),
-                ("device_tick_s", C.c_double), ("device_ticks_timed", C.c_int64)]
+                ("device_tick_s", C.c_double), ("device_ticks_timed", C.c_int64), ("grid_requests", C.c_int64)]
 
 
 if not os.path.exists(LIB_PATH):

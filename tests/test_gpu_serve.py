@@ -98,6 +98,27 @@ def test_wide_layers_equal_oracle():
             assert_equal(om, em, f"mode {mode} request {k} MACs")
 
 
+def test_grid_launch_requests_equal_oracle():
+    """Requests of at least 2^20 gates (p61 and p127) run in the heuristic
+    mode as one fused launch each (a cooperative launch with device barriers
+    between layers, on a side stream), beside small requests in ticks and
+    cluster launches: every wire equals the oracle's and every check
+    passes."""
+    big = [W.Request(rid=0, arrival_s=0.0, p=O.P61, gates=1200000, depth=4, seed=51),
+           W.Request(rid=1, arrival_s=0.0, p=O.P127, gates=1100000, depth=3, seed=52)]
+    trace = [(r, W.request_dag(r)) for r in big] + small_trace(count=4, seed=53)
+    assert all(d.n_gates >= 2**20 for _, d in trace[:2])
+    O.set_threads(8)
+    expect = [oracle_wires(r, d) for r, d in trace]
+    outs, res, st = serve(trace, S.SPDZ_SERVE_HEURISTIC, budget=2 << 30, cluster_width=1024)
+    assert st.requests == len(trace) and st.grid_requests == 2
+    assert [res[k].mode for k in range(2)] == [2, 2]
+    for k, ((ov, om), (ev, em)) in enumerate(zip(outs, expect)):
+        assert res[k].passed == 1, k
+        assert_equal(ov, ev, f"grid-launch trace, request {k} values")
+        assert_equal(om, em, f"grid-launch trace, request {k} MACs")
+
+
 def test_admission_respects_the_memory_budget():
     trace = small_trace(count=12, seed=8, rate=1e6)     # all arrive at once
     per = []
@@ -168,7 +189,7 @@ def model_ctx():
 
 def test_learned_mode_every_result_equals_oracle(model_ctx):
     """The learned serving mode (the cost model decides, per request, between
-    ticks and one cluster launch): every request of a mixed-field trace
+    ticks, one cluster launch and one grid launch): every request of a mixed-field trace
     equals the oracle's evaluation of that request alone, with its check
     passed; the same requests alone give the same shares.  The p99 latency of
     the learned, heuristic and batched modes on the same 200-request trace
@@ -178,7 +199,7 @@ def test_learned_mode_every_result_equals_oracle(model_ctx):
     outs, res, st = serve(trace, S.SPDZ_SERVE_LEARNED, model_ctx=model_ctx)
     assert st.requests == len(trace)
     for k, ((ov, om), (ev, em)) in enumerate(zip(outs, expect)):
-        assert res[k].passed == 1 and res[k].mode in (0, 1), k
+        assert res[k].passed == 1 and res[k].mode in (0, 1, 2), k
         assert_equal(ov, ev, f"learned mode request {k} values")
         assert_equal(om, em, f"learned mode request {k} MACs")
     for k in (1, 4):
