@@ -620,9 +620,9 @@ void spdz_server::loop() {
                 L->cluster = L->wmax <= cluster_width;
                 L->grid = !L->cluster && L->gates >= grid_gates;
             } else if (mode == SPDZ_SERVE_LEARNED) {
-                // cluster launch when the whole circuit in one cluster is
-                // predicted to finish before its layers would by ticks, each
-                // tick lasting at least the shortest measured tick
+                // the cheapest of ticks, one cluster launch and one grid
+                // launch, each priced from the cost model's per-layer
+                // predictions (below)
                 ServeCircuit &Cm = *L->circ;
                 if (!Cm.predicted) {
                     spdz_dag tmp;
