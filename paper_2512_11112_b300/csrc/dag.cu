@@ -106,8 +106,20 @@ static int launch_tagged(spdz_ctx *ctx, spdz_dag *dag, const spdz_plan &plan, Da
         a.final_check = final_check ? 1 : 0;
         a.l0 = l0;
         a.l1 = l1;
-        kern<<<grid, block, smem, s>>>(a);
-        if (cudaError_t e = cudaGetLastError(); e != cudaSuccess)
+        // a programmatic dependent launch: its CTAs are scheduled while the
+        // kernel before it (the run's begin kernel) finishes, and wait for it
+        // in the kernel
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3((unsigned)block);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if (cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a); e != cudaSuccess)
             return set_err(ctx, SPDZ_ERR_CUDA, "tagged circuit launch: %s", cudaGetErrorString(e));
         *grid_out = grid;
         return SPDZ_OK;

@@ -312,6 +312,9 @@ __device__ __forceinline__ bool grid_wait_relaxed(DevState *ds, unsigned int tar
 // counters and error flags.  Its argument is updated before every replay of
 // a captured run.
 static __global__ void k_run_begin(DevState *ds, uint64_t tri_base, uint32_t df_tag) {
+    // a tagged kernel launched after this one may start its CTAs now: it
+    // waits for this grid's writes (griddepcontrol.wait) before reading them
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     ds->tri_cursor = tri_base;
     ds->bar_count = 0;
     ds->bar_abort = 0;
@@ -652,6 +655,9 @@ __device__ __forceinline__ bool df_layer(const DagArgs<F61> &a, const LayerRow &
 template <int NP>
 __global__ void __launch_bounds__(256, 2) k_dag_tagged(DagArgs<F61> a) {
     using F = F61;
+    // launched as a programmatic dependent of the kernel before it: wait for
+    // that grid's writes (the run's state) before anything reads them
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     extern __shared__ __align__(16) unsigned char smem[];
     Stage<F, NP> st;
     st.init(smem, blockDim.x);
