@@ -143,6 +143,68 @@ __global__ void __launch_bounds__(256) k_ll_open_e(const typename F::T *xv, cons
     block_accumulate<F, NP + 1>(acc, ds->acc);
 }
 
+// The same for p = 2^32-5 with 16-byte rows (din a multiple of 4): a
+// thread takes four consecutive columns k .. k+3 of the tiles blockIdx.y,
+// blockIdx.y + gridDim.y, ... (column index from the grid, no division), with
+// 16-byte loads and stores, and keeps its check terms as exact 128-bit sums
+// of the 64-bit products r * e, reduced once at the end (2^64 == 25 mod p).
+struct Sum128 {
+    uint64_t lo = 0, hi = 0;
+    __device__ __forceinline__ void add(uint64_t v) {
+        asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(lo), "+l"(hi) : "l"(v));
+    }
+    __device__ __forceinline__ uint32_t get() const { return F32::add(F32::reduce64(lo), F32::reduce64(25 * hi)); }
+};
+
+template <int NP>
+__global__ void __launch_bounds__(256) k_ll_open_e4(const uint32_t *xv, const uint32_t *xm, int64_t xs,
+                                                    const uint32_t *bv, const uint32_t *bm, int64_t bs, int64_t T,
+                                                    int64_t din, int64_t R, uint64_t base, uint32_t *E,
+                                                    DevState *ds) {
+    using F = F32;
+    const uint64_t key = ds->key;
+    Sum128 sum[NP + 1];
+    const int64_t k = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+    if (k < din) {
+        uint32_t x[NP][4], gx[NP][4];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(xv + i * xs + k);
+            const uint4 m = *reinterpret_cast<const uint4 *>(xm + i * xs + k);
+            x[i][0] = v.x; x[i][1] = v.y; x[i][2] = v.z; x[i][3] = v.w;
+            gx[i][0] = m.x; gx[i][1] = m.y; gx[i][2] = m.z; gx[i][3] = m.w;
+        }
+        for (int64_t t = blockIdx.y; t < T; t += gridDim.y) {
+            const int64_t j = t * din + k;
+            uint32_t e[4] = {0, 0, 0, 0}, g[NP][4];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                const uint4 b = __ldcs(reinterpret_cast<const uint4 *>(bv + i * bs + j));
+                const uint4 gb = __ldcs(reinterpret_cast<const uint4 *>(bm + i * bs + j));
+                const uint32_t bb[4] = {b.x, b.y, b.z, b.w}, gg[4] = {gb.x, gb.y, gb.z, gb.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    e[u] = F::add(e[u], F::sub(x[i][u], bb[u]));
+                    g[i][u] = F::sub(gx[i][u], gg[u]);
+                }
+            }
+            *reinterpret_cast<uint4 *>(E + j) = make_uint4(e[0], e[1], e[2], e[3]);
+            const uint64_t j0 = base + (uint64_t)(t * (din + R * din) + k);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t r = Draw<F>::at(key, j0 + u);
+                sum[0].add(r * e[u]);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) sum[1 + i].add(r * g[i][u]);
+            }
+        }
+    }
+    uint32_t acc[NP + 1];
+#pragma unroll
+    for (int q = 0; q < NP + 1; ++q) acc[q] = sum[q].get();
+    block_accumulate<F, NP + 1>(acc, ds->acc);
+}
+
 template <class F> struct LLArgs {
     using T = typename F::T;
     const T *wv, *wm;  int64_t ws;        // W   [n][dout*din]
@@ -564,10 +626,24 @@ static void launch_ll(spdz_ctx *ctx, LLState *s, const spdz_buf *W, const spdz_b
     if constexpr (!std::is_same_v<F, F127>) {
         using Tt = typename F::T;
         Tt *E = E_out_dev ? (Tt *)E_out_dev : (Tt *)s->ws;
-        auto ke = k_ll_open_e<F, NP>;
-        ke<<<grid_for(ctx, (const void *)ke, 256, 0, T * din), 256, 0, ctx->stream>>>(
-            (const Tt *)x->val, (const Tt *)x->mac, x->stride, (const Tt *)s->B.val, (const Tt *)s->B.mac,
-            s->B.stride, T, din, R, base, E, ctx->ds);
+        auto al16 = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+        const bool e4 = std::is_same_v<F, F32> && din % 4 == 0 && al16(x->val) && al16(x->mac) && al16(s->B.val) &&
+                        al16(s->B.mac) && al16(E) && (x->stride * 4) % 16 == 0 && (s->B.stride * 4) % 16 == 0;
+        if constexpr (std::is_same_v<F, F32>) {
+            if (e4) {
+                const dim3 g((unsigned)((din / 4 + 255) / 256), (unsigned)std::min<int64_t>(T, 65535));
+                k_ll_open_e4<NP><<<g, 256, 0, ctx->stream>>>((const uint32_t *)x->val, (const uint32_t *)x->mac,
+                                                             x->stride, (const uint32_t *)s->B.val,
+                                                             (const uint32_t *)s->B.mac, s->B.stride, T, din, R, base,
+                                                             E, ctx->ds);
+            }
+        }
+        if (!e4) {
+            auto ke = k_ll_open_e<F, NP>;
+            ke<<<grid_for(ctx, (const void *)ke, 256, 0, T * din), 256, 0, ctx->stream>>>(
+                (const Tt *)x->val, (const Tt *)x->mac, x->stride, (const Tt *)s->B.val, (const Tt *)s->B.mac,
+                s->B.stride, T, din, R, base, E, ctx->ds);
+        }
         LLArgs<F> a{};
         a.wv = (const Tt *)W->val; a.wm = (const Tt *)W->mac; a.ws = W->stride;
         a.av = (const Tt *)s->A.val; a.am = (const Tt *)s->A.mac; a.as = s->A.stride;
