@@ -47,9 +47,12 @@ int sched_cluster_width();
 int sched_grid_config();
 double sched_switch_us(spdz_ctx *ctx);
 
-// CTAs of a request's grid launch: half the SMs' worth, so two such launches
-// (or one and the ticks) share the GPU.
-static int serve_grid_ctas(int sm_count) { return std::max(1, sm_count / 2); }
+// CTAs of a request's grid launch: half of what the GPU holds of the kernel
+// (p61: two CTAs per SM, so one per SM; p127: one per SM, so one per two),
+// so that two such launches (or one and the ticks) share the GPU.
+static int serve_grid_ctas(int sm_count, int field) {
+    return std::max(1, field == SPDZ_F61 ? sm_count : sm_count / 2);
+}
 
 // Device-side descriptor of one admitted request (pointers into the arena).
 struct ReqDev {
@@ -666,11 +669,11 @@ void spdz_server::loop() {
                     // clusters the SMs hold at once
                     const double conc = std::max(1, sm_count / std::max(1, sched_cluster_width()));
                     const double t_cluster = cluster_backlog_us / conc + Cm.pred_cluster_us;
-                    // a grid launch on GRID_CTAS CTAs: each layer at least
-                    // its predicted time on the whole grid and its bytes at
-                    // that share of DRAM bandwidth, after the grid launches
-                    // already waiting (two run at once)
-                    const double share = hbm_bytes_per_us * serve_grid_ctas(sm_count) / std::max(1, 2 * sm_count);
+                    // a grid launch: each layer at least its predicted time on
+                    // the whole grid and its bytes at the launch's share of
+                    // DRAM bandwidth (its CTAs over what the GPU holds), after
+                    // the grid launches already waiting (two run at once)
+                    const double share = hbm_bytes_per_us * serve_grid_ctas(sm_count, field) / std::max(1, (field == SPDZ_F61 ? 2 : 1) * sm_count);
                     const double w = field == SPDZ_F61 ? 8.0 : 16.0;
                     double pred_grid = 0;
                     for (int l = 0; l < L->depth; ++l) {
@@ -758,7 +761,7 @@ void spdz_server::loop() {
                     auto gk = F::WORDS == 1 ? k_dag_fused<F, NP> : k_dag_fused_wide<F, NP>;
                     if (smem > 48 * 1024) cudaFuncSetAttribute((const void *)gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                     void *args[1] = {&a};
-                    cudaLaunchCooperativeKernel((const void *)gk, dim3(serve_grid_ctas(sm_count)), dim3(blk), args, smem, st);
+                    cudaLaunchCooperativeKernel((const void *)gk, dim3(serve_grid_ctas(sm_count, L->field)), dim3(blk), args, smem, st);
                     k_serve_check_one<F, NP><<<1, 32, 0, st>>>(H.ds);
                 }));
                 cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming);
