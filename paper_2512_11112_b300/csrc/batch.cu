@@ -327,8 +327,10 @@ __device__ __forceinline__ void cp_async_wait_all_groups() { asm volatile("cp.as
 // are issued at once; party i's c share and five MAC shares are read from
 // their slots just before party i's combine, and the copies of the next
 // product's are issued at once.  Every copy is in flight for about one
-// product's arithmetic, and no more than one party's shares are live in
-// registers, so 12 warps fit an SM.  Slot k of thread t is at k * B127S + t:
+// product's arithmetic, and besides every party's a and b value shares only
+// one party's other shares are read into registers at a time, so a thread
+// needs 168 registers and 12 warps fit an SM.  Slot k of thread t is at
+// k * B127S + t:
 // a warp's 16-byte accesses of one slot cover 512 consecutive bytes.  Each
 // thread reads only its own slots, after its own cp.async waits: no block
 // barrier.  Per product 1 + NP copy groups are committed, in order: the
