@@ -175,7 +175,7 @@ class Circuit:
         self.wires = SH.alloc(self.field, N_PARTIES, dag.n_wires)
         S.spdz_deal_shared(self.ctx, seed, S.SPDZ_KIND_INPUT, INPUT_SUB, 0, dag.n_inputs, self.alpha_sh,
                            None, self.wires.buf())
-        self.pool_runs = min(runs, pool_runs) if pool_runs else runs
+        self.pool_runs = pool_runs if pool_runs else runs   # refilled as the runs use it
         self.T = self.pool_runs * dag.n_mul
         self.tri = [SH.alloc(self.field, N_PARTIES, self.T) for _ in range(3)]
         self.next_j0 = 0
